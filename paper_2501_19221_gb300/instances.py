@@ -1,0 +1,274 @@
+"""Seeded synthetic problem instances shaped like the benchmark families of the
+VeloxQ benchmark paper (arXiv:2501.19221).
+
+This module only draws random numbers and lays out graphs. It holds none of the
+solver's arithmetic: no energy, no QUBO/Ising conversion (App. A), no dynamics,
+no normalisation. Both the CUDA library and the FP64 oracle consume what it
+returns, so a mistake here cannot hide a disagreement between the two.
+
+Families (each cites the passage whose shape it imitates):
+
+* ``dense_int_qubo``  -- small dense QUBO with integer couplings; the dense
+  all-to-all instances of Sec. "Brute force" use couplings uniform in [-1, 1].
+* ``sk_qubo``         -- dense Sherrington-Kirkpatrick-type QUBO with Gaussian
+  couplings scaled by 1/sqrt(n) (dense instances of the B&B comparison).
+* ``chimera_ising``   -- Chimera C_{m,n} graph of K_{4,4} cells with +-J
+  couplings (Sec. "Structure-exploiting solvers").
+* ``wishart_ising``   -- Wishart planted ensemble (Sec. "Wishart ensemble").
+* ``cubic_lattice_ising`` -- periodic 3-D +-J lattice (periodic-lattice
+  planting family, very large sparse instances of Sec. "Zephyr").
+* ``random_sparse_qubo`` -- ragged sparse QUBO (empty rows, uneven degree) used
+  as an edge case by the tests.
+
+Sparse instances are returned as symmetric CSR (both (i, j) and (j, i) are
+stored, column indices strictly increasing within each row, no diagonal).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "SparseCoupling",
+    "dense_int_qubo",
+    "sk_qubo",
+    "chimera_edges",
+    "chimera_ising",
+    "cubic_lattice_ising",
+    "wishart_ising",
+    "wishart_sizes",
+    "random_sparse_qubo",
+    "uniform_state",
+    "random_binary",
+]
+
+
+@dataclass
+class SparseCoupling:
+    """A symmetric sparse coupling matrix in CSR form plus a linear term.
+
+    ``rowptr`` is int64 (n+1), ``col`` int32 (nnz), ``val`` the coupling values
+    (int8 / int32 / float32 / float64), ``lin`` the linear term (h for an Ising
+    model, c for a QUBO) as float64 (n).
+    """
+
+    n: int
+    rowptr: np.ndarray
+    col: np.ndarray
+    val: np.ndarray
+    lin: np.ndarray
+
+    @property
+    def nnz(self) -> int:
+        return int(self.rowptr[-1])
+
+    def to_dense(self, dtype=np.float64) -> np.ndarray:
+        out = np.zeros((self.n, self.n), dtype=dtype)
+        rows = np.repeat(np.arange(self.n), np.diff(self.rowptr))
+        out[rows, self.col] = self.val
+        return out
+
+
+def _csr_from_edges(n: int, u: np.ndarray, v: np.ndarray, w: np.ndarray) -> tuple:
+    """Symmetric CSR from an undirected edge list (u < v), sorted columns."""
+    rows = np.concatenate([u, v]).astype(np.int64)
+    cols = np.concatenate([v, u]).astype(np.int64)
+    vals = np.concatenate([w, w])
+    order = np.lexsort((cols, rows))
+    rows, cols, vals = rows[order], cols[order], vals[order]
+    counts = np.bincount(rows, minlength=n)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    return rowptr, cols.astype(np.int32), vals
+
+
+def dense_int_qubo(n: int = 20, lo: int = -8, hi: int = 8, seed: int = 0):
+    """Dense symmetric integer QUBO matrix (int32, n x n) and c = 0.
+
+    The upper triangle including the diagonal is drawn uniformly from the
+    integers [lo, hi] and mirrored into the lower triangle.
+    """
+    rng = np.random.default_rng(seed)
+    upper = rng.integers(lo, hi + 1, size=(n, n), dtype=np.int64)
+    Q = np.triu(upper) + np.triu(upper, 1).T
+    return Q.astype(np.int32), np.zeros(n, dtype=np.float64)
+
+
+def sk_qubo(n: int = 8192, seed: int = 0, dtype=np.float32):
+    """Dense symmetric Gaussian QUBO: Q_ij ~ N(0, 1)/sqrt(n), Q_ii = 0, c = 0."""
+    rng = np.random.default_rng(seed)
+    g = rng.standard_normal((n, n), dtype=np.float32) if dtype == np.float32 else rng.standard_normal((n, n))
+    Q = np.triu(g, 1)
+    Q = Q + Q.T
+    Q *= np.asarray(1.0 / np.sqrt(n), dtype=Q.dtype)
+    return np.ascontiguousarray(Q.astype(dtype)), np.zeros(n, dtype=np.float64)
+
+
+def chimera_edges(m: int = 16, n: int = 16, t: int = 4):
+    """Edges (u < v) of the Chimera graph C_{m,n} with shore size t.
+
+    Vertex (row, col, shore, k) has index ((row*n + col)*2 + shore)*t + k.
+    Inside a cell the two shores form a complete bipartite graph K_{t,t};
+    shore 0 couples to the same k in the cell below, shore 1 to the same k in
+    the cell to the right.
+    """
+    def vid(r, c, s, k):
+        return ((r * n + c) * 2 + s) * t + k
+
+    us, vs = [], []
+    for r in range(m):
+        for c in range(n):
+            for k1 in range(t):
+                for k2 in range(t):
+                    us.append(vid(r, c, 0, k1))
+                    vs.append(vid(r, c, 1, k2))
+            for k in range(t):
+                if r + 1 < m:
+                    us.append(vid(r, c, 0, k))
+                    vs.append(vid(r + 1, c, 0, k))
+                if c + 1 < n:
+                    us.append(vid(r, c, 1, k))
+                    vs.append(vid(r, c + 1, 1, k))
+    u = np.asarray(us, dtype=np.int64)
+    v = np.asarray(vs, dtype=np.int64)
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    return lo, hi
+
+
+def chimera_ising(m: int = 16, n: int = 16, t: int = 4, seed: int = 0) -> SparseCoupling:
+    """Ising model on C_{m,n}: J uniform on {-1, +1} per edge (int8), h = 0."""
+    u, v = chimera_edges(m, n, t)
+    rng = np.random.default_rng(seed)
+    w = (2 * rng.integers(0, 2, size=u.shape[0]) - 1).astype(np.int8)
+    nv = 2 * t * m * n
+    rowptr, col, val = _csr_from_edges(nv, u, v, w)
+    return SparseCoupling(nv, rowptr, col, val, np.zeros(nv, dtype=np.float64))
+
+
+def cubic_lattice_ising(L: int, seed: int = 0) -> SparseCoupling:
+    """Periodic L x L x L +-J lattice (int8 couplings, h = 0), L >= 3.
+
+    Site (x, y, z) has index (z*L + y)*L + x. Each site owns the three bonds
+    to +x, +y, +z; every row therefore holds exactly six entries.
+    """
+    if L < 3:
+        raise ValueError("L must be >= 3 so that the six neighbours are distinct")
+    n = L * L * L
+    rng = np.random.default_rng(seed)
+    # one +-1 bond per site and direction (bond from i to i + e_d)
+    bonds = (2 * rng.integers(0, 2, size=(3, n), dtype=np.int8) - 1).astype(np.int8)
+    idx = np.arange(n, dtype=np.int64)
+    x = idx % L
+    y = (idx // L) % L
+    z = idx // (L * L)
+    strides = (1, L, L * L)
+    coords = (x, y, z)
+    cols = np.empty((6, n), dtype=np.int64)
+    vals = np.empty((6, n), dtype=np.int8)
+    for d in range(3):
+        s = strides[d]
+        c = coords[d]
+        plus = idx + np.where(c == L - 1, -(L - 1) * s, s)
+        minus = idx - np.where(c == 0, -(L - 1) * s, s)
+        cols[2 * d] = plus
+        vals[2 * d] = bonds[d]
+        cols[2 * d + 1] = minus
+        vals[2 * d + 1] = bonds[d][minus]
+    del idx, x, y, z
+    # sort the six columns of every row: odd-even transposition sort, 6 rounds
+    pairs = [(0, 1), (2, 3), (4, 5), (1, 2), (3, 4)] * 3
+    for a, b in pairs:
+        swap = cols[a] > cols[b]
+        ca, cb = cols[a].copy(), cols[b].copy()
+        va, vb = vals[a].copy(), vals[b].copy()
+        cols[a] = np.where(swap, cb, ca)
+        cols[b] = np.where(swap, ca, cb)
+        vals[a] = np.where(swap, vb, va)
+        vals[b] = np.where(swap, va, vb)
+    col = np.ascontiguousarray(cols.T).reshape(-1).astype(np.int32)
+    val = np.ascontiguousarray(vals.T).reshape(-1)
+    rowptr = np.arange(n + 1, dtype=np.int64) * 6
+    return SparseCoupling(n, rowptr, col, val, np.zeros(n, dtype=np.float64))
+
+
+def wishart_ising(N: int, alpha: float, seed: int = 0, dtype=np.float64) -> dict:
+    """Wishart planted ensemble (Sec. "Wishart ensemble").
+
+    Draws a planted +-1 vector t (gauge randomisation of the ferromagnetic
+    state), M = max(1, round(alpha*N)) columns w ~ N(0, Sigma) with
+    Sigma = N/(N-1) (I - t t^T / N), and returns
+
+    * ``J``  -- the coupling matrix of H_WP = -1/2 sum_{i,j} J_ij s_i s_j,
+      J = Jt - diag(Jt) with Jt = -W W^T / N (zero diagonal, symmetric);
+    * ``Jt_diag`` -- diag(Jt), from which the planted energy follows;
+    * ``t``  -- the planted state (int8);
+    * ``W``  -- the N x M matrix.
+    """
+    rng = np.random.default_rng(seed)
+    t = (2 * rng.integers(0, 2, size=N) - 1).astype(np.float64)
+    M = max(1, int(round(alpha * N)))
+    z = rng.standard_normal((N, M))
+    proj = z - np.outer(t, t @ z) / N
+    W = np.sqrt(N / (N - 1.0)) * proj
+    Jt = -(W @ W.T) / N
+    d = np.diag(Jt).copy()
+    J = Jt - np.diag(d)
+    return {"J": J.astype(dtype), "Jt_diag": d, "t": t.astype(np.int8), "W": W}
+
+
+def wishart_sizes(count: int = 512, nmin: int = 100, nmax: int = 2000, seed: int = 0) -> np.ndarray:
+    """Instance sizes n_i uniform on {nmin, ..., nmax} for a Wishart batch."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(nmin, nmax + 1, size=count)
+
+
+def random_sparse_qubo(n: int, mean_degree: float, seed: int = 0, vtype=np.int32,
+                       lo: int = -5, hi: int = 5, empty_rows: int = 0,
+                       with_diag: bool = True) -> SparseCoupling:
+    """Ragged symmetric sparse QUBO for edge-case tests.
+
+    Edges are drawn uniformly (duplicates removed); the first ``empty_rows``
+    vertices get no edges at all. Values are integers in [lo, hi] \\ {0}
+    (cast to ``vtype``). If ``with_diag`` the diagonal is stored too, so the
+    CSR also carries linear terms the way a QUBO matrix does.
+    """
+    rng = np.random.default_rng(seed)
+    m = int(mean_degree * n / 2)
+    u = rng.integers(empty_rows, n, size=m)
+    v = rng.integers(empty_rows, n, size=m)
+    keep = u != v
+    u, v = u[keep], v[keep]
+    lo_, hi_ = np.minimum(u, v), np.maximum(u, v)
+    key = np.unique(lo_ * n + hi_)
+    lo_, hi_ = key // n, key % n
+    w = rng.integers(lo, hi + 1, size=lo_.shape[0])
+    w[w == 0] = 1
+    if with_diag:
+        diag_idx = np.arange(n, dtype=np.int64)
+        dw = rng.integers(lo, hi + 1, size=n)
+        rows = np.concatenate([lo_, hi_, diag_idx])
+        cols = np.concatenate([hi_, lo_, diag_idx])
+        vals = np.concatenate([w, w, dw])
+        order = np.lexsort((cols, rows))
+        rows, cols, vals = rows[order], cols[order], vals[order]
+        counts = np.bincount(rows, minlength=n)
+        rowptr = np.zeros(n + 1, dtype=np.int64)
+        np.cumsum(counts, out=rowptr[1:])
+        col = cols.astype(np.int32)
+        val = vals
+    else:
+        rowptr, col, val = _csr_from_edges(n, lo_, hi_, w)
+    return SparseCoupling(n, rowptr, col, np.asarray(val).astype(vtype), np.zeros(n, dtype=np.float64))
+
+
+def uniform_state(R: int, n: int, lo: float = -1.0, hi: float = 1.0, seed: int = 0) -> np.ndarray:
+    """A float32 replica-major state block [R][n] with entries uniform in [lo, hi)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(lo, hi, size=(R, n)).astype(np.float32)
+
+
+def random_binary(B: int, n: int, seed: int = 0, p: float = 0.5) -> np.ndarray:
+    """A uint8 batch [B][n] of binary vectors with P(x_i = 1) = p."""
+    rng = np.random.default_rng(seed)
+    return (rng.random((B, n)) < p).astype(np.uint8)

@@ -1,0 +1,400 @@
+"""Pins of the FP64 oracle against facts that do not come from the oracle itself:
+published test vectors, hand-derived optima, closed forms, brute force and
+mathematical identities. Each test names the plausible oracle mistake it would
+catch. CPU only."""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_19221_gb300 import instances as I
+
+
+def _read_rows(path):
+    rows = []
+    with open(path) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line.split())
+    return rows
+
+
+# ---------------------------------------------------------------- Philox
+def test_philox_published_vectors(golden_dir):
+    """Random123 known-answer vectors (catches a wrong multiplier, key bump,
+    word order or round count)."""
+    rows = _read_rows(os.path.join(golden_dir, "philox4x32_10_kat.txt"))
+    assert len(rows) == 3
+    for row in rows:
+        v = [int(t, 16) for t in row]
+        out = O.philox4x32_10(v[0:4], v[4:6])
+        assert [int(o) for o in out] == v[6:10]
+
+
+def test_init_state_range_and_exactness():
+    S0, Y0 = O.init_state(257, 3, seed=12345, sigma0=0.1)
+    assert S0.dtype == np.float32 and S0.shape == (3, 257)
+    assert np.all(np.abs(S0) < 0.1) and np.all(np.abs(Y0) < 0.1)
+    # u = m 2^-24 exactly => v = sigma0 (2u-1); recompute from the raw words
+    w = O.philox4x32_10([5, 0, 2, 0], [12345, 0])
+    u = np.float32(w[0] >> 8) * np.float32(2.0 ** -24)
+    assert S0[2, 5] == np.float32(0.1) * (np.float32(2.0) * u - np.float32(1.0))
+    # different replicas / seeds differ
+    assert not np.array_equal(S0[0], S0[1])
+    S1, _ = O.init_state(257, 3, seed=12346, sigma0=0.1)
+    assert not np.array_equal(S0, S1)
+
+
+# ---------------------------------------------------------------- energies
+def test_worked_example_sdk_bqm(golden_dir):
+    """The paper's SDK example, optimum derived by hand (catches a sign error
+    in the App. A conversion constant or in the energy)."""
+    row = [float(t) for t in _read_rows(os.path.join(golden_dir, "sdk_bqm_example.txt"))[0]]
+    n = int(row[0])
+    h = np.array(row[1:4])
+    J = np.zeros((3, 3))
+    J[0, 1], J[0, 2], J[1, 2] = row[4:7]
+    H_min, s_star = row[7], np.array(row[8:11], dtype=np.int8)
+    assert O.ising_energy(J, h, s_star) == H_min
+    Hs = [O.ising_energy(J, h, np.array(s, dtype=np.int8)) for s in itertools.product([-1, 1], repeat=n)]
+    assert min(Hs) == H_min and Hs.count(H_min) == 1
+    Q, C = O.ising_to_qubo(J, h)
+    p = O.problem_from_dense(Q)
+    E, x, _ = O.bruteforce(p)
+    assert 2 * E + C == pytest.approx(H_min, abs=1e-12)
+    assert np.array_equal(2 * x.astype(int) - 1, s_star)
+
+
+def test_single_flip_identity_nonsymmetric():
+    """E(x ^ e_i) - E(x) = (1 - 2x_i)(Q_ii + c_i + sum_{j!=i}(Q_ij + Q_ji) x_j)
+    on every x of a non-symmetric integer QUBO with linear terms (catches a
+    dropped diagonal, linear or transposed term in the energy)."""
+    rng = np.random.default_rng(3)
+    n = 9
+    Q = rng.integers(-7, 8, size=(n, n))
+    c = rng.integers(-5, 6, size=n).astype(np.float64)
+    p = O.problem_from_dense(Q, c)
+    X = np.array(list(itertools.product([0, 1], repeat=n)), dtype=np.uint8)
+    E = O.energy(p, X)
+    assert E.dtype == np.int64
+    idx = {tuple(x): e for x, e in zip(X.tolist(), E.tolist())}
+    for x, e in zip(X, E):
+        for i in range(n):
+            xf = x.copy()
+            xf[i] ^= 1
+            dE = idx[tuple(xf.tolist())] - e
+            rhs = (1 - 2 * int(x[i])) * (Q[i, i] + c[i] + sum((Q[i, j] + Q[j, i]) * int(x[j]) for j in range(n) if j != i))
+            assert dE == rhs
+
+
+def test_energy_small_values_by_hand():
+    """E(0) = 0, E(e_i) = Q_ii + c_i, E(e_i + e_j) = Q_ii + Q_jj + Q_ij + Q_ji + c_i + c_j."""
+    Q = np.array([[2, -3, 0], [5, 1, 4], [0, -6, -2]])
+    c = np.array([1.0, 0.0, -1.0])
+    p = O.problem_from_dense(Q, c)
+    X = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0], [0, 1, 1], [1, 1, 1]], dtype=np.uint8)
+    assert O.energy(p, X).tolist() == [0, 3, 1, 2 + 1 - 3 + 5 + 1, 1 - 2 + 4 - 6 - 1, 2 + 1 - 2 - 3 + 5 + 4 - 6 + 1 - 1]
+
+
+def test_bruteforce_diagonal_closed_form():
+    """Separable QUBO: min E = sum_i min(0, Q_ii + c_i), and the count of
+    minimisers is 2^(number of zero diagonal terms)."""
+    d = np.array([3, -2, 0, -5, 4, 0, -1])
+    p = O.problem_from_dense(np.diag(d))
+    E, x, count = O.bruteforce(p)
+    assert E == np.minimum(d, 0).sum()
+    assert count == 4
+    assert O.energy(p, x)[0] == E
+
+
+def test_bruteforce_is_global_minimum_n20():
+    """The n = 20 dense integer workload: the enumerated minimum is attained by
+    the returned x, no single flip improves it, and random vectors never beat it."""
+    Q, c = I.dense_int_qubo(20, seed=0)
+    p = O.problem_from_dense(Q, c)
+    E, x, count = O.bruteforce(p)
+    assert O.energy(p, x)[0] == E and count >= 1
+    flips = np.repeat(x[None, :], 20, axis=0)
+    flips[np.arange(20), np.arange(20)] ^= 1
+    assert np.all(O.energy(p, flips) >= E)
+    rnd = I.random_binary(2000, 20, seed=9)
+    assert np.all(O.energy(p, rnd) >= E)
+
+
+def test_float_energy_matches_exact_rationals():
+    """FP64 energy against exact fractions on dyadic values."""
+    from fractions import Fraction
+    rng = np.random.default_rng(1)
+    n = 12
+    Q = rng.integers(-64, 64, size=(n, n)) / 8.0
+    c = rng.integers(-64, 64, size=n) / 4.0
+    p = O.problem_from_dense(Q, c)
+    X = I.random_binary(50, n, seed=2)
+    E = O.energy(p, X)
+    for x, e in zip(X, E):
+        ref = sum(Fraction(Q[i, j]) for i in range(n) for j in range(n) if x[i] and x[j]) + \
+            sum(Fraction(c[i]) for i in range(n) if x[i])
+        assert Fraction(e) == ref
+
+
+# ---------------------------------------------------------------- App. A
+def test_ising_to_qubo_identity_all_states():
+    """H(s) = 2 Q(x) + C for every s (catches the sign of C, a missing row sum
+    or a factor 2 in the diagonal)."""
+    rng = np.random.default_rng(7)
+    n = 10
+    J = np.triu(rng.normal(size=(n, n)), 1)
+    J = J + J.T
+    h = rng.normal(size=n)
+    Q, C = O.ising_to_qubo(J, h)
+    p = O.problem_from_dense(Q)
+    S = np.array(list(itertools.product([-1, 1], repeat=n)), dtype=np.int8)
+    X = ((S + 1) // 2).astype(np.uint8)
+    E = O.energy(p, X)
+    H = np.array([O.ising_energy(J, h, s) for s in S])
+    assert np.allclose(H, 2 * E + C, rtol=0, atol=1e-10)
+    # the paper's printed constant (opposite sign) fails unless C == 0
+    assert abs(C) > 1e-3 and not np.allclose(H, 2 * E - C, atol=1e-6)
+
+
+def test_qubo_to_ising_identity_all_states():
+    """Q(x) = H(s)/2 + C/2 for symmetric Q (App. A, derived sign)."""
+    rng = np.random.default_rng(8)
+    n = 9
+    A = rng.normal(size=(n, n))
+    Q = A + A.T
+    J, h, C = O.qubo_to_ising(Q)
+    p = O.problem_from_dense(Q)
+    S = np.array(list(itertools.product([-1, 1], repeat=n)), dtype=np.int8)
+    X = ((S + 1) // 2).astype(np.uint8)
+    E = O.energy(p, X)
+    H = np.array([O.ising_energy(J, h, s) for s in S])
+    assert np.allclose(E, 0.5 * H + 0.5 * C, rtol=0, atol=1e-10)
+
+
+def test_ising_to_qubo_uses_upper_triangle():
+    """eq. (ising_model) sums i < j: the lower triangle of J is ignored."""
+    rng = np.random.default_rng(2)
+    n = 6
+    U = np.triu(rng.normal(size=(n, n)), 1)
+    h = rng.normal(size=n)
+    Q1, C1 = O.ising_to_qubo(U, h)
+    Q2, C2 = O.ising_to_qubo(U + rng.normal(size=(n, n)) * np.tril(np.ones((n, n)), -1), h)
+    assert np.array_equal(Q1, Q2) and C1 == C2
+
+
+# ---------------------------------------------------------------- Wishart
+@pytest.mark.parametrize("alpha", [0.2, 0.75, 1.0])
+def test_wishart_planted_ground_state(alpha):
+    """Sec. Wishart ensemble: E0 = -t^T J t / 2 = Tr(Jt)/2 and no state is
+    lower (H(s) - E0 = |W^T s|^2 / (2N) >= 0); checked by enumeration, and
+    through the App. A conversion to a QUBO."""
+    N = 12
+    w = I.wishart_ising(N, alpha, seed=4)
+    J, t, W = w["J"], w["t"].astype(np.float64), w["W"]
+    E0 = 0.5 * w["Jt_diag"].sum()
+    Jis = -J                     # H_WP = -1/2 sum_{ij} J s s = sum_{i<j} (-J_ij) s s
+    h = np.zeros(N)
+    assert O.ising_energy(Jis, h, t.astype(np.int8)) == pytest.approx(E0, rel=1e-12)
+    S = np.array(list(itertools.product([-1, 1], repeat=N)), dtype=np.int8)
+    H = np.array([O.ising_energy(Jis, h, s) for s in S])
+    assert H.min() == pytest.approx(E0, rel=1e-10)
+    gap = ((S.astype(np.float64) @ W) ** 2).sum(axis=1) / (2 * N)
+    assert np.allclose(H - E0, gap, atol=1e-9)
+    Q, C = O.ising_to_qubo(Jis, h)
+    Emin, x, _ = O.bruteforce(O.problem_from_dense(Q))
+    assert 2 * Emin + C == pytest.approx(E0, rel=1e-10)
+
+
+# ---------------------------------------------------------------- field / bias
+def test_relaxed_energy_equals_energy_on_binary_states():
+    """For binary s = 2x - 1: s^T Qoff s/4 + b^T s/2 + K0 = E(x) (catches a
+    dropped or mis-scaled term in the field, in b or in K0)."""
+    rng = np.random.default_rng(5)
+    n = 8
+    Q = rng.normal(size=(n, n))          # non-symmetric on purpose
+    c = rng.normal(size=n)
+    p = O.problem_from_dense(Q, c)
+    X = np.array(list(itertools.product([0, 1], repeat=n)), dtype=np.uint8)
+    S = 2.0 * X - 1.0
+    assert np.allclose(O.relaxed_energy(p, S), O.energy(p, X), atol=1e-11)
+
+
+def test_field_is_gradient_of_relaxed_energy():
+    """dE_relax/ds = (Qoff s + b)/2 by central differences (catches a
+    transposed operand or a diagonal left in the field)."""
+    rng = np.random.default_rng(6)
+    n = 7
+    Q = rng.normal(size=(n, n))
+    c = rng.normal(size=n)
+    p = O.problem_from_dense(Q, c)
+    s = rng.uniform(-1, 1, size=(1, n))
+    F = O.field(p, s)
+    b, _ = O.bias(p)
+    h = 1e-6
+    for i in range(n):
+        sp, sm = s.copy(), s.copy()
+        sp[0, i] += h
+        sm[0, i] -= h
+        g = (O.relaxed_energy(p, sp)[0] - O.relaxed_energy(p, sm)[0]) / (2 * h)
+        assert g == pytest.approx(0.5 * F[0, i] + 0.5 * b[i], rel=1e-7, abs=1e-8)
+
+
+def test_field_csr_equals_dense_form():
+    """The same Q given as CSR (stored entries only) and as a dense matrix
+    gives the same field, bias and energies."""
+    sp = I.random_sparse_qubo(40, 5, seed=11, empty_rows=4)
+    pc = O.problem_from_csr(sp.n, sp.rowptr, sp.col, sp.val)
+    pd = O.problem_from_dense(sp.to_dense())
+    S = I.uniform_state(3, 40, seed=1).astype(np.float64)
+    assert np.allclose(O.field(pc, S), O.field(pd, S), atol=1e-12)
+    assert np.allclose(O.bias(pc)[0], O.bias(pd)[0]) and O.bias(pc)[1] == pytest.approx(O.bias(pd)[1])
+    X = I.random_binary(20, 40, seed=2)
+    assert np.array_equal(O.energy(pc, X), O.energy(pd, X))
+
+
+# ---------------------------------------------------------------- schedule
+def test_schedule_default_and_knots():
+    K = 11
+    a = O.schedule(K, [0.0, 1.0])
+    assert np.allclose(a, np.arange(K) / (K - 1))
+    a3 = O.schedule(K, [0.0, 0.2, 1.0])
+    assert a3[0] == 0.0 and a3[5] == pytest.approx(0.2) and a3[10] == pytest.approx(1.0)
+    assert a3[3] == pytest.approx(0.2 * 3 / 5)
+    assert O.schedule(1, [0.0, 1.0])[0] == 0.0
+
+
+# ---------------------------------------------------------------- dynamics
+def test_uncoupled_dynamics_closed_form():
+    """Q = 0, c = 0: each spin is the linear map
+    [s', y'] = [[1 - dt^2 a0 (a0 - a_k), dt a0], [-dt (a0 - a_k), 1]] [s, y]
+    until a wall is hit (catches a wrong update order or sign)."""
+    n, R, K = 5, 2, 40
+    p = O.problem_from_dense(np.zeros((n, n), dtype=np.int64))
+    S0, Y0 = O.init_state(n, R, seed=3, sigma0=0.1)
+    dt, a0 = 0.3, 1.0
+    out = O.bsb_run(p, R, K, dt, a0, 0.7, [0.0, a0], 0, S0, Y0, n_snap=K)
+    a = O.schedule(K, [0.0, a0])
+    s, y = S0.astype(np.float64).copy(), Y0.astype(np.float64).copy()
+    for k in range(K):
+        M = np.array([[1 - dt * dt * a0 * (a0 - a[k]), dt * a0], [-dt * (a0 - a[k]), 1.0]])
+        s, y = M[0, 0] * s + M[0, 1] * y, M[1, 0] * s + M[1, 1] * y
+        assert np.all(np.abs(s) < 1)
+        assert np.allclose(out["S_snap"][k], s, atol=1e-14)
+        assert np.allclose(out["Y_snap"][k], y, atol=1e-14)
+
+
+def test_wall_resets_position_and_momentum():
+    """|s| > 1 after the position update => s = sign(s), y = 0; |s| = 1 exactly is kept."""
+    F = np.zeros((1, 3))
+    b = np.zeros(3)
+    S = np.array([[0.9, -0.9, 0.5]])
+    Y = np.array([[0.5, -0.5, 1.0]])
+    S1, Y1 = O.bsb_update(F, b, 1.0, 0.5, 1.0, 1.0, S, Y)   # a_k = a0: free drift
+    assert S1.tolist() == [[1.0, -1.0, 1.0]]
+    assert Y1.tolist() == [[0.0, 0.0, 1.0]]
+
+
+def _chimera_problem():
+    sp = I.chimera_ising(2, 2, 4, seed=1)
+    J = sp.to_dense()
+    Q, C = O.ising_to_qubo(np.triu(J, 1), sp.lin)
+    return O.problem_from_dense(Q.astype(np.int64)), Q
+
+
+def test_z2_equivariance_bitwise():
+    """b = 0 (h = 0 Ising instance): negating (s0, y0) negates the whole
+    trajectory bit for bit (catches a stray bias or asymmetric clamp)."""
+    p, _ = _chimera_problem()
+    assert np.all(O.bias(p)[0] == 0)
+    S0, Y0 = O.init_state(p.n, 3, seed=5, sigma0=0.5)
+    A = O.bsb_run(p, 3, 60, 0.4, 1.0, 0.3, [0, 1], 0, S0, Y0)
+    B = O.bsb_run(p, 3, 60, 0.4, 1.0, 0.3, [0, 1], 0, -S0, -Y0)
+    assert np.array_equal(A["S"], -B["S"]) and np.array_equal(A["Y"], -B["Y"])
+    assert np.any(np.abs(A["S"]) == 1.0)   # walls were exercised
+
+
+def test_replica_permutation_bitwise():
+    """Replicas are independent columns: permuting them permutes every output."""
+    sp = I.random_sparse_qubo(30, 4, seed=2)
+    p = O.problem_from_csr(sp.n, sp.rowptr, sp.col, sp.val)
+    S0, Y0 = O.init_state(p.n, 5, seed=8, sigma0=0.3)
+    perm = np.array([3, 0, 4, 1, 2])
+    A = O.bsb_run(p, 5, 80, 0.5, 1.0, 0.1, [0, 1], 10, S0, Y0)
+    B = O.bsb_run(p, 5, 80, 0.5, 1.0, 0.1, [0, 1], 10, S0[perm], Y0[perm])
+    assert np.array_equal(A["S"][perm], B["S"])
+    assert np.array_equal(A["best_E_i64"][perm], B["best_E_i64"])
+    assert np.array_equal(A["best_x"][perm], B["best_x"])
+
+
+def test_run_best_is_energy_of_best_x_and_readout_cadence():
+    """best_E equals the exact energy of best_x; with readout only at the end,
+    best_x is the sign readout of the final state."""
+    Q, c = I.dense_int_qubo(20, seed=0)
+    p = O.problem_from_dense(Q, c)
+    S0, Y0 = O.init_state(20, 16, seed=1, sigma0=0.1)
+    out = O.bsb_run(p, 16, 300, 0.5, 1.0, 0.05, [0, 1], 0, S0, Y0)
+    assert np.array_equal(O.energy(p, out["best_x"]), out["best_E_i64"])
+    assert np.array_equal(out["best_x"], (out["S"] > 0).astype(np.uint8))
+    assert np.all(out["best_step"] == 300)
+    Emin, _, _ = O.bruteforce(p)
+    assert out["E_min"] >= Emin
+
+
+def test_dynamics_reach_ground_state_n20():
+    """Solution-quality sanity of the method as specified: on the n = 20 dense
+    integer workload some replica of a 2000-step run reaches the enumerated
+    ground state (an unpinned quality claim, recorded as such)."""
+    Q, c = I.dense_int_qubo(20, seed=0)
+    p = O.problem_from_dense(Q, c)
+    Emin, _, _ = O.bruteforce(p)
+    rho = O.spectral_radius(p)
+    S0, Y0 = O.init_state(20, 128, seed=0, sigma0=0.1)
+    out = O.bsb_run(p, 128, 2000, 0.5, 1.0, 2.0 / rho, [0, 1], 50, S0, Y0)
+    assert out["E_min"] == Emin
+
+
+# ---------------------------------------------------------------- spectral radius
+def test_spectral_radius_closed_forms():
+    """K_n with unit couplings: eigenvalues n-1 and -1 => rho = n-1; the
+    ferromagnetic periodic cubic lattice: rho = 6."""
+    n = 9
+    p = O.problem_from_dense(np.ones((n, n)) - np.eye(n) + np.diag(np.arange(n)))
+    assert O.spectral_radius(p) == pytest.approx(n - 1, rel=1e-12)
+    L = I.cubic_lattice_ising(4, seed=0)
+    p2 = O.problem_from_csr(L.n, L.rowptr, L.col, np.abs(L.val).astype(np.int64))
+    assert O.spectral_radius(p2) == pytest.approx(6.0, rel=1e-12)
+
+
+# ---------------------------------------------------------------- gradient
+@pytest.mark.parametrize("knots", [[0.0, 1.0], [0.0, 0.4, 0.7, 1.0]])
+def test_gradient_matches_central_differences(knots):
+    """Hand-written reverse mode vs central finite differences of the loss
+    (catches a dropped chain-rule term or a wrong mask)."""
+    L = I.cubic_lattice_ising(3, seed=2)
+    p = O.problem_from_csr(L.n, L.rowptr, L.col, L.val.astype(np.int64))
+    R, K, dt, a0, c0 = 4, 30, 0.35, 1.0, 0.2
+    S0, Y0 = O.init_state(p.n, R, seed=4, sigma0=0.2)
+    g = O.bsb_grad(p, R, K, dt, a0, c0, knots, S0, Y0)
+    run = O.bsb_run(p, R, K, dt, a0, c0, knots, 0, S0, Y0)
+    assert 0 < np.sum(np.abs(run["S"]) == 1.0) < run["S"].size   # some walls active, some free
+    assert g["loss"] == pytest.approx(O.bsb_loss(p, R, K, dt, a0, c0, knots, S0, Y0), rel=1e-14)
+    h = 1e-6
+
+    def fd(f):
+        return (f(+h) - f(-h)) / (2 * h)
+
+    d_dt = fd(lambda e: O.bsb_loss(p, R, K, dt + e, a0, c0, knots, S0, Y0))
+    d_c0 = fd(lambda e: O.bsb_loss(p, R, K, dt, a0, c0 + e, knots, S0, Y0))
+    assert g["d_dt"] == pytest.approx(d_dt, rel=1e-5, abs=1e-7)
+    assert g["d_c0"] == pytest.approx(d_c0, rel=1e-5, abs=1e-7)
+    for j in range(len(knots)):
+        kp = list(knots)
+        km = list(knots)
+        kp[j] += h
+        km[j] -= h
+        dj = (O.bsb_loss(p, R, K, dt, a0, c0, kp, S0, Y0) - O.bsb_loss(p, R, K, dt, a0, c0, km, S0, Y0)) / (2 * h)
+        assert g["d_knots"][j] == pytest.approx(dj, rel=1e-5, abs=1e-7)
