@@ -1,0 +1,238 @@
+/*
+ * veloxq.h -- C ABI of a GB300 (sm_103a) implementation of the data-parallel
+ * hot path of the physics-inspired QUBO solver benchmarked in
+ * "VeloxQ: A Fast and Efficient QUBO Solver" (arXiv:2501.19221).
+ *
+ * The problem (Sec. 2, eq. qubo_model; read as a sum over every stored entry):
+ *     minimise  E(x) = sum_{i,j} Q_ij x_i x_j + sum_i c_i x_i ,  x in {0,1}^n .
+ * Ising input (Sec. 2, eq. ising_model) H(s) = sum_{i<j} J_ij s_i s_j +
+ * sum_i h_i s_i is mapped to a QUBO by App. A (eq. qij_SK).
+ *
+ * The solver integrates R replicas of a ballistic simulated-bifurcation
+ * system (App. B, eqs. sbm2/sbm without the quartic term, with walls at
+ * |s| = 1) in lockstep. With Qs = (Q + Q^T)/2, Qoff its off-diagonal part and
+ * b = Qs 1 + c, one step k (of K) is
+ *     F   = Qoff s                       (local field, the dominant product)
+ *     phi = -(F + b)/2
+ *     y  <- y + dt (-(a0 - a_k) s + c0 phi)
+ *     s  <- s + dt a0 y ;   |s| > 1 => s = sign(s), y = 0
+ * and the readout is x = [s > 0] (App. B, s_i = sign(q_i)). The exact energy of
+ * the read-out vectors is kept as best-so-far per replica; the result is the
+ * lowest energy over replicas (lowest replica index on ties).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns a veloxq_status (0 = OK) and never aborts. On failure
+ *    veloxq_last_error() returns a thread-local message.
+ *  - Host pointers are owned by the caller and only read or written during
+ *    the call. Calls that take host pointers synchronise their stream before
+ *    returning.
+ *  - Entry points whose name ends in _dev take DEVICE pointers (for instance
+ *    from PyTorch tensors) owned by the caller; they are enqueued on the
+ *    context's stream and return without synchronising.
+ *  - State blocks (S, Y, F) are replica-major float32: element (r, i) of R
+ *    replicas of n variables is at r*n + i. Binary batches are uint8 [B][n]
+ *    with values 0/1.
+ *  - A context owns every device buffer it allocates; veloxq_destroy frees
+ *    them. A context is not thread-safe; different contexts are independent.
+ */
+#ifndef VELOXQ_H
+#define VELOXQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct veloxq_ctx veloxq_ctx; /* opaque, library-owned */
+
+typedef enum {
+    VELOXQ_OK = 0,
+    VELOXQ_EINVAL = -1,      /* invalid argument or input (message says which) */
+    VELOXQ_ENOMEM = -2,      /* device or host allocation failed */
+    VELOXQ_ECUDA = -3,       /* CUDA runtime error (no device, launch failure) */
+    VELOXQ_ETIMEDOUT = -4,   /* a bounded device-side wait gave up */
+    VELOXQ_EUNSUPPORTED = -5 /* valid request this build or device cannot run */
+} veloxq_status;
+
+/* Element type of a coupling array passed in. */
+typedef enum { VELOXQ_I8 = 0, VELOXQ_I32 = 1, VELOXQ_F32 = 2, VELOXQ_F64 = 3 } veloxq_vtype;
+
+/* Operand precision of the dense local-field product F = Qoff S. FP32 runs on
+ * the CUDA cores; BF16 and FP8 (E4M3 with one FP32 scale per row of Qoff and
+ * one per replica of S) run on the tcgen05 tensor cores; all accumulate in
+ * FP32. Sparse contexts always use FP32 (or exact int8 couplings). */
+typedef enum { VELOXQ_PREC_FP32 = 0, VELOXQ_PREC_BF16 = 1, VELOXQ_PREC_FP8 = 2 } veloxq_prec;
+
+/* Kernel path selection (VELOXQ_PATH_AUTO picks by size and format). */
+typedef enum {
+    VELOXQ_PATH_AUTO = 0,
+    VELOXQ_PATH_RESIDENT = 1,  /* sparse rows, whole run in one launch, state in shared memory */
+    VELOXQ_PATH_STREAM = 2,    /* sparse rows, one fused launch per step, state in HBM */
+    VELOXQ_PATH_DENSE = 3      /* dense Q, one fused field+update launch per step */
+} veloxq_path;
+
+/* Integration schedule. App. B fixes a0 = 1, c0 = 1/lambda_max(J) and a(t)
+ * increasing linearly through the bifurcation at a(t) ~ a0; the rest is not
+ * given by the paper and has the defaults below. The Ising coupling of the
+ * dynamics is J = -Qoff/2, so the default c0 is kappa / rho(J) with rho the
+ * spectral radius, computed by power iteration when the context is created. */
+typedef struct {
+    float dt;               /* step size; default 0.5 */
+    float a0;               /* default 1 */
+    float kappa;            /* c0 = kappa / rho(J) unless c0 > 0; default 1 */
+    float c0;               /* > 0 overrides kappa / rho(J); default 0 */
+    float sigma0;           /* initial s, y ~ U(-sigma0, sigma0); default 0.1 */
+    int32_t n_knots;        /* 0 => a(t) through {0, a0}, i.e. a_k = a0 k/(K-1) */
+    const float* a_knots;   /* host, n_knots values spread evenly over steps 0..K-1 */
+    int32_t readout_every;  /* read out every this many steps (and after the last); 0 => last only */
+    veloxq_prec prec;       /* dense field operand precision; default FP32 */
+    veloxq_path path;       /* default AUTO */
+} veloxq_schedule;
+
+/* Context facts computed at creation. */
+typedef struct {
+    int64_t n;              /* variables */
+    int64_t nnz_field;      /* stored off-diagonal entries of Qs (n*(n-1) for dense) */
+    int32_t is_dense;       /* 1 for dense contexts */
+    int32_t is_integer;     /* 1 when Q and c are integer-valued: energies are exact int64 */
+    double rho;             /* spectral radius of Qoff by power iteration */
+    double K0;              /* E(x) = s^T Qoff s / 4 + b^T s / 2 + K0 for s = 2x - 1 */
+    double ising_offset;    /* Ising contexts: H(s) = 2 E(x) + ising_offset; else 0 */
+} veloxq_info;
+
+/* Fill *s with the defaults listed above. */
+void veloxq_schedule_default(veloxq_schedule* s);
+
+/* ---------------------------------------------------------------------------
+ * Creation (Sec. 2 problem statement; inputs as biases and couplings in dense
+ * or sparse form, Sec. "Comparison of VeloxQ SDK and D-Wave Ocean SDK").
+ * ------------------------------------------------------------------------- */
+
+/* Dense QUBO. Q: host, n*n row-major of type vt, used as given (need not be
+ * symmetric); c: host, n doubles, or NULL for c = 0. stream: a cudaStream_t to
+ * run on, or NULL for the default stream. Q and c are copied to the device,
+ * Qs/Qoff/b/K0 are formed there, and rho is computed by power iteration.
+ * Errors: EINVAL for n < 1, NULL Q, non-finite values or n > 2^20; ENOMEM. */
+int veloxq_create_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, const void* Q,
+                        const double* c, void* stream);
+
+/* Sparse QUBO in CSR form. rowptr: host, n+1 int64 (rowptr[0] = 0,
+ * non-decreasing); col: host, rowptr[n] int32 in [0, n), strictly increasing
+ * within a row; val: host, rowptr[n] values of type vt. Diagonal entries are
+ * linear terms. The sparsity pattern must be structurally symmetric (values
+ * may differ: the dynamics use (Q + Q^T)/2, the energy uses Q as given).
+ * Errors: EINVAL for a malformed CSR or non-finite values; EUNSUPPORTED for a
+ * structurally non-symmetric pattern; ENOMEM. */
+int veloxq_create_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, const int32_t* col,
+                      veloxq_vtype vt, const void* val, const double* c, void* stream);
+
+/* Dense Ising model (Sec. 2, eq. ising_model): J host n*n row-major of type
+ * vt, read from its strict upper triangle; h host n doubles or NULL. Mapped to
+ * the QUBO of App. A (eq. qij_SK) on the device: Q_ij = J_ij (i != j),
+ * Q_ii = h_i - sum_l J_il, with H(s) = 2 E(x) + ising_offset,
+ * ising_offset = sum_{i<j} J_ij - sum_i h_i. Errors as veloxq_create_dense. */
+int veloxq_create_ising_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, const void* J,
+                              const double* h, void* stream);
+
+/* Sparse Ising model in CSR form (structurally symmetric pattern, no diagonal
+ * entries; the coupling of a pair is the value stored at its (i<j) position).
+ * Mapped to a QUBO as veloxq_create_ising_dense. Errors as veloxq_create_csr,
+ * plus EINVAL for a stored diagonal entry. */
+int veloxq_create_ising_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, const int32_t* col,
+                            veloxq_vtype vt, const void* J, const double* h, void* stream);
+
+/* Release every device and host resource of ctx (NULL is a no-op). */
+void veloxq_destroy(veloxq_ctx* ctx);
+
+/* Thread-local message describing the last non-OK status of this thread. */
+const char* veloxq_last_error(void);
+
+/* Context facts (host struct written). */
+int veloxq_get_info(veloxq_ctx* ctx, veloxq_info* info);
+
+/* Change the stream later calls run on (a cudaStream_t, or NULL). */
+int veloxq_set_stream(veloxq_ctx* ctx, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Solve (App. B dynamics, replicas evolved in parallel and the best kept;
+ * the returned state comes with its energy, Sec. "Structure-exploiting
+ * solvers"; the per-replica energies are the low-energy spectrum of
+ * Sec. "Pegasus topology").
+ * ------------------------------------------------------------------------- */
+
+/* Run `replicas` replicas for `steps` steps from a Philox4x32-10 initial state
+ * keyed by seed (counter (i_lo, i_hi, r, 0); word 0 -> s, word 1 -> y).
+ * sched: NULL for defaults. Outputs (host; any may be NULL):
+ *   x_best        n bytes 0/1, the best vector (lowest energy, lowest replica);
+ *   E_best        its energy as a double;
+ *   E_best_int    its exact int64 energy (integer contexts only, else untouched);
+ *   E_per_replica `replicas` doubles, each replica's best energy.
+ * Errors: EINVAL (replicas < 1, steps < 1, bad schedule), EUNSUPPORTED (path
+ * or precision not available for this context), ENOMEM, ECUDA. */
+int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched,
+                 uint64_t seed, uint8_t* x_best, double* E_best, int64_t* E_best_int,
+                 double* E_per_replica);
+
+/* Solve several independent contexts (for instance a batch of instances of
+ * uneven size) with the same replicas, steps, schedule and seed. x_best[m] is
+ * a host buffer of n_m bytes (or NULL), E_best[m] the best energy. Errors as
+ * veloxq_solve; m-th failure reported with its index. */
+int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas, int32_t steps,
+                       const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best,
+                       double* E_best);
+
+/* ---------------------------------------------------------------------------
+ * Energies (Sec. 2, eq. qubo_model)
+ * ------------------------------------------------------------------------- */
+
+/* E(x) for a host batch X [batch][n] of 0/1 bytes. E: host, batch doubles (or
+ * NULL); E_int: host, batch int64 (integer contexts only, else must be NULL).
+ * Errors: EINVAL (batch < 0, NULL X with batch > 0, E_int on a real context). */
+int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
+
+/* As veloxq_energy with device pointers; asynchronous on the context stream. */
+int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
+
+/* ---------------------------------------------------------------------------
+ * Pieces of the step, for parity tests and for callers that drive the
+ * integration themselves (device pointers, asynchronous).
+ * ------------------------------------------------------------------------- */
+
+/* Philox initial state S, Y [R][n] for seed and sigma0 (same draw as solve). */
+int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, float* S, float* Y);
+
+/* Local field F = Qoff S for S [R][n] in the given operand precision (FP8 also
+ * quantises S with one scale per replica). Errors: EUNSUPPORTED for BF16/FP8
+ * on a sparse context. */
+int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F);
+
+/* Advance S, Y [R][n] in place by steps k_begin .. k_begin+k_count-1 of a
+ * K-step schedule, on the kernel path the schedule selects (the same kernels
+ * veloxq_solve runs). If F_last is not NULL it receives the field used in the
+ * last step. Errors: EINVAL for k_begin < 0 or k_begin + k_count > K. */
+int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_count, int32_t K,
+                     const veloxq_schedule* sched, float* S, float* Y, float* F_last);
+
+/* Spectral radius of Qoff as used for the default c0 (power iteration). */
+int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho);
+
+/* ---------------------------------------------------------------------------
+ * Differentiation of the unrolled integrator (adjoint of the step).
+ * ------------------------------------------------------------------------- */
+
+/* Loss L = mean_r E_relax(s_K,r) with E_relax(s) = s^T Qoff s/4 + b^T s/2 + K0
+ * (the QUBO energy identity under x = (1+s)/2, evaluated at continuous s),
+ * after `steps` steps from the Philox state of seed. Returns L and its
+ * gradient w.r.t. dt, kappa (c0 = kappa/rho(J); w.r.t. c0 itself when
+ * sched->c0 > 0) and the a(t) knots (n_knots values, or the 2 default knots).
+ * Forward states are checkpointed every ckpt_every steps and each segment is
+ * recomputed in the reverse sweep. Host outputs; any may be NULL. */
+int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched,
+                uint64_t seed, int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa,
+                double* d_knots);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VELOXQ_H */

@@ -70,6 +70,7 @@ def _load():
                                                i32, P, P, P, P, P, P, P]),
             "oracle_bsb_loss": (ctypes.c_int, [i64, i64, P, P, P, P, i32, i32, f64, f64, f64,
                                                i32, P, P, P, P]),
+            "oracle_ising_pairs_to_qubo": (None, [i64, i64, P, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -219,6 +220,34 @@ def ising_to_qubo(J: np.ndarray, h: np.ndarray):
     C = ctypes.c_double(0.0)
     lib.oracle_ising_to_qubo(n, _p(J), _p(h), _p(Q), ctypes.byref(C))
     return Q, C.value
+
+
+def ising_csr_to_qubo(n, rowptr, col, J, h=None):
+    """App. A Ising -> QUBO for a sparse Ising model given in CSR; the pair
+    (i < j) takes the value stored at its upper-triangle position. Returns
+    (Problem, C) with H(s) = 2 E(x) + C. Integer J and h give an integer Problem."""
+    lib = _load()
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    rows = np.repeat(np.arange(n, dtype=np.int64), np.diff(rowptr))
+    col = np.asarray(col, dtype=np.int64)
+    upper = col > rows                      # select the (i < j) entries: no arithmetic
+    pi = np.ascontiguousarray(rows[upper])
+    pj = np.ascontiguousarray(col[upper])
+    Jv = np.asarray(J)
+    pv = np.ascontiguousarray(Jv[upper], dtype=np.float64)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    m = pi.shape[0]
+    er = np.zeros(2 * m + n, dtype=np.int64)
+    ec = np.zeros(2 * m + n, dtype=np.int64)
+    ev = np.zeros(2 * m + n, dtype=np.float64)
+    C = ctypes.c_double(0.0)
+    lib.oracle_ising_pairs_to_qubo(n, m, _p(pi), _p(pj), _p(pv), _p(hh), _p(er), _p(ec), _p(ev), ctypes.byref(C))
+    integer = np.issubdtype(Jv.dtype, np.integer) and (hh is None or np.all(hh == np.round(hh)))
+    p = Problem(n, er, ec, ev, np.zeros(n))
+    if integer:
+        p.ev_i64 = np.ascontiguousarray(np.round(ev).astype(np.int64))
+        p.c_i64 = np.zeros(n, dtype=np.int64)
+    return p, C.value
 
 
 def qubo_to_ising(Q: np.ndarray):

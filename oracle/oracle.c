@@ -521,3 +521,27 @@ int oracle_bsb_loss(int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec
     free(S); free(Y); free(F); free(b); free(a); free(E);
     return 0;
 }
+
+/* Sparse Ising -> QUBO (App. A, eq. qij_SK) from the coupled pairs (i < j):
+ * Q_ij = Q_ji = J_ij and Q_ii = h_i - sum_l J_il, written as a coordinate list
+ * of 2*npairs + n entries (pairs first, then the diagonal); C receives
+ * sum_{i<j} J_ij - sum_i h_i so that H(s) = 2 Q(x) + C. */
+void oracle_ising_pairs_to_qubo(int64_t n, int64_t npairs, const int64_t* pi, const int64_t* pj, const double* pv,
+                                const double* h, int64_t* er, int64_t* ec, double* ev, double* C)
+{
+    double sumJ = 0.0, sumh = 0.0;
+    for (int64_t i = 0; i < n; ++i) {
+        er[2 * npairs + i] = i;
+        ec[2 * npairs + i] = i;
+        ev[2 * npairs + i] = h ? h[i] : 0.0;
+        if (h) sumh += h[i];
+    }
+    for (int64_t e = 0; e < npairs; ++e) {
+        er[2 * e] = pi[e]; ec[2 * e] = pj[e]; ev[2 * e] = pv[e];
+        er[2 * e + 1] = pj[e]; ec[2 * e + 1] = pi[e]; ev[2 * e + 1] = pv[e];
+        ev[2 * npairs + pi[e]] -= pv[e];
+        ev[2 * npairs + pj[e]] -= pv[e];
+        sumJ += pv[e];
+    }
+    *C = sumJ - sumh;
+}

@@ -1,0 +1,535 @@
+// vq_api.cu -- the C ABI declared in include/veloxq.h: argument checks,
+// context lifetime, path selection, the solve driver (CUDA-graph captured
+// step loops or a single resident launch) and host <-> device marshalling.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace {
+thread_local std::string g_err;
+}
+
+void set_error(const std::string& msg) { g_err = msg; }
+
+int fail(int status, const std::string& msg) {
+    g_err = msg;
+    return status;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) return VELOXQ_ENOMEM;
+    return VELOXQ_ECUDA;
+}
+
+int DevBuf::ensure(size_t b) {
+    if (b <= bytes && p) return VELOXQ_OK;
+    release();
+    if (b == 0) b = 16;
+    cudaError_t e = cudaMalloc(&p, b);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        bytes = 0;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? VELOXQ_ENOMEM : VELOXQ_ECUDA,
+                    std::string("device allocation of ") + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    bytes = b;
+    return VELOXQ_OK;
+}
+
+// extra per-context state kept out of the public struct definition
+struct CtxExtra {
+    cudaStream_t work = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<uint64_t> graph_key;
+    cudaGraphExec_t graph = nullptr;
+    ~CtxExtra() {
+        if (graph) cudaGraphExecDestroy(graph);
+        if (ev) cudaEventDestroy(ev);
+        if (work) cudaStreamDestroy(work);
+    }
+};
+
+std::map<const veloxq_ctx*, std::unique_ptr<CtxExtra>>& extras() {
+    static std::map<const veloxq_ctx*, std::unique_ptr<CtxExtra>> m;
+    return m;
+}
+
+CtxExtra* extra(const veloxq_ctx* ctx) {
+    auto it = extras().find(ctx);
+    return it == extras().end() ? nullptr : it->second.get();
+}
+
+int resolve(const veloxq_ctx* ctx, const veloxq_schedule* s_in, int32_t K, RunParams* p) {
+    veloxq_schedule s;
+    veloxq_schedule_default(&s);
+    if (s_in) s = *s_in;
+    if (!(std::isfinite(s.dt) && s.dt > 0)) return fail(VELOXQ_EINVAL, "schedule dt must be finite and > 0");
+    if (!(std::isfinite(s.a0) && s.a0 > 0)) return fail(VELOXQ_EINVAL, "schedule a0 must be finite and > 0");
+    if (!std::isfinite(s.kappa)) return fail(VELOXQ_EINVAL, "schedule kappa must be finite");
+    if (!(std::isfinite(s.c0) && s.c0 >= 0)) return fail(VELOXQ_EINVAL, "schedule c0 must be finite and >= 0");
+    if (!(std::isfinite(s.sigma0) && s.sigma0 >= 0)) return fail(VELOXQ_EINVAL, "schedule sigma0 must be finite and >= 0");
+    if (s.n_knots < 0 || (s.n_knots > 0 && !s.a_knots)) return fail(VELOXQ_EINVAL, "schedule knots: n_knots < 0 or a_knots NULL");
+    if (s.readout_every < 0) return fail(VELOXQ_EINVAL, "schedule readout_every must be >= 0");
+    if (s.prec < VELOXQ_PREC_FP32 || s.prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
+    if (s.path < VELOXQ_PATH_AUTO || s.path > VELOXQ_PATH_DENSE) return fail(VELOXQ_EINVAL, "unknown path");
+    p->dt = s.dt;
+    p->a0 = s.a0;
+    p->sigma0 = s.sigma0;
+    // J = -Qoff/2 => rho(J) = rho(Qoff)/2 and c0 = kappa / rho(J)
+    p->c0 = s.c0 > 0 ? s.c0 : (ctx->rho > 1e-12 ? (float)(2.0 * s.kappa / ctx->rho) : s.kappa);
+    p->K = K;
+    p->readout_every = s.readout_every;
+    p->prec = s.prec;
+    p->path = s.path;
+    p->knots.clear();
+    if (s.n_knots > 0) {
+        for (int j = 0; j < s.n_knots; ++j) {
+            if (!std::isfinite(s.a_knots[j])) return fail(VELOXQ_EINVAL, "schedule knot is not finite");
+            p->knots.push_back(s.a_knots[j]);
+        }
+    } else {
+        p->knots = {0.0, (double)s.a0};
+    }
+    return VELOXQ_OK;
+}
+
+// a_k, k = 0..K-1: piecewise linear through evenly spread knots
+std::vector<float> schedule_table(const RunParams& p) {
+    std::vector<float> a((size_t)p.K);
+    const int nk = (int)p.knots.size();
+    for (int k = 0; k < p.K; ++k) {
+        if (p.K == 1 || nk == 1) { a[k] = (float)p.knots[0]; continue; }
+        const double t = (double)k * (double)(nk - 1) / (double)(p.K - 1);
+        int j = (int)std::floor(t);
+        if (j > nk - 2) j = nk - 2;
+        const double w = t - (double)j;
+        a[k] = (float)(p.knots[j] * (1.0 - w) + p.knots[j + 1] * w);
+    }
+    return a;
+}
+
+int upload_schedule(veloxq_ctx* ctx, const RunParams& p) {
+    std::vector<float> a = schedule_table(p);
+    VQ_TRY(ctx->a_table.ensure(sizeof(float) * a.size()));
+    VQ_CUDA(cudaMemcpyAsync(ctx->a_table.p, a.data(), sizeof(float) * a.size(), cudaMemcpyHostToDevice, ctx->stream));
+    // the host vector dies at return: make the copy complete first
+    VQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return VELOXQ_OK;
+}
+
+veloxq_path choose_path(const veloxq_ctx* ctx, veloxq_path want, int32_t R) {
+    if (ctx->dense) return VELOXQ_PATH_DENSE;
+    if (want == VELOXQ_PATH_STREAM || want == VELOXQ_PATH_RESIDENT) return want;
+    return resident_fits(ctx, R, nullptr, nullptr, nullptr) ? VELOXQ_PATH_RESIDENT : VELOXQ_PATH_STREAM;
+}
+
+int check_path(const veloxq_ctx* ctx, veloxq_path path, veloxq_prec prec, int32_t R) {
+    if (path == VELOXQ_PATH_DENSE && !ctx->dense) return fail(VELOXQ_EUNSUPPORTED, "dense path requested for a sparse context");
+    if (ctx->dense && path != VELOXQ_PATH_DENSE && path != VELOXQ_PATH_AUTO)
+        return fail(VELOXQ_EUNSUPPORTED, "sparse path requested for a dense context");
+    if (path == VELOXQ_PATH_RESIDENT && !resident_fits(ctx, R, nullptr, nullptr, nullptr))
+        return fail(VELOXQ_EUNSUPPORTED, "instance does not fit the resident kernel");
+    if (prec != VELOXQ_PREC_FP32)
+        return fail(VELOXQ_EUNSUPPORTED, ctx->dense ? "BF16/FP8 dense field is not available in this build"
+                                                    : "sparse contexts run the field in FP32 (or exact int8)");
+    return VELOXQ_OK;
+}
+
+bool is_readout(const RunParams& p, int k) {
+    return (k == p.K - 1) || (p.readout_every > 0 && ((k + 1) % p.readout_every) == 0);
+}
+
+// Enqueue the step loop (steps, readouts, argmin) on ctx->stream.
+int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts) {
+    const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
+    float* cur = ctx->s_a.as<float>();
+    float* nxt = ctx->s_b.as<float>();
+    float* Y = ctx->y.as<float>();
+    const float* at = ctx->a_table.as<float>();
+    int np = nparts;
+    for (int k = 0; k < p.K; ++k) {
+        if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+        else VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+        std::swap(cur, nxt);
+        if (!is_readout(p, k)) continue;
+        int64_t* parts = ctx->ework.as<int64_t>();
+        if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_energy(ctx, R, cur, parts, &np));
+        else VQ_TRY(stream_energy(ctx, R, cur, parts, &np));
+        VQ_TRY(launch_best_update(ctx, R, np, parts, ctx->best_e.as<int64_t>(), ctx->flags.as<uint8_t>()));
+        VQ_TRY(launch_best_bits(ctx, R, lay, cur, ctx->flags.as<uint8_t>(), ctx->best_bits.as<uint32_t>()));
+    }
+    VQ_TRY(launch_argmin_unpack(ctx, R, ctx->best_e.as<int64_t>(), ctx->best_bits.as<uint32_t>(),
+                                ctx->misc.as<int64_t>(), ctx->xout.as<uint8_t>()));
+    return VELOXQ_OK;
+}
+
+int stream_energy_parts_count(veloxq_ctx* ctx, veloxq_path path, int32_t R);
+
+}  // namespace vq
+
+// ---- forward declaration from vq_stream.cu
+namespace vq {
+int stream_energy_parts(int32_t R);
+int stream_energy_parts_count(veloxq_ctx* ctx, veloxq_path path, int32_t R) {
+    return path == VELOXQ_PATH_DENSE ? (int)div_up(ctx->n, 64) : stream_energy_parts(R);
+}
+}  // namespace vq
+
+using namespace vq;
+
+extern "C" {
+
+void veloxq_schedule_default(veloxq_schedule* s) {
+    if (!s) return;
+    s->dt = 0.5f;
+    s->a0 = 1.0f;
+    s->kappa = 1.0f;
+    s->c0 = 0.0f;
+    s->sigma0 = 0.1f;
+    s->n_knots = 0;
+    s->a_knots = nullptr;
+    s->readout_every = 50;
+    s->prec = VELOXQ_PREC_FP32;
+    s->path = VELOXQ_PATH_AUTO;
+}
+
+const char* veloxq_last_error(void) { return g_err.c_str(); }
+
+static int new_ctx(veloxq_ctx** out, int64_t n, void* stream, veloxq_ctx** made) {
+    if (!out) return fail(VELOXQ_EINVAL, "out must not be NULL");
+    *out = nullptr;
+    if (n < 1) return fail(VELOXQ_EINVAL, "n must be >= 1");
+    if (n > ((int64_t)1 << 31) - 2) return fail(VELOXQ_EINVAL, "n must be < 2^31 - 1");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice (no CUDA device?)");
+    veloxq_ctx* ctx = new (std::nothrow) veloxq_ctx();
+    if (!ctx) return fail(VELOXQ_ENOMEM, "host allocation failed");
+    ctx->device = dev;
+    ctx->stream = (cudaStream_t)stream;
+    ctx->n = n;
+    auto ex = std::make_unique<CtxExtra>();
+    e = cudaStreamCreateWithFlags(&ex->work, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ex->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        delete ctx;
+        return cuda_fail(e, "stream creation");
+    }
+    extras()[ctx] = std::move(ex);
+    *made = ctx;
+    return VELOXQ_OK;
+}
+
+static int finish_ctx(veloxq_ctx* ctx, int st, veloxq_ctx** out) {
+    if (st == VELOXQ_OK) st = power_iteration(ctx, 300, &ctx->rho);
+    if (st != VELOXQ_OK) {
+        std::string keep = g_err;
+        veloxq_destroy(ctx);
+        g_err = keep;
+        return st;
+    }
+    *out = ctx;
+    return VELOXQ_OK;
+}
+
+int veloxq_create_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, const void* Q, const double* c, void* stream) {
+    if (!Q) return fail(VELOXQ_EINVAL, "Q must not be NULL");
+    if (n > (1 << 20)) return fail(VELOXQ_EINVAL, "dense n must be <= 2^20");
+    veloxq_ctx* ctx = nullptr;
+    VQ_TRY(new_ctx(out, n, stream, &ctx));
+    return finish_ctx(ctx, ingest_dense(ctx, vt, Q, c, false), out);
+}
+
+int veloxq_create_ising_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, const void* J, const double* h, void* stream) {
+    if (!J) return fail(VELOXQ_EINVAL, "J must not be NULL");
+    if (n > (1 << 20)) return fail(VELOXQ_EINVAL, "dense n must be <= 2^20");
+    veloxq_ctx* ctx = nullptr;
+    VQ_TRY(new_ctx(out, n, stream, &ctx));
+    return finish_ctx(ctx, ingest_dense(ctx, vt, J, h, true), out);
+}
+
+int veloxq_create_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, const int32_t* col, veloxq_vtype vt,
+                      const void* val, const double* c, void* stream) {
+    if (!rowptr) return fail(VELOXQ_EINVAL, "rowptr must not be NULL");
+    veloxq_ctx* ctx = nullptr;
+    VQ_TRY(new_ctx(out, n, stream, &ctx));
+    return finish_ctx(ctx, ingest_csr(ctx, rowptr, col, vt, val, c, false), out);
+}
+
+int veloxq_create_ising_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, const int32_t* col, veloxq_vtype vt,
+                            const void* J, const double* h, void* stream) {
+    if (!rowptr) return fail(VELOXQ_EINVAL, "rowptr must not be NULL");
+    veloxq_ctx* ctx = nullptr;
+    VQ_TRY(new_ctx(out, n, stream, &ctx));
+    return finish_ctx(ctx, ingest_csr(ctx, rowptr, col, vt, J, h, true), out);
+}
+
+void veloxq_destroy(veloxq_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    extras().erase(ctx);
+    delete ctx;
+}
+
+int veloxq_get_info(veloxq_ctx* ctx, veloxq_info* info) {
+    if (!ctx || !info) return fail(VELOXQ_EINVAL, "ctx and info must not be NULL");
+    info->n = ctx->n;
+    info->nnz_field = ctx->nnz;
+    info->is_dense = ctx->dense ? 1 : 0;
+    info->is_integer = ctx->integer ? 1 : 0;
+    info->rho = ctx->rho;
+    info->K0 = ctx->K0;
+    info->ising_offset = ctx->ising_offset;
+    return VELOXQ_OK;
+}
+
+int veloxq_set_stream(veloxq_ctx* ctx, void* stream) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    ctx->stream = (cudaStream_t)stream;
+    return VELOXQ_OK;
+}
+
+int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho) {
+    if (!ctx || !rho) return fail(VELOXQ_EINVAL, "ctx and rho must not be NULL");
+    *rho = ctx->rho;
+    return VELOXQ_OK;
+}
+
+int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
+                 uint8_t* x_best, double* E_best, int64_t* E_best_int, double* E_per_replica) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (replicas < 1) return fail(VELOXQ_EINVAL, "replicas must be >= 1");
+    if (steps < 1) return fail(VELOXQ_EINVAL, "steps must be >= 1");
+    if (E_best_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_best_int requires an integer-valued context");
+    RunParams p;
+    VQ_TRY(resolve(ctx, sched, steps, &p));
+    const veloxq_path path = choose_path(ctx, p.path, replicas);
+    VQ_TRY(check_path(ctx, path, p.prec, replicas));
+    CtxExtra* ex = extra(ctx);
+    const int64_t n = ctx->n, R = replicas, nw = div_up(n, 32);
+    // run on the context's private stream, ordered after the caller's stream
+    cudaStream_t user = ctx->stream;
+    VQ_CUDA(cudaEventRecord(ex->ev, user));
+    VQ_CUDA(cudaStreamWaitEvent(ex->work, ex->ev, 0));
+    ctx->stream = ex->work;
+    struct Restore {
+        veloxq_ctx* c;
+        cudaStream_t s;
+        ~Restore() { c->stream = s; }
+    } restore{ctx, user};
+
+    VQ_TRY(upload_schedule(ctx, p));
+    VQ_TRY(ctx->best_e.ensure(sizeof(int64_t) * R));
+    VQ_TRY(ctx->best_bits.ensure(sizeof(uint32_t) * R * nw));
+    VQ_TRY(ctx->misc.ensure(sizeof(int64_t) * 16));
+    VQ_TRY(ctx->xout.ensure((size_t)n));
+    if (path == VELOXQ_PATH_RESIDENT) {
+        VQ_TRY(resident_run(ctx, replicas, p, seed, 0, steps, nullptr, nullptr, nullptr, nullptr, nullptr,
+                            ctx->best_e.as<int64_t>(), ctx->best_bits.as<uint32_t>()));
+        VQ_TRY(launch_argmin_unpack(ctx, replicas, ctx->best_e.as<int64_t>(), ctx->best_bits.as<uint32_t>(),
+                                    ctx->misc.as<int64_t>(), ctx->xout.as<uint8_t>()));
+    } else {
+        const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
+        const int nparts = stream_energy_parts_count(ctx, path, replicas);
+        VQ_TRY(ctx->s_a.ensure(sizeof(float) * n * R));
+        VQ_TRY(ctx->s_b.ensure(sizeof(float) * n * R));
+        VQ_TRY(ctx->y.ensure(sizeof(float) * n * R));
+        VQ_TRY(ctx->ework.ensure(sizeof(int64_t) * (size_t)nparts * R));
+        VQ_TRY(ctx->flags.ensure((size_t)R));
+        VQ_TRY(launch_init_state(ctx, replicas, seed, p.sigma0, lay, ctx->s_a.as<float>(), ctx->y.as<float>()));
+        VQ_CUDA(cudaMemsetAsync(ctx->best_e.p, 0x7f, sizeof(int64_t) * R, ctx->stream));
+        VQ_CUDA(cudaMemsetAsync(ctx->best_bits.p, 0, sizeof(uint32_t) * R * nw, ctx->stream));
+        // the captured loop depends on every pointer and parameter below
+        std::vector<uint64_t> key = {(uint64_t)path, (uint64_t)R, (uint64_t)steps, (uint64_t)p.readout_every,
+                                     (uint64_t)(uintptr_t)ctx->s_a.p, (uint64_t)(uintptr_t)ctx->s_b.p,
+                                     (uint64_t)(uintptr_t)ctx->y.p, (uint64_t)(uintptr_t)ctx->ework.p,
+                                     (uint64_t)(uintptr_t)ctx->best_e.p, (uint64_t)(uintptr_t)ctx->best_bits.p,
+                                     (uint64_t)(uintptr_t)ctx->flags.p, (uint64_t)(uintptr_t)ctx->misc.p,
+                                     (uint64_t)(uintptr_t)ctx->xout.p, (uint64_t)(uintptr_t)ctx->a_table.p};
+        float fp[3] = {p.dt, p.a0, p.c0};
+        for (float f : fp) {
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            key.push_back(u);
+        }
+        if (!ex->graph || ex->graph_key != key) {
+            if (ex->graph) {
+                cudaGraphExecDestroy(ex->graph);
+                ex->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            VQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+            int st = enqueue_loop(ctx, path, replicas, p, nparts);
+            cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
+            if (st != VELOXQ_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
+            ce = cudaGraphInstantiate(&ex->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (ce != cudaSuccess) {
+                ex->graph = nullptr;
+                return cuda_fail(ce, "graph instantiate");
+            }
+            ex->graph_key = key;
+        }
+        VQ_CUDA(cudaGraphLaunch(ex->graph, ctx->stream));
+    }
+    std::vector<int64_t> be((size_t)R);
+    int64_t misc[2] = {0, 0};
+    VQ_CUDA(cudaMemcpyAsync(be.data(), ctx->best_e.p, sizeof(int64_t) * R, cudaMemcpyDeviceToHost, ctx->stream));
+    VQ_CUDA(cudaMemcpyAsync(misc, ctx->misc.p, sizeof(misc), cudaMemcpyDeviceToHost, ctx->stream));
+    if (x_best) VQ_CUDA(cudaMemcpyAsync(x_best, ctx->xout.p, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+    VQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    VQ_LAUNCH_CHECK("solve");
+    const int sh = ctx->energy_shift;
+    if (E_best) *E_best = std::ldexp((double)misc[1], -sh);
+    if (E_best_int) *E_best_int = misc[1] >> sh;
+    if (E_per_replica)
+        for (int64_t r = 0; r < R; ++r) E_per_replica[r] = std::ldexp((double)be[r], -sh);
+    return VELOXQ_OK;
+}
+
+int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas, int32_t steps,
+                       const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best, double* E_best) {
+    if (count < 0 || (count > 0 && !ctxs)) return fail(VELOXQ_EINVAL, "ctxs must hold count contexts");
+    for (int32_t m = 0; m < count; ++m) {
+        int st = veloxq_solve(ctxs[m], replicas, steps, sched, seed, x_best ? x_best[m] : nullptr,
+                              E_best ? E_best + m : nullptr, nullptr, nullptr);
+        if (st != VELOXQ_OK) return fail(st, "instance " + std::to_string(m) + ": " + g_err);
+    }
+    return VELOXQ_OK;
+}
+
+static int energy_impl(veloxq_ctx* ctx, int64_t B, const uint8_t* Xd, double* Ed, int64_t* Eid) {
+    int64_t* parts;
+    int np = 0;
+    const int64_t chunk = 65535;
+    for (int64_t b0 = 0; b0 < B; b0 += chunk) {
+        const int64_t nb = std::min(chunk, B - b0);
+        const int npmax = ctx->dense ? (int)div_up(ctx->n, 64) : 64;
+        VQ_TRY(ctx->ework.ensure(sizeof(int64_t) * (size_t)npmax * nb));
+        parts = ctx->ework.as<int64_t>();
+        if (ctx->dense) VQ_TRY(dense_energy_x(ctx, nb, Xd + b0 * ctx->n, parts, &np));
+        else VQ_TRY(sparse_energy_x(ctx, nb, Xd + b0 * ctx->n, parts, &np));
+        VQ_TRY(launch_sum_parts(ctx, nb, np, parts, Ed ? Ed + b0 : nullptr, Eid ? Eid + b0 : nullptr));
+    }
+    return VELOXQ_OK;
+}
+
+int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (batch < 0) return fail(VELOXQ_EINVAL, "batch must be >= 0");
+    if (batch > 0 && !X) return fail(VELOXQ_EINVAL, "X must not be NULL");
+    if (E_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_int requires an integer-valued context");
+    return energy_impl(ctx, batch, X, E, E_int);
+}
+
+int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (batch < 0) return fail(VELOXQ_EINVAL, "batch must be >= 0");
+    if (batch > 0 && !X) return fail(VELOXQ_EINVAL, "X must not be NULL");
+    if (E_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_int requires an integer-valued context");
+    if (batch == 0) return VELOXQ_OK;
+    DevBuf xd, ed, eid;
+    VQ_TRY(xd.ensure((size_t)(batch * ctx->n)));
+    VQ_TRY(ed.ensure(sizeof(double) * batch));
+    if (E_int) VQ_TRY(eid.ensure(sizeof(int64_t) * batch));
+    VQ_CUDA(cudaMemcpyAsync(xd.p, X, (size_t)(batch * ctx->n), cudaMemcpyHostToDevice, ctx->stream));
+    VQ_TRY(energy_impl(ctx, batch, xd.as<uint8_t>(), ed.as<double>(), E_int ? eid.as<int64_t>() : nullptr));
+    if (E) VQ_CUDA(cudaMemcpyAsync(E, ed.p, sizeof(double) * batch, cudaMemcpyDeviceToHost, ctx->stream));
+    if (E_int) VQ_CUDA(cudaMemcpyAsync(E_int, eid.p, sizeof(int64_t) * batch, cudaMemcpyDeviceToHost, ctx->stream));
+    VQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return VELOXQ_OK;
+}
+
+int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, float* S, float* Y) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (R < 1 || !S || !Y) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, Y required");
+    if (!(std::isfinite(sigma0) && sigma0 >= 0)) return fail(VELOXQ_EINVAL, "sigma0 must be finite and >= 0");
+    return launch_init_state(ctx, R, seed, sigma0, LAYOUT_RN, S, Y);
+}
+
+int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (R < 1 || !S || !F) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, F required");
+    if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
+    if (ctx->dense) {
+        if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "BF16/FP8 dense field is not available in this build");
+        return dense_field(ctx, R, S, F);
+    }
+    if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "sparse contexts run the field in FP32 (or exact int8)");
+    const int64_t nR = ctx->n * (int64_t)R;
+    VQ_TRY(ctx->s_a.ensure(sizeof(float) * nR));
+    VQ_TRY(ctx->f.ensure(sizeof(float) * nR));
+    VQ_TRY(launch_transpose(ctx->stream, S, ctx->s_a.as<float>(), R, ctx->n));
+    VQ_TRY(stream_field(ctx, R, ctx->s_a.as<float>(), ctx->f.as<float>()));
+    return launch_transpose(ctx->stream, ctx->f.as<float>(), F, ctx->n, R);
+}
+
+int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_count, int32_t K,
+                     const veloxq_schedule* sched, float* S, float* Y, float* F_last) {
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    if (R < 1 || !S || !Y) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, Y required");
+    if (K < 1 || k_begin < 0 || k_count < 0 || (int64_t)k_begin + k_count > K)
+        return fail(VELOXQ_EINVAL, "need 0 <= k_begin, 0 <= k_count, k_begin + k_count <= K");
+    if (k_count == 0) return VELOXQ_OK;
+    RunParams p;
+    VQ_TRY(resolve(ctx, sched, K, &p));
+    const veloxq_path path = choose_path(ctx, p.path, R);
+    VQ_TRY(check_path(ctx, path, p.prec, R));
+    VQ_TRY(upload_schedule(ctx, p));
+    const int64_t n = ctx->n, nR = n * (int64_t)R;
+    const int k_end = k_begin + k_count;
+    if (path == VELOXQ_PATH_RESIDENT)
+        return resident_run(ctx, R, p, 0, k_begin, k_end, S, Y, S, Y, F_last, nullptr, nullptr);
+    VQ_TRY(ctx->s_a.ensure(sizeof(float) * nR));
+    VQ_TRY(ctx->s_b.ensure(sizeof(float) * nR));
+    const float* at = ctx->a_table.as<float>();
+    float* cur = ctx->s_a.as<float>();
+    float* nxt = ctx->s_b.as<float>();
+    if (path == VELOXQ_PATH_DENSE) {
+        VQ_CUDA(cudaMemcpyAsync(cur, S, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
+        for (int k = k_begin; k < k_end; ++k) {
+            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, k == k_end - 1 ? F_last : nullptr));
+            std::swap(cur, nxt);
+        }
+        VQ_CUDA(cudaMemcpyAsync(S, cur, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
+        return VELOXQ_OK;
+    }
+    VQ_TRY(ctx->y.ensure(sizeof(float) * nR));
+    VQ_TRY(ctx->f.ensure(sizeof(float) * nR));
+    VQ_TRY(launch_transpose(ctx->stream, S, cur, R, n));
+    VQ_TRY(launch_transpose(ctx->stream, Y, ctx->y.as<float>(), R, n));
+    for (int k = k_begin; k < k_end; ++k) {
+        VQ_TRY(stream_step(ctx, R, cur, nxt, ctx->y.as<float>(), at, k, p.dt, p.a0, p.c0,
+                           k == k_end - 1 && F_last ? ctx->f.as<float>() : nullptr));
+        std::swap(cur, nxt);
+    }
+    VQ_TRY(launch_transpose(ctx->stream, cur, S, n, R));
+    VQ_TRY(launch_transpose(ctx->stream, ctx->y.as<float>(), Y, n, R));
+    if (F_last) VQ_TRY(launch_transpose(ctx->stream, ctx->f.as<float>(), F_last, n, R));
+    return VELOXQ_OK;
+}
+
+int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
+                int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa, double* d_knots) {
+    (void)replicas; (void)steps; (void)sched; (void)seed; (void)ckpt_every;
+    (void)loss; (void)d_dt; (void)d_kappa; (void)d_knots;
+    if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    return fail(VELOXQ_EUNSUPPORTED, "gradient kernels are not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,233 @@
+// vq_dense.cu -- dense instances on the CUDA cores (the plain FP32 form):
+// F = S Qoff as a register-tiled SGEMM (M = replicas, N = K = n; S replica-major
+// [R][n], Qoff symmetric row-major) with the ballistic-SB update fused into the
+// epilogue, and the exact readout energy in int64 fixed point.
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;   // 256 threads, 8x8 outputs each
+
+// C[r][i] = sum_j S[r][j] Qoff[j][i]. Tiles are zero-filled past the edges.
+template <bool FIELD_ONLY>
+__global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const float* __restrict__ S_cur,
+                                                    const float* __restrict__ Qoff, float* __restrict__ S_nxt,
+                                                    float* __restrict__ Y, const float* __restrict__ bf,
+                                                    const float* __restrict__ a_table, int k, float dt, float a0,
+                                                    float c0, float* __restrict__ F_out) {
+    __shared__ __align__(16) float As[2][BK][BM];
+    __shared__ __align__(16) float Bs[2][BK][BN];
+    const int tid = threadIdx.x;
+    const int tx = tid % 16, ty = tid / 16;
+    const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
+    // A tile: 128 rows x 8 k -> thread loads 4 consecutive k of one row
+    const int a_row = tid / 2, a_k = (tid % 2) * 4;
+    // B tile: 8 k x 128 cols -> thread loads 4 consecutive cols of one k
+    const int b_k = tid / 32, b_col = (tid % 32) * 4;
+    float acc[TM][TN];
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = 0.0f;
+
+    auto load_tiles = [&](int kt, float (&ra)[4], float (&rb)[4]) {
+        const int64_t gr = m0 + a_row;
+        const int64_t gk = (int64_t)kt * BK + a_k;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) ra[q] = (gr < R && gk + q < n) ? __ldg(S_cur + gr * n + gk + q) : 0.0f;
+        const int64_t bk = (int64_t)kt * BK + b_k;
+        const int64_t bc = n0 + b_col;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) rb[q] = (bk < n && bc + q < n) ? __ldg(Qoff + bk * n + bc + q) : 0.0f;
+    };
+    auto store_tiles = [&](int buf, const float (&ra)[4], const float (&rb)[4]) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) As[buf][a_k + q][a_row] = ra[q];
+        *reinterpret_cast<float4*>(&Bs[buf][b_k][b_col]) = make_float4(rb[0], rb[1], rb[2], rb[3]);
+    };
+
+    const int ktiles = (int)div_up(n, BK);
+    float ra[4], rb[4];
+    load_tiles(0, ra, rb);
+    store_tiles(0, ra, rb);
+    __syncthreads();
+    for (int kt = 0; kt < ktiles; ++kt) {
+        const int cur = kt & 1;
+        if (kt + 1 < ktiles) load_tiles(kt + 1, ra, rb);
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float av[TM], bv[TN];
+            const float4 a0v = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
+            const float4 a1v = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
+            const float4 b0v = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
+            const float4 b1v = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+            av[0] = a0v.x; av[1] = a0v.y; av[2] = a0v.z; av[3] = a0v.w;
+            av[4] = a1v.x; av[5] = a1v.y; av[6] = a1v.z; av[7] = a1v.w;
+            bv[0] = b0v.x; bv[1] = b0v.y; bv[2] = b0v.z; bv[3] = b0v.w;
+            bv[4] = b1v.x; bv[5] = b1v.y; bv[6] = b1v.z; bv[7] = b1v.w;
+#pragma unroll
+            for (int i = 0; i < TM; ++i)
+#pragma unroll
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+        }
+        if (kt + 1 < ktiles) store_tiles(cur ^ 1, ra, rb);
+        __syncthreads();
+    }
+    // ---- epilogue: field -> update (per output element) ----
+    const float a_kv = FIELD_ONLY ? 0.0f : __ldg(a_table + k);
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+        const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+        if (r >= R) continue;
+#pragma unroll
+        for (int j = 0; j < TN; ++j) {
+            const int64_t c = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+            if (c >= n) continue;
+            const int64_t p = r * n + c;
+            const float F = acc[i][j];
+            if (F_out) F_out[p] = F;
+            if constexpr (!FIELD_ONLY) {
+                float s = S_cur[p], yv = Y[p];
+                vqd::bsb_update(F, __ldg(bf + c), a_kv, dt, a0, c0, s, yv);
+                S_nxt[p] = s;
+                Y[p] = yv;
+            }
+        }
+    }
+}
+
+template <typename QT> __device__ __forceinline__ int64_t qfix(QT q, int shift);
+template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int) { return (int64_t)q; }
+template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int) { return (int64_t)q; }
+template <> __device__ __forceinline__ int64_t qfix<float>(float q, int shift) {
+    return __double2ll_rn((double)q * ldexp(1.0, shift));
+}
+template <> __device__ __forceinline__ int64_t qfix<double>(double q, int shift) {
+    return __double2ll_rn(q * ldexp(1.0, shift));
+}
+
+// Exact energy of x_r = [S_r > 0] (or of a caller batch of bytes), fixed
+// point: parts[g][r] = sum over the 64 rows of tile g of
+// x_ri (dfix_i + sum_{j != i} qfix(Q_ij) x_rj), Q as given.
+// Block: 32 replicas x 8 row groups; the Q tile is staged in shared memory
+// as int64 and broadcast to the 32 replica lanes.
+template <typename QT, bool FROM_BYTES>
+__global__ void __launch_bounds__(256) k_dense_energy(int64_t R, int32_t n, const QT* __restrict__ Q, int shift,
+                                                      const int64_t* __restrict__ dfix, const float* __restrict__ S,
+                                                      const uint8_t* __restrict__ X, int64_t* __restrict__ parts) {
+    __shared__ int64_t qt[64][33];
+    __shared__ uint32_t xw[32];
+    __shared__ int64_t red[8][32];
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.y * 32 + lane;
+    const int64_t i0 = (int64_t)blockIdx.x * 64;
+    int64_t row[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) row[q] = 0;
+    for (int64_t j0 = 0; j0 < n; j0 += 32) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < 64 * 32; e += 256) {
+            const int ii = e / 32, jj = e % 32;
+            const int64_t gi = i0 + ii, gj = j0 + jj;
+            qt[ii][jj] = (gi < n && gj < n && gi != gj) ? qfix<QT>(Q[gi * n + gj], shift) : 0;
+        }
+        if (g == 0) {
+            // bit jj of xw[lane] = x[r][j0 + jj]
+            uint32_t w = 0;
+            if (r < R)
+                for (int jj = 0; jj < 32; ++jj) {
+                    const int64_t gj = j0 + jj;
+                    bool b = false;
+                    if (gj < n) b = FROM_BYTES ? X[r * n + gj] != 0 : S[r * n + gj] > 0.0f;
+                    w |= (uint32_t)b << jj;
+                }
+            xw[lane] = w;
+        }
+        __syncthreads();
+        const uint32_t w = xw[lane];
+#pragma unroll 4
+        for (int jj = 0; jj < 32; ++jj) {
+            const bool on = (w >> jj) & 1u;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) row[q] += on ? qt[g * 8 + q][jj] : 0;
+        }
+    }
+    int64_t part = 0;
+    if (r < R) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const int64_t gi = i0 + g * 8 + q;
+            if (gi < n) {
+                const bool xi = FROM_BYTES ? X[r * n + gi] != 0 : S[r * n + gi] > 0.0f;
+                if (xi) part += __ldg(dfix + gi) + row[q];
+            }
+        }
+    }
+    red[g][lane] = part;
+    __syncthreads();
+    if (g == 0 && r < R) {
+        int64_t tot = 0;
+        for (int q = 0; q < 8; ++q) tot += red[q][lane];
+        parts[(int64_t)blockIdx.x * R + r] = tot;
+    }
+}
+
+template <bool FIELD_ONLY>
+int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table,
+                      int k, float dt, float a0, float c0, float* F_out) {
+    const int32_t n = (int32_t)ctx->n;
+    dim3 g((unsigned)div_up(n, BN), (unsigned)div_up(R, BM));
+    k_dense_step<FIELD_ONLY><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
+                                                         ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out);
+    VQ_LAUNCH_CHECK("dense_step");
+    return VELOXQ_OK;
+}
+
+template <bool FROM_BYTES>
+int launch_dense_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_t* X, int64_t* parts, int* nparts) {
+    const int32_t n = (int32_t)ctx->n;
+    *nparts = (int)div_up(n, 64);
+    if (R == 0) return VELOXQ_OK;
+    dim3 g((unsigned)div_up(n, 64), (unsigned)div_up(R, 32));
+    const int sh = ctx->energy_shift;
+    const int64_t* df = ctx->dfix.as<int64_t>();
+    switch (ctx->qx_type) {
+        case VELOXQ_I8:
+            k_dense_energy<int8_t, FROM_BYTES><<<g, 256, 0, ctx->stream>>>(R, n, ctx->qx.as<int8_t>(), sh, df, S, X, parts);
+            break;
+        case VELOXQ_I32:
+            k_dense_energy<int32_t, FROM_BYTES><<<g, 256, 0, ctx->stream>>>(R, n, ctx->qx.as<int32_t>(), sh, df, S, X, parts);
+            break;
+        case VELOXQ_F32:
+            k_dense_energy<float, FROM_BYTES><<<g, 256, 0, ctx->stream>>>(R, n, ctx->qx.as<float>(), sh, df, S, X, parts);
+            break;
+        case VELOXQ_F64:
+            k_dense_energy<double, FROM_BYTES><<<g, 256, 0, ctx->stream>>>(R, n, ctx->qx.as<double>(), sh, df, S, X, parts);
+            break;
+    }
+    VQ_LAUNCH_CHECK("dense_energy");
+    return VELOXQ_OK;
+}
+
+}  // namespace
+
+int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
+               float dt, float a0, float c0, float* F_out) {
+    return launch_dense_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out);
+}
+
+int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
+    return launch_dense_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+}
+
+int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts) {
+    return launch_dense_energy<false>(ctx, R, S, nullptr, parts, nparts);
+}
+
+int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts) {
+    return launch_dense_energy<true>(ctx, B, nullptr, X, parts, nparts);
+}
+
+}  // namespace vq

@@ -1,0 +1,615 @@
+// vq_ingest.cu -- building a context on the device: validation, the symmetric
+// off-diagonal operand Qoff, the bias b, the constant K0, fixed-point energy
+// weights and the spectral radius (power iteration).
+//
+// Identity used throughout (Sec. 2 eq. qubo_model with x = (1 + s)/2):
+//   E(x) = s^T Qoff s / 4 + b^T s / 2 + K0,  b = Qs 1 + c,
+//   K0   = sum_{i != j} Qs_ij / 4 + sum_i d_i / 2,  d_i = Q_ii + c_i,
+// and, for the exact energy of a binary x,
+//   E(x) = sum_i x_i (d_i + sum_{j != i} Qs_ij x_j).
+// Energies are accumulated as int64 multiples of 2^-S (S = energy_shift):
+// exact for integer Q (S = 0 dense, S = 1 sparse, where 2 Qs is an integer)
+// and, for real Q, exact sums of values rounded to 2^-S with S chosen so that
+// no sum can overflow -- order-independent, unlike FP64 summation.
+#include <cub/cub.cuh>
+
+#include <cmath>
+#include <cstring>
+
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace {
+
+constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedThreads = 512;
+
+template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
+
+// deterministic two-stage sum (fixed partition and tree order)
+__global__ void k_sum_stage1(const double* __restrict__ x, int64_t n, int square, double* __restrict__ part) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double v = x[i];
+        acc += square ? v * v : v;
+    }
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_stage2(const double* __restrict__ part, int nparts, double* __restrict__ out) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = sh[0];
+}
+
+int reduce_sum(cudaStream_t st, const double* x, int64_t n, int square, double* out, double* part) {
+    k_sum_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(x, n, square, part);
+    k_sum_stage2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, out);
+    VQ_LAUNCH_CHECK("reduce_sum");
+    return VELOXQ_OK;
+}
+
+// error word layout: bit flags, plus first offending row
+enum { ERR_ROWPTR = 1, ERR_COL = 2, ERR_ORDER = 4, ERR_NONFINITE = 8, ERR_ASYM = 16, ERR_DIAG = 32,
+       ERR_RANGE = 64 };
+
+template <typename T> __device__ __forceinline__ bool finite_val(T v) { return true; }
+template <> __device__ __forceinline__ bool finite_val<float>(float v) { return isfinite(v); }
+template <> __device__ __forceinline__ bool finite_val<double>(double v) { return isfinite(v); }
+
+// ------------------------------- dense ------------------------------------
+template <typename T>
+__global__ void k_dense_check(const T* __restrict__ q, int64_t total, int* err) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x)
+        if (!finite_val(q[p])) atomicOr(err, ERR_NONFINITE);
+}
+
+// Ising: mirror the strict upper triangle into the lower one (in place).
+template <typename T>
+__global__ void k_dense_mirror(T* q, int64_t n) {
+    const int64_t total = n * n;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < total; p += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = p / n, j = p % n;
+        if (i > j) q[p] = q[j * n + i];
+        else if (i == j) q[p] = T(0);
+    }
+}
+
+// Per row: off-diagonal row sum, |.| row sum, diagonal (one block per row).
+template <typename T>
+__global__ void k_dense_rows(const T* __restrict__ q, int64_t n, double* rowsum, double* absrow, double* diag) {
+    __shared__ double s1[256], s2[256];
+    const int64_t i = blockIdx.x;
+    const T* row = q + i * n;
+    double a = 0.0, b = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
+        if (j != i) {
+            const double v = to_d(row[j]);
+            a += v;
+            b += fabs(v);
+        }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            s1[threadIdx.x] += s1[threadIdx.x + s];
+            s2[threadIdx.x] += s2[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        rowsum[i] = s1[0];
+        absrow[i] = s2[0];
+        diag[i] = to_d(row[i]);
+    }
+}
+
+// Per column: off-diagonal column sum (coalesced over columns).
+template <typename T>
+__global__ void k_dense_cols(const T* __restrict__ q, int64_t n, double* colsum) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double a = 0.0;
+    for (int64_t i = 0; i < n; ++i)
+        if (i != j) a += to_d(q[i * n + j]);
+    colsum[j] = a;
+}
+
+// Qoff_ij = (Q_ij + Q_ji)/2 off the diagonal, 0 on it; 32x32 tiles through shared memory.
+template <typename T>
+__global__ void k_dense_qoff(const T* __restrict__ q, int64_t n, float* __restrict__ out) {
+    __shared__ double tile[32][33];
+    const int64_t bi = (int64_t)blockIdx.y * 32, bj = (int64_t)blockIdx.x * 32;
+    // load the transposed tile Q[bj.., bi..]
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t gi = bj + r, gj = bi + threadIdx.x;
+        tile[r][threadIdx.x] = (gi < n && gj < n) ? to_d(q[gi * n + gj]) : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t gi = bi + r, gj = bj + threadIdx.x;
+        if (gi < n && gj < n) {
+            const double v = 0.5 * (to_d(q[gi * n + gj]) + tile[threadIdx.x][r]);
+            out[gi * n + gj] = (gi == gj) ? 0.0f : (float)v;
+        }
+    }
+}
+
+// d_i, b_i, |d_i| for dense contexts
+__global__ void k_dense_bias(int64_t n, int ising, const double* __restrict__ rowsum, const double* __restrict__ colsum,
+                             const double* __restrict__ diag, const double* __restrict__ lin, double* d, float* bf,
+                             double* absd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = lin ? lin[i] : 0.0;
+    const double di = ising ? c - rowsum[i] : diag[i] + c;   // Ising: Q_ii = h_i - sum_l J_il
+    d[i] = di;
+    absd[i] = fabs(di);
+    bf[i] = (float)(di + 0.5 * (rowsum[i] + colsum[i]));
+}
+
+// -------------------------------- CSR -------------------------------------
+template <typename T>
+__global__ void k_csr_validate(int64_t n, int64_t nnz, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               const T* __restrict__ val, int ising, int* err, int64_t* bad_row) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t b = rp[i], e = rp[i + 1];
+    int f = 0;
+    // offsets are checked against the arrays before any entry is read
+    if (b < 0 || e < b || e > nnz) f |= ERR_ROWPTR;
+    else {
+        int32_t prev = -1;
+        for (int64_t p = b; p < e; ++p) {
+            const int32_t j = col[p];
+            if (j < 0 || (int64_t)j >= n) { f |= ERR_COL; break; }
+            if (j <= prev) { f |= ERR_ORDER; break; }
+            prev = j;
+            if (!finite_val(val[p])) f |= ERR_NONFINITE;
+            if (ising && j == i) f |= ERR_DIAG;
+        }
+    }
+    if (f) {
+        atomicOr(err, f);
+        atomicMin((unsigned long long*)bad_row, (unsigned long long)i);
+    }
+}
+
+__device__ __forceinline__ int64_t find_in_row(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                               int64_t row, int32_t target) {
+    int64_t lo = rp[row], hi = rp[row + 1] - 1;
+    while (lo <= hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        const int32_t c = col[mid];
+        if (c == target) return mid;
+        if (c < target) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+// Symmetric value of the stored entry p = (i, j), i != j.
+template <typename T>
+__device__ __forceinline__ bool sym_value(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                          const T* __restrict__ val, int64_t i, int64_t p, int ising,
+                                          double* qs, int64_t* w2) {
+    const int32_t j = col[p];
+    const int64_t t = find_in_row(rp, col, j, (int32_t)i);
+    if (t < 0) return false;
+    const double vij = to_d(val[p]), vji = to_d(val[t]);
+    if (ising) {
+        // the pair's coupling is the value stored at its upper-triangle position
+        const double v = (i < j) ? vij : vji;
+        *qs = v;
+        *w2 = (int64_t)(2.0 * v);
+    } else {
+        *qs = 0.5 * (vij + vji);
+        *w2 = (int64_t)vij + (int64_t)vji;
+    }
+    return true;
+}
+
+template <typename T>
+__global__ void k_csr_pass1(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const T* __restrict__ val, int ising, int integer, int64_t* cnt, double* rowsum,
+                            double* absrow, double* diag, int* err, int64_t* bad_row, unsigned long long* maxw2) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t c = 0;
+    double rs = 0.0, ab = 0.0, dg = 0.0;
+    unsigned long long mw = 0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        if ((int64_t)col[p] == i) { dg = to_d(val[p]); continue; }
+        double qs;
+        int64_t w2;
+        if (!sym_value(rp, col, val, i, p, ising, &qs, &w2)) {
+            atomicOr(err, ERR_ASYM);
+            atomicMin((unsigned long long*)bad_row, (unsigned long long)i);
+            return;
+        }
+        ++c;
+        rs += qs;
+        ab += fabs(qs);
+        if (integer) {
+            const unsigned long long a = (unsigned long long)(w2 < 0 ? -w2 : w2);
+            if (a > mw) mw = a;
+        }
+    }
+    cnt[i] = c;
+    rowsum[i] = rs;
+    absrow[i] = ab;
+    diag[i] = dg;
+    if (integer && mw) atomicMax(maxw2, mw);
+}
+
+template <typename T>
+__global__ void k_csr_pass2(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                            const T* __restrict__ val, int ising, int integer, int shift,
+                            const int64_t* __restrict__ rp_f, int32_t* col_f, float* wf, int8_t* w8, int64_t* wfix) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t o = rp_f[i];
+    const double scale = ldexp(1.0, shift);
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) {
+        if ((int64_t)col[p] == i) continue;
+        double qs;
+        int64_t w2;
+        sym_value(rp, col, val, i, p, ising, &qs, &w2);
+        col_f[o] = col[p];
+        wf[o] = (float)qs;
+        if (w8) w8[o] = (int8_t)w2;
+        if (wfix) wfix[o] = integer ? w2 : __double2ll_rn(qs * scale);
+        ++o;
+    }
+}
+
+__global__ void k_csr_bias(int64_t n, int ising, const double* __restrict__ rowsum, const double* __restrict__ diag,
+                           const double* __restrict__ lin, double* d, float* bf, double* absd) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double c = lin ? lin[i] : 0.0;
+    const double di = ising ? c - rowsum[i] : diag[i] + c;
+    d[i] = di;
+    absd[i] = fabs(di);
+    bf[i] = (float)(di + rowsum[i]);
+}
+
+__global__ void k_fix(int64_t n, const double* __restrict__ d, int shift, int64_t* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = __double2ll_rn(d[i] * ldexp(1.0, shift));
+}
+
+// ---------------------------- power iteration -----------------------------
+__global__ void k_pi_init(int64_t n, double* v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t h = (uint32_t)i * 2654435761u;
+    h ^= h >> 15;
+    h *= 2246822519u;
+    h ^= h >> 13;
+    const double mag = 1.0 + (double)((h >> 1) & 1023u) / 4096.0;
+    v[i] = (h & 1u) ? mag : -mag;
+}
+
+__global__ void k_pi_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                          const float* __restrict__ w, const double* __restrict__ v, const double* __restrict__ nrm2,
+                          double* out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double inv = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+    double a = 0.0;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a += (double)w[p] * v[col[p]];
+    out[i] = a * inv;
+}
+
+__global__ void k_pi_gemv(int64_t n, const float* __restrict__ q, const double* __restrict__ v,
+                          const double* __restrict__ nrm2, double* out) {
+    __shared__ double sh[256];
+    const int64_t i = blockIdx.x;
+    const float* row = q + i * n;
+    double a = 0.0;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a += (double)row[j] * v[j];
+    sh[threadIdx.x] = a;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[i] = *nrm2 > 0.0 ? sh[0] / sqrt(*nrm2) : 0.0;
+}
+
+template <typename T>
+int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising, bool integer) {
+    const int64_t n = ctx->n;
+    cudaStream_t st = ctx->stream;
+    const size_t qbytes = sizeof(T) * (size_t)n * (size_t)n;
+    VQ_TRY(ctx->qx.ensure(qbytes));
+    VQ_CUDA(cudaMemcpyAsync(ctx->qx.p, Qh, qbytes, cudaMemcpyHostToDevice, st));
+    T* q = ctx->qx.as<T>();
+    DevBuf tmp;
+    // rowsum, colsum, absrow, diag, lin, d, absd, part, scalars
+    VQ_TRY(tmp.ensure(sizeof(double) * (size_t)(7 * n + kRedBlocks + 8) + 64));
+    double* rowsum = tmp.as<double>();
+    double* colsum = rowsum + n;
+    double* absrow = colsum + n;
+    double* diag = absrow + n;
+    double* lin = diag + n;
+    double* d = lin + n;
+    double* absd = d + n;
+    double* part = absd + n;
+    double* scal = part + kRedBlocks;          // [0] sum rowsum [1] sum d [2] sum absrow [3] sum absd [4] sum lin
+    int* err = (int*)(scal + 8);
+    VQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    if (ch) VQ_CUDA(cudaMemcpyAsync(lin, ch, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    else VQ_CUDA(cudaMemsetAsync(lin, 0, sizeof(double) * n, st));
+    const int64_t total = n * n;
+    const int gb = (int)std::min<int64_t>(div_up(total, 256), 152 * 16);
+    k_dense_check<T><<<gb, 256, 0, st>>>(q, total, err);
+    if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
+    k_dense_rows<T><<<(unsigned)n, 256, 0, st>>>(q, n, rowsum, absrow, diag);
+    k_dense_cols<T><<<(unsigned)div_up(n, 128), 128, 0, st>>>(q, n, colsum);
+    VQ_TRY(ctx->qoff32.ensure(sizeof(float) * (size_t)total));
+    dim3 tb(32, 8), tg((unsigned)div_up(n, 32), (unsigned)div_up(n, 32));
+    k_dense_qoff<T><<<tg, tb, 0, st>>>(q, n, ctx->qoff32.as<float>());
+    VQ_TRY(ctx->bf.ensure(sizeof(float) * n));
+    k_dense_bias<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, ising ? 1 : 0, rowsum, colsum, diag,
+                                                            lin, d, ctx->bf.as<float>(), absd);
+    VQ_LAUNCH_CHECK("dense ingest");
+    VQ_TRY(reduce_sum(st, rowsum, n, 0, scal + 0, part));
+    VQ_TRY(reduce_sum(st, d, n, 0, scal + 1, part));
+    VQ_TRY(reduce_sum(st, absrow, n, 0, scal + 2, part));
+    VQ_TRY(reduce_sum(st, absd, n, 0, scal + 3, part));
+    VQ_TRY(reduce_sum(st, lin, n, 0, scal + 4, part));
+    double hs[5];
+    int herr = 0;
+    VQ_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    if (herr & ERR_NONFINITE) return fail(VELOXQ_EINVAL, "coupling matrix holds a non-finite value");
+    ctx->K0 = 0.25 * hs[0] + 0.5 * hs[1];
+    ctx->ising_offset = ising ? 0.5 * hs[0] - hs[4] : 0.0;
+    const double Tsum = hs[2] + hs[3];
+    if (integer) {
+        if (Tsum >= 9.0e18) return fail(VELOXQ_EUNSUPPORTED, "integer couplings too large for int64 energies");
+        ctx->energy_shift = 0;
+    } else {
+        int e = 0;
+        std::frexp(Tsum > 0 ? Tsum : 1.0, &e);     // Tsum < 2^e
+        ctx->energy_shift = std::max(0, std::min(200, 61 - e));
+    }
+    VQ_TRY(ctx->dfix.ensure(sizeof(int64_t) * n));
+    k_fix<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, d, ctx->energy_shift, ctx->dfix.as<int64_t>());
+    VQ_LAUNCH_CHECK("dense ingest fix");
+    VQ_CUDA(cudaStreamSynchronize(st));
+    ctx->nnz = n * (n - 1);
+    ctx->max_row = (int)(n - 1);
+    return VELOXQ_OK;
+}
+
+template <typename T>
+int ingest_csr_t(veloxq_ctx* ctx, const int64_t* rph, const int32_t* colh, const void* valh, const double* ch,
+                 bool ising, bool integer) {
+    const int64_t n = ctx->n;
+    cudaStream_t st = ctx->stream;
+    if (rph[0] != 0) return fail(VELOXQ_EINVAL, "rowptr[0] must be 0");
+    const int64_t nnz_in = rph[n];
+    if (nnz_in < 0) return fail(VELOXQ_EINVAL, "rowptr[n] must be >= 0");
+    if (nnz_in > 0 && (!colh || !valh)) return fail(VELOXQ_EINVAL, "col and val must not be NULL when nnz > 0");
+    DevBuf d_rp, d_col, d_val, tmp;
+    VQ_TRY(d_rp.ensure(sizeof(int64_t) * (n + 1)));
+    VQ_TRY(d_col.ensure(sizeof(int32_t) * std::max<int64_t>(nnz_in, 1)));
+    VQ_TRY(d_val.ensure(sizeof(T) * std::max<int64_t>(nnz_in, 1)));
+    VQ_CUDA(cudaMemcpyAsync(d_rp.p, rph, sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st));
+    if (nnz_in > 0) {
+        VQ_CUDA(cudaMemcpyAsync(d_col.p, colh, sizeof(int32_t) * nnz_in, cudaMemcpyHostToDevice, st));
+        VQ_CUDA(cudaMemcpyAsync(d_val.p, valh, sizeof(T) * nnz_in, cudaMemcpyHostToDevice, st));
+    }
+    // rowsum, absrow, diag, lin, d, absd | cnt (n+1) | part | scalars | err, bad_row, maxw2
+    VQ_TRY(tmp.ensure(sizeof(double) * (size_t)(6 * n + (n + 1) + kRedBlocks + 8) + 256));
+    double* rowsum = tmp.as<double>();
+    double* absrow = rowsum + n;
+    double* diag = absrow + n;
+    double* lin = diag + n;
+    double* d = lin + n;
+    double* absd = d + n;
+    int64_t* cnt = (int64_t*)(absd + n);
+    double* part = (double*)(cnt + n + 1);
+    double* scal = part + kRedBlocks;
+    int* err = (int*)(scal + 8);
+    int64_t* bad_row = (int64_t*)(scal + 9);
+    unsigned long long* maxw2 = (unsigned long long*)(scal + 10);
+    VQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
+    VQ_CUDA(cudaMemsetAsync(bad_row, 0x7f, sizeof(int64_t), st));
+    VQ_CUDA(cudaMemsetAsync(maxw2, 0, sizeof(unsigned long long), st));
+    VQ_CUDA(cudaMemsetAsync(cnt + n, 0, sizeof(int64_t), st));
+    if (ch) VQ_CUDA(cudaMemcpyAsync(lin, ch, sizeof(double) * n, cudaMemcpyHostToDevice, st));
+    else VQ_CUDA(cudaMemsetAsync(lin, 0, sizeof(double) * n, st));
+    const unsigned gr = (unsigned)div_up(n, 256);
+    const int64_t* rp = d_rp.as<int64_t>();
+    const int32_t* cl = d_col.as<int32_t>();
+    const T* vl = d_val.as<T>();
+    k_csr_validate<T><<<gr, 256, 0, st>>>(n, nnz_in, rp, cl, vl, ising ? 1 : 0, err, bad_row);
+    int herr = 0;
+    int64_t hbad = 0;
+    VQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(&hbad, bad_row, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    VQ_LAUNCH_CHECK("csr validate");
+    if (herr) {
+        std::string m = "malformed CSR input at row " + std::to_string(hbad) + ":";
+        if (herr & ERR_ROWPTR) m += " rowptr decreases or leaves [0, rowptr[n]];";
+        if (herr & ERR_COL) m += " column index out of range;";
+        if (herr & ERR_ORDER) m += " column indices not strictly increasing;";
+        if (herr & ERR_NONFINITE) m += " non-finite value;";
+        if (herr & ERR_DIAG) m += " Ising couplings must not hold diagonal entries;";
+        return fail(VELOXQ_EINVAL, m);
+    }
+    k_csr_pass1<T><<<gr, 256, 0, st>>>(n, rp, cl, vl, ising ? 1 : 0, integer ? 1 : 0, cnt, rowsum, absrow, diag,
+                                       err, bad_row, maxw2);
+    VQ_LAUNCH_CHECK("csr pass1");
+    unsigned long long hmaxw = 0;
+    VQ_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(&hbad, bad_row, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(&hmaxw, maxw2, sizeof(hmaxw), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    if (herr & ERR_ASYM)
+        return fail(VELOXQ_EUNSUPPORTED, "CSR pattern is not structurally symmetric (row " + std::to_string(hbad) +
+                                             " has an entry whose transpose is missing)");
+    // exclusive scan of the per-row counts -> field rowptr
+    VQ_TRY(ctx->rowptr.ensure(sizeof(int64_t) * (n + 1)));
+    size_t tbytes = 0;
+    cub::DeviceScan::ExclusiveSum(nullptr, tbytes, cnt, ctx->rowptr.as<int64_t>(), n + 1, st);
+    DevBuf ctmp;
+    VQ_TRY(ctmp.ensure(tbytes + 16));
+    VQ_CUDA(cub::DeviceScan::ExclusiveSum(ctmp.p, tbytes, cnt, ctx->rowptr.as<int64_t>(), n + 1, st));
+    int64_t nnz_f = 0;
+    VQ_CUDA(cudaMemcpyAsync(&nnz_f, ctx->rowptr.as<int64_t>() + n, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    VQ_TRY(ctx->bf.ensure(sizeof(float) * n));
+    k_csr_bias<<<gr, 256, 0, st>>>(n, ising ? 1 : 0, rowsum, diag, lin, d, ctx->bf.as<float>(), absd);
+    VQ_LAUNCH_CHECK("csr bias");
+    VQ_TRY(reduce_sum(st, rowsum, n, 0, scal + 0, part));
+    VQ_TRY(reduce_sum(st, d, n, 0, scal + 1, part));
+    VQ_TRY(reduce_sum(st, absrow, n, 0, scal + 2, part));
+    VQ_TRY(reduce_sum(st, absd, n, 0, scal + 3, part));
+    VQ_TRY(reduce_sum(st, lin, n, 0, scal + 4, part));
+    double hs[5];
+    VQ_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    ctx->nnz = nnz_f;
+    ctx->K0 = 0.25 * hs[0] + 0.5 * hs[1];
+    ctx->ising_offset = ising ? 0.5 * hs[0] - hs[4] : 0.0;
+    const double Tm = hs[2] + hs[3];
+    if (integer) {
+        if (Tm >= 4.0e18 || hmaxw > (unsigned long long)INT32_MAX)
+            return fail(VELOXQ_EUNSUPPORTED, "integer couplings too large for int64 energies");
+        ctx->energy_shift = 1;            // 2 Qs is an integer
+    } else {
+        int e = 0;
+        std::frexp(Tm > 0 ? Tm : 1.0, &e);
+        ctx->energy_shift = std::max(0, std::min(200, 61 - e));
+    }
+    const bool use8 = integer && hmaxw <= 127;
+    VQ_TRY(ctx->col.ensure(sizeof(int32_t) * std::max<int64_t>(nnz_f, 1)));
+    VQ_TRY(ctx->wf.ensure(sizeof(float) * std::max<int64_t>(nnz_f, 1)));
+    if (use8) {
+        VQ_TRY(ctx->w8.ensure(sizeof(int8_t) * std::max<int64_t>(nnz_f, 1) + 16));
+        ctx->wfix.release();
+    } else {
+        VQ_TRY(ctx->wfix.ensure(sizeof(int64_t) * std::max<int64_t>(nnz_f, 1)));
+        ctx->w8.release();
+    }
+    k_csr_pass2<T><<<gr, 256, 0, st>>>(n, rp, cl, vl, ising ? 1 : 0, integer ? 1 : 0, ctx->energy_shift,
+                                       ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(), ctx->wf.as<float>(),
+                                       use8 ? ctx->w8.as<int8_t>() : nullptr,
+                                       use8 ? nullptr : ctx->wfix.as<int64_t>());
+    VQ_TRY(ctx->dfix.ensure(sizeof(int64_t) * n));
+    k_fix<<<gr, 256, 0, st>>>(n, d, integer ? 1 : ctx->energy_shift, ctx->dfix.as<int64_t>());
+    VQ_LAUNCH_CHECK("csr pass2");
+    // longest row of the field structure (for kernel selection)
+    {
+        std::vector<int64_t> hcnt;
+        // counts are small relative to the arrays; read back only their maximum
+        size_t mb = 0;
+        int64_t* dmax = (int64_t*)(scal + 11);
+        cub::DeviceReduce::Max(nullptr, mb, cnt, dmax, n, st);
+        DevBuf mtmp;
+        VQ_TRY(mtmp.ensure(mb + 16));
+        VQ_CUDA(cub::DeviceReduce::Max(mtmp.p, mb, cnt, dmax, n, st));
+        int64_t hm = 0;
+        VQ_CUDA(cudaMemcpyAsync(&hm, dmax, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        VQ_CUDA(cudaStreamSynchronize(st));
+        ctx->max_row = (int)hm;
+    }
+    return VELOXQ_OK;
+}
+
+}  // namespace
+
+int ingest_dense(veloxq_ctx* ctx, veloxq_vtype vt, const void* Qh, const double* ch, bool ising) {
+    ctx->dense = true;
+    ctx->qx_type = vt;
+    bool integer = (vt == VELOXQ_I8 || vt == VELOXQ_I32);
+    if (integer && ch)
+        for (int64_t i = 0; i < ctx->n; ++i)
+            if (!(std::fabs(ch[i]) < 4.0e15) || ch[i] != std::floor(ch[i])) { integer = false; break; }
+    if (ch)
+        for (int64_t i = 0; i < ctx->n; ++i)
+            if (!std::isfinite(ch[i])) return fail(VELOXQ_EINVAL, "linear term holds a non-finite value");
+    ctx->integer = integer;
+    switch (vt) {
+        case VELOXQ_I8: return ingest_dense_t<int8_t>(ctx, Qh, ch, ising, integer);
+        case VELOXQ_I32: return ingest_dense_t<int32_t>(ctx, Qh, ch, ising, integer);
+        case VELOXQ_F32: return ingest_dense_t<float>(ctx, Qh, ch, ising, integer);
+        case VELOXQ_F64: return ingest_dense_t<double>(ctx, Qh, ch, ising, integer);
+    }
+    return fail(VELOXQ_EINVAL, "unknown value type");
+}
+
+int ingest_csr(veloxq_ctx* ctx, const int64_t* rowptr, const int32_t* col, veloxq_vtype vt, const void* val,
+               const double* ch, bool ising) {
+    ctx->dense = false;
+    bool integer = (vt == VELOXQ_I8 || vt == VELOXQ_I32);
+    if (integer && ch)
+        for (int64_t i = 0; i < ctx->n; ++i)
+            if (!(std::fabs(ch[i]) < 4.0e15) || ch[i] != std::floor(ch[i])) { integer = false; break; }
+    if (ch)
+        for (int64_t i = 0; i < ctx->n; ++i)
+            if (!std::isfinite(ch[i])) return fail(VELOXQ_EINVAL, "linear term holds a non-finite value");
+    ctx->integer = integer;
+    switch (vt) {
+        case VELOXQ_I8: return ingest_csr_t<int8_t>(ctx, rowptr, col, val, ch, ising, integer);
+        case VELOXQ_I32: return ingest_csr_t<int32_t>(ctx, rowptr, col, val, ch, ising, integer);
+        case VELOXQ_F32: return ingest_csr_t<float>(ctx, rowptr, col, val, ch, ising, integer);
+        case VELOXQ_F64: return ingest_csr_t<double>(ctx, rowptr, col, val, ch, ising, integer);
+    }
+    return fail(VELOXQ_EINVAL, "unknown value type");
+}
+
+// rho(Qoff) by power iteration: w_t = Qoff (w_{t-1} / |w_{t-1}|), rho ~ |w_T|.
+int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
+    const int64_t n = ctx->n;
+    cudaStream_t st = ctx->stream;
+    DevBuf buf;
+    VQ_TRY(buf.ensure(sizeof(double) * (size_t)(2 * n + kRedBlocks + 4)));
+    double* v = buf.as<double>();
+    double* w = v + n;
+    double* part = w + n;
+    double* nrm = part + kRedBlocks;
+    const unsigned gr = (unsigned)div_up(n, 256);
+    k_pi_init<<<gr, 256, 0, st>>>(n, v);
+    VQ_TRY(reduce_sum(st, v, n, 1, nrm, part));
+    for (int t = 0; t < iters; ++t) {
+        if (ctx->dense)
+            k_pi_gemv<<<(unsigned)n, 256, 0, st>>>(n, ctx->qoff32.as<float>(), v, nrm, w);
+        else
+            k_pi_spmv<<<gr, 256, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(), ctx->wf.as<float>(),
+                                          v, nrm, w);
+        VQ_TRY(reduce_sum(st, w, n, 1, nrm, part));
+        std::swap(v, w);
+    }
+    VQ_LAUNCH_CHECK("power iteration");
+    double h = 0.0;
+    VQ_CUDA(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    *rho = std::sqrt(h);
+    return VELOXQ_OK;
+}
+
+}  // namespace vq

@@ -1,0 +1,203 @@
+// vq_internal.cuh -- internal declarations of libveloxq (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/veloxq.h"
+
+// ---------------------------------------------------------------------------
+// error plumbing: every entry point returns a status, the message is
+// thread-local.
+// ---------------------------------------------------------------------------
+namespace vq {
+
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define VQ_CUDA(call)                                               \
+    do {                                                            \
+        cudaError_t _e = (call);                                    \
+        if (_e != cudaSuccess) return ::vq::cuda_fail(_e, #call);   \
+    } while (0)
+
+#define VQ_TRY(call)                    \
+    do {                                \
+        int _s = (call);                \
+        if (_s != VELOXQ_OK) return _s; \
+    } while (0)
+
+#define VQ_LAUNCH_CHECK(what)                                           \
+    do {                                                                \
+        cudaError_t _e = cudaGetLastError();                            \
+        if (_e != cudaSuccess) return ::vq::cuda_fail(_e, what);        \
+    } while (0)
+
+// Device buffer owned by a context.
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    // grow to at least `b` bytes (contents not kept)
+    int ensure(size_t b);
+    template <typename T> T* as() const { return static_cast<T*>(p); }
+};
+
+// Row layout of a state block in device memory.
+enum Layout { LAYOUT_RN = 0 /* [R][n], replica-major */, LAYOUT_NR = 1 /* [n][R] */ };
+
+// Resolved schedule for one run.
+struct RunParams {
+    float dt, a0, c0, sigma0;
+    int32_t K;
+    int32_t readout_every;
+    veloxq_prec prec;
+    veloxq_path path;
+    std::vector<double> knots;  // at least 1
+};
+
+}  // namespace vq
+
+// ---------------------------------------------------------------------------
+// the context
+// ---------------------------------------------------------------------------
+struct veloxq_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t n = 0;
+    bool dense = false;
+    bool integer = false;
+    double K0 = 0.0;
+    double rho = 0.0;
+    double ising_offset = 0.0;
+    int energy_shift = 0;         // fixed-point exponent S: energies are int64 multiples of 2^-S
+
+    // ---- sparse: off-diagonal part of Qs in CSR ----
+    int64_t nnz = 0;
+    vq::DevBuf rowptr;            // int64 [n+1]
+    vq::DevBuf col;               // int32 [nnz]
+    vq::DevBuf wf;                // float [nnz]   Qs_ij (field operand)
+    vq::DevBuf w8;                // int8  [nnz]   2 Qs_ij when integer and |2Qs| <= 127
+    vq::DevBuf wfix;              // int64 [nnz]   round(Qs_ij 2^S) (energy), when w8 is absent
+    int max_row = 0;              // longest row of the field structure
+
+    // ---- dense ----
+    veloxq_vtype qx_type = VELOXQ_F32;
+    vq::DevBuf qx;                // [n][n] Q as given (input type; diagonal unused)
+    vq::DevBuf qoff32;            // float [n][n] Qoff
+    vq::DevBuf qoff16;            // bf16  [n][n] Qoff (tensor-core operand)
+    vq::DevBuf qoff8;             // e4m3  [n][n] Qoff / scale_i
+    vq::DevBuf qscale8;           // float [n] per-row FP8 scales
+
+    // ---- common ----
+    vq::DevBuf bf;                // float  [n] b = Qs 1 + c
+    vq::DevBuf dfix;              // int64  [n] round((Q_ii + c_i) 2^S)
+
+    // ---- scratch reused across calls ----
+    vq::DevBuf s_a, s_b, y, f, ework, best_e, best_bits, flags, a_table, xout, misc;
+};
+
+namespace vq {
+
+// sizes and helpers
+__host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// ingest (vq_ingest.cu)
+int ingest_dense(veloxq_ctx* ctx, veloxq_vtype vt, const void* Qh, const double* ch, bool ising);
+int ingest_csr(veloxq_ctx* ctx, const int64_t* rowptr, const int32_t* col, veloxq_vtype vt,
+               const void* val, const double* ch, bool ising);
+int power_iteration(veloxq_ctx* ctx, int iters, double* rho);
+
+// state init, readout, best, argmin (vq_common.cu)
+int launch_init_state(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, Layout layout,
+                      float* S, float* Y);
+int launch_transpose(cudaStream_t st, const float* in, float* out, int64_t rows, int64_t cols);
+int launch_best_update(veloxq_ctx* ctx, int32_t R, int nparts, const int64_t* parts, int64_t* best,
+                       uint8_t* improved);
+int launch_best_bits(veloxq_ctx* ctx, int32_t R, Layout layout, const float* S, const uint8_t* improved,
+                     uint32_t* bits);
+int launch_argmin_unpack(veloxq_ctx* ctx, int32_t R, const int64_t* best, const uint32_t* bits,
+                         int64_t* misc, uint8_t* x);
+
+// sparse streaming kernels (vq_stream.cu)
+int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y,
+                const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+int stream_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
+int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
+
+// sparse resident kernel (vq_resident.cu)
+bool resident_fits(const veloxq_ctx* ctx, int32_t R, int* rc, int* threads, size_t* smem);
+int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, uint64_t seed, int k_begin, int k_end,
+                 const float* S_in, const float* Y_in, float* S_out, float* Y_out, float* F_out,
+                 int64_t* best_e, uint32_t* best_bits);
+
+// dense kernels (vq_dense.cu)
+int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y,
+               const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
+int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
+int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
+
+}  // namespace vq
+
+// ---------------------------------------------------------------------------
+// device helpers shared by the kernels
+// ---------------------------------------------------------------------------
+namespace vqd {
+
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11).
+__device__ __forceinline__ void philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                              uint32_t k0, uint32_t k1, uint32_t out[4]) {
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        const uint32_t hi0 = __umulhi(M0, c0), lo0 = M0 * c0;
+        const uint32_t hi1 = __umulhi(M1, c2), lo1 = M1 * c2;
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+// s0, y0 of variable i, replica r: sigma0 (2u - 1), u = (w >> 8) 2^-24.
+__device__ __forceinline__ void init_pair(int64_t i, int32_t r, uint64_t seed, float sigma0, float* s, float* y) {
+    uint32_t w[4];
+    philox4x32_10((uint32_t)i, (uint32_t)((uint64_t)i >> 32), (uint32_t)r, 0u, (uint32_t)seed,
+                  (uint32_t)(seed >> 32), w);
+    const float us = __uint2float_rn(w[0] >> 8) * 5.9604644775390625e-8f;
+    const float uy = __uint2float_rn(w[1] >> 8) * 5.9604644775390625e-8f;
+    *s = __fmul_rn(sigma0, __fsub_rn(__fmul_rn(2.0f, us), 1.0f));
+    *y = __fmul_rn(sigma0, __fsub_rn(__fmul_rn(2.0f, uy), 1.0f));
+}
+
+// One ballistic-SB update of a single (variable, replica) given its field F.
+// Rounded operation by operation (no contraction) so that it is the same
+// arithmetic in every kernel that uses it.
+__device__ __forceinline__ void bsb_update(float F, float b, float a_k, float dt, float a0, float c0,
+                                           float& s, float& y) {
+    const float phi = __fmul_rn(-0.5f, __fadd_rn(F, b));
+    const float drive = __fadd_rn(__fmul_rn(-__fsub_rn(a0, a_k), s), __fmul_rn(c0, phi));
+    float yn = __fadd_rn(y, __fmul_rn(dt, drive));
+    float sn = __fadd_rn(s, __fmul_rn(__fmul_rn(dt, a0), yn));
+    if (fabsf(sn) > 1.0f) {
+        sn = copysignf(1.0f, sn);
+        yn = 0.0f;
+    }
+    s = sn;
+    y = yn;
+}
+
+}  // namespace vqd

@@ -1,0 +1,259 @@
+// vq_stream.cu -- sparse local field fused with the ballistic-SB update, one
+// launch per step, state in HBM (variable-major [n][R]: the R replicas of a
+// variable are contiguous, so a neighbour's state is one coalesced vector
+// load shared by all lanes of the row), plus the exact readout energy.
+//
+// Step (App. B, ballistic form):  F_i = sum_{j != i} Qs_ij s_j  over the CSR
+// row of i, then phi, y, s, walls. Couplings come as FP32 Qs or, for integer
+// instances with |2 Qs| <= 127, as int8 2Qs (F = acc / 2, exact scaling).
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace {
+
+template <int V> struct VecT;
+template <> struct VecT<1> { using T = float; };
+template <> struct VecT<2> { using T = float2; };
+template <> struct VecT<4> { using T = float4; };
+
+template <int V> __device__ __forceinline__ void vload(const float* p, float (&v)[V]) {
+    if constexpr (V == 4) { const float4 t = __ldg(reinterpret_cast<const float4*>(p)); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (V == 2) { const float2 t = __ldg(reinterpret_cast<const float2*>(p)); v[0] = t.x; v[1] = t.y; }
+    else { v[0] = __ldg(p); }
+}
+template <int V> __device__ __forceinline__ void vload_plain(const float* p, float (&v)[V]) {
+    if constexpr (V == 4) { const float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (V == 2) { const float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y; }
+    else { v[0] = *p; }
+}
+template <int V> __device__ __forceinline__ void vstore(float* p, const float (&v)[V]) {
+    if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (V == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else *p = v[0];
+}
+
+__device__ __forceinline__ float wval(float w) { return w; }
+__device__ __forceinline__ float wval(int8_t w) { return (float)w; }
+
+// One thread per (variable i, vector v of V replicas).
+template <int V, typename WT, bool FIELD_ONLY>
+__global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const WT* __restrict__ w,
+                                                     float wscale, const float* __restrict__ S_cur,
+                                                     float* __restrict__ S_nxt, float* __restrict__ Y,
+                                                     const float* __restrict__ bf, const float* __restrict__ a_table,
+                                                     int k, float dt, float a0, float c0, float* __restrict__ F_out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i = t / nvec;
+    if (i >= n) return;
+    const int32_t v = (int32_t)(t - i * nvec);
+    const int64_t off = (int64_t)v * V;
+    float acc[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) acc[l] = 0.0f;
+    const int64_t p1 = __ldg(rp + i + 1);
+    for (int64_t p = __ldg(rp + i); p < p1; ++p) {
+        const int64_t j = __ldg(col + p);
+        const float wv = wval(__ldg(w + p));
+        float sj[V];
+        vload<V>(S_cur + j * R + off, sj);
+#pragma unroll
+        for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
+    }
+    float F[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) F[l] = acc[l] * wscale;     // wscale is 1 or 1/2: exact
+    const int64_t me = i * R + off;
+    if (F_out) vstore<V>(F_out + me, F);
+    if constexpr (FIELD_ONLY) return;
+    float s[V], y[V];
+    vload<V>(S_cur + me, s);
+    vload_plain<V>(Y + me, y);
+    const float b = __ldg(bf + i);
+    const float a_k = __ldg(a_table + k);
+#pragma unroll
+    for (int l = 0; l < V; ++l) vqd::bsb_update(F[l], b, a_k, dt, a0, c0, s[l], y[l]);
+    vstore<V>(S_nxt + me, s);
+    vstore<V>(Y + me, y);
+}
+
+__device__ __forceinline__ int64_t ewval(int8_t w) { return (int64_t)w; }
+__device__ __forceinline__ int64_t ewval(int64_t w) { return w; }
+
+// Exact readout energy, fixed point: parts[g][r] = sum over the rows of group
+// g of x_ri (dfix_i + sum_j wE_ij x_rj), x = [s > 0]. Block (TX, TY): TX
+// vectors of replicas, TY rows; rows of a group are grid-strided.
+template <int V, typename EW>
+__global__ void __launch_bounds__(256) k_stream_energy(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
+                                                       const int32_t* __restrict__ col, const EW* __restrict__ we,
+                                                       const int64_t* __restrict__ dfix, const float* __restrict__ S,
+                                                       int64_t* __restrict__ parts) {
+    extern __shared__ int64_t sh[];
+    const int TX = blockDim.x, TY = blockDim.y;
+    const int32_t v = blockIdx.x * TX + threadIdx.x;
+    int64_t part[V];
+#pragma unroll
+    for (int l = 0; l < V; ++l) part[l] = 0;
+    if (v < nvec) {
+        const int64_t off = (int64_t)v * V;
+        for (int64_t i = (int64_t)blockIdx.y * TY + threadIdx.y; i < n; i += (int64_t)gridDim.y * TY) {
+            float si[V];
+            vload<V>(S + i * R + off, si);
+            bool any = false;
+#pragma unroll
+            for (int l = 0; l < V; ++l) any |= si[l] > 0.0f;
+            if (!any) continue;
+            int64_t row[V];
+#pragma unroll
+            for (int l = 0; l < V; ++l) row[l] = 0;
+            const int64_t p1 = __ldg(rp + i + 1);
+            for (int64_t p = __ldg(rp + i); p < p1; ++p) {
+                const int64_t j = __ldg(col + p);
+                const int64_t wq = ewval(__ldg(we + p));
+                float sj[V];
+                vload<V>(S + j * R + off, sj);
+#pragma unroll
+                for (int l = 0; l < V; ++l) row[l] += sj[l] > 0.0f ? wq : 0;
+            }
+            const int64_t d = __ldg(dfix + i);
+#pragma unroll
+            for (int l = 0; l < V; ++l) part[l] += si[l] > 0.0f ? d + row[l] : 0;
+        }
+    }
+    // reduce over TY in a fixed order
+#pragma unroll
+    for (int l = 0; l < V; ++l) sh[((int64_t)threadIdx.y * TX + threadIdx.x) * V + l] = part[l];
+    __syncthreads();
+    if (threadIdx.y == 0 && v < nvec) {
+#pragma unroll
+        for (int l = 0; l < V; ++l) {
+            int64_t tot = 0;
+            for (int y = 0; y < TY; ++y) tot += sh[((int64_t)y * TX + threadIdx.x) * V + l];
+            const int32_t r = v * V + l;
+            if (r < R) parts[(int64_t)blockIdx.y * R + r] = tot;
+        }
+    }
+}
+
+// Energy of a caller batch X [B][n] (uint8): parts[g][b].
+template <typename EW>
+__global__ void __launch_bounds__(256) k_sparse_energy_x(int64_t n, int64_t B, const int64_t* __restrict__ rp,
+                                                         const int32_t* __restrict__ col, const EW* __restrict__ we,
+                                                         const int64_t* __restrict__ dfix, const uint8_t* __restrict__ X,
+                                                         int64_t* __restrict__ parts) {
+    __shared__ int64_t sh[256];
+    const int64_t b = blockIdx.y;
+    const uint8_t* x = X + b * n;
+    int64_t part = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        if (!x[i]) continue;
+        int64_t row = __ldg(dfix + i);
+        const int64_t p1 = __ldg(rp + i + 1);
+        for (int64_t p = __ldg(rp + i); p < p1; ++p)
+            if (x[__ldg(col + p)]) row += ewval(__ldg(we + p));
+        part += row;
+    }
+    sh[threadIdx.x] = part;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) parts[(int64_t)blockIdx.x * B + b] = sh[0];
+}
+
+int vec_width(int32_t R) { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
+
+template <bool FIELD_ONLY>
+int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
+                float dt, float a0, float c0, float* F_out) {
+    const int V = vec_width(R);
+    const int32_t nvec = R / V;
+    const int64_t total = ctx->n * (int64_t)nvec;
+    const unsigned g = (unsigned)div_up(total, 256);
+    const int64_t* rp = ctx->rowptr.as<int64_t>();
+    const int32_t* cl = ctx->col.as<int32_t>();
+    const float* bf = ctx->bf.as<float>();
+    cudaStream_t st = ctx->stream;
+#define VQ_STEP(VV, WT, WPTR, SC)                                                                                   \
+    k_stream_step<VV, WT, FIELD_ONLY><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, Y, bf,   \
+                                                         a_table, k, dt, a0, c0, F_out)
+    if (ctx->w8.p) {
+        const int8_t* w = ctx->w8.as<int8_t>();
+        if (V == 4) VQ_STEP(4, int8_t, w, 0.5f); else if (V == 2) VQ_STEP(2, int8_t, w, 0.5f); else VQ_STEP(1, int8_t, w, 0.5f);
+    } else {
+        const float* w = ctx->wf.as<float>();
+        if (V == 4) VQ_STEP(4, float, w, 1.0f); else if (V == 2) VQ_STEP(2, float, w, 1.0f); else VQ_STEP(1, float, w, 1.0f);
+    }
+#undef VQ_STEP
+    VQ_LAUNCH_CHECK("stream_step");
+    return VELOXQ_OK;
+}
+
+}  // namespace
+
+int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
+                float dt, float a0, float c0, float* F_out) {
+    return launch_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out);
+}
+
+int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
+    return launch_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+}
+
+// number of row groups (partial sums) used by stream_energy
+static int energy_groups(int32_t gx) { return std::max(1, 608 / std::max(1, gx)); }
+
+int stream_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts) {
+    const int V = vec_width(R);
+    const int32_t nvec = R / V;
+    int TX = 1;
+    while (TX < nvec && TX < 32) TX <<= 1;
+    const int TY = 256 / TX;
+    const int32_t gx = (int32_t)div_up(nvec, TX);
+    const int gy = energy_groups(gx);
+    *nparts = gy;
+    dim3 blk(TX, TY), grd(gx, gy);
+    const size_t sm = sizeof(int64_t) * 256 * V;
+    cudaStream_t st = ctx->stream;
+    const int64_t* rp = ctx->rowptr.as<int64_t>();
+    const int32_t* cl = ctx->col.as<int32_t>();
+    const int64_t* df = ctx->dfix.as<int64_t>();
+#define VQ_EN(VV, EW, WPTR) k_stream_energy<VV, EW><<<grd, blk, sm, st>>>(ctx->n, R, nvec, rp, cl, WPTR, df, S, parts)
+    if (ctx->w8.p) {
+        const int8_t* w = ctx->w8.as<int8_t>();
+        if (V == 4) VQ_EN(4, int8_t, w); else if (V == 2) VQ_EN(2, int8_t, w); else VQ_EN(1, int8_t, w);
+    } else {
+        const int64_t* w = ctx->wfix.as<int64_t>();
+        if (V == 4) VQ_EN(4, int64_t, w); else if (V == 2) VQ_EN(2, int64_t, w); else VQ_EN(1, int64_t, w);
+    }
+#undef VQ_EN
+    VQ_LAUNCH_CHECK("stream_energy");
+    return VELOXQ_OK;
+}
+
+int stream_energy_parts(int32_t R) {
+    const int V = vec_width(R);
+    const int32_t nvec = R / V;
+    int TX = 1;
+    while (TX < nvec && TX < 32) TX <<= 1;
+    return energy_groups((int32_t)div_up(nvec, TX));
+}
+
+int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts) {
+    const int G = 64;
+    *nparts = G;
+    if (B == 0) return VELOXQ_OK;
+    dim3 grd(G, (unsigned)B);
+    if (ctx->w8.p)
+        k_sparse_energy_x<int8_t><<<grd, 256, 0, ctx->stream>>>(ctx->n, B, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                                ctx->w8.as<int8_t>(), ctx->dfix.as<int64_t>(), X, parts);
+    else
+        k_sparse_energy_x<int64_t><<<grd, 256, 0, ctx->stream>>>(ctx->n, B, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                                 ctx->wfix.as<int64_t>(), ctx->dfix.as<int64_t>(), X, parts);
+    VQ_LAUNCH_CHECK("sparse_energy_x");
+    return VELOXQ_OK;
+}
+
+}  // namespace vq

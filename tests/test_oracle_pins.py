@@ -398,3 +398,19 @@ def test_gradient_matches_central_differences(knots):
         km[j] -= h
         dj = (O.bsb_loss(p, R, K, dt, a0, c0, kp, S0, Y0) - O.bsb_loss(p, R, K, dt, a0, c0, km, S0, Y0)) / (2 * h)
         assert g["d_knots"][j] == pytest.approx(dj, rel=1e-5, abs=1e-7)
+
+
+def test_sparse_ising_conversion_matches_dense_and_identity():
+    """The sparse App. A conversion equals the dense one and satisfies
+    H(s) = 2 E(x) + C on every state of a small Chimera instance."""
+    sp = I.chimera_ising(1, 2, 2, seed=3)          # 8 variables
+    J = sp.to_dense()
+    h = np.arange(sp.n, dtype=np.float64) - 3.0
+    p, C = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, h)
+    Qd, Cd = O.ising_to_qubo(np.triu(J, 1), h)
+    assert C == pytest.approx(Cd) and np.allclose(p.dense(), Qd)
+    S = np.array(list(itertools.product([-1, 1], repeat=sp.n)), dtype=np.int8)
+    X = ((S + 1) // 2).astype(np.uint8)
+    H = np.array([O.ising_energy(np.triu(J, 1), h, s) for s in S])
+    assert np.allclose(H, 2 * O.energy(p, X) + C, atol=1e-9)
+    assert p.integer and O.energy(p, X).dtype == np.int64
