@@ -1,0 +1,347 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the VeloxQ hot path (ballistic simulated
+bifurcation, arXiv:2501.19221 App. B) on one GB300.
+
+A "step" of this benchmark is one complete solve of the workload: Philox
+initial state, every integration step (field, fused update, walls, readout),
+the exact readout energies, best-so-far and the argmin over replicas.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Metric: spin-updates/s = n * replicas * integration steps / solve time.
+Default workload: the Chimera C16 +-J instance (2048 variables, int8 CSR),
+1024 replicas, 5000 integration steps, FP32 state, readout every 50 steps.
+With --gpus N (launched by torchrun) every rank solves its own replica of the
+workload (weak scaling, no data-path collective); the time is the max over
+ranks. --impl reference times the FP64 oracle on the host cores on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+from paper_2501_19221_gb300 import instances as I
+
+L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
+NUM_SMS = 152
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ----------------------------------------------------------------------------- workloads
+def workload(name: str) -> dict:
+    if name == "chimera_c16":
+        sp = I.chimera_ising(16, 16, 4, seed=0)
+        return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 1024, "K": 5000,
+                "readout_every": 50, "desc": "Chimera C16 (16x16 K_{4,4} cells), J = +-1, h = 0, int8 CSR"}
+    if name == "lattice_l100":
+        sp = I.cubic_lattice_ising(100, seed=0)
+        return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 256, "K": 400,
+                "readout_every": 50, "desc": "periodic 3-D +-J lattice L=100, int8 CSR"}
+    if name == "lattice_l464":
+        sp = I.cubic_lattice_ising(464, seed=0)
+        return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
+                "readout_every": 50, "desc": "periodic 3-D +-J lattice L=464 (n ~ 1e8), int8 CSR"}
+    if name == "dense_n20":
+        Q, c = I.dense_int_qubo(20, seed=0)
+        return {"name": name, "kind": "dense", "Q": Q, "c": c, "n": 20, "R": 128, "K": 2000,
+                "readout_every": 50, "desc": "dense int QUBO n=20, entries in [-8, 8]"}
+    raise SystemExit(f"unknown workload {name}")
+
+
+def create(B, w, stream=None):
+    if w["kind"] == "ising_csr":
+        sp = w["sp"]
+        return B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
+    return B.veloxq_create_dense(w["Q"], w["c"], stream)
+
+
+def input_arrays(w) -> list:
+    if w["kind"] == "ising_csr":
+        sp = w["sp"]
+        return [sp.rowptr, sp.col, sp.val, sp.lin]
+    return [w["Q"], w["c"]]
+
+
+def oracle_problem(w):
+    import oracle as O
+    if w["kind"] == "ising_csr":
+        sp = w["sp"]
+        p, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+        return p
+    return O.problem_from_dense(w["Q"], w["c"])
+
+
+def oracle_sample_rate(w, R_s: int, K_s: int) -> tuple:
+    """Spin-updates/s of the FP64 oracle (single thread) on R_s replicas x the
+    first K_s steps of the workload's schedule."""
+    import oracle as O
+    p = oracle_problem(w)
+    rho = O.spectral_radius(p) if p.n <= 6000 else 6.0
+    c0 = 2.0 / rho
+    S0, Y0 = O.init_state(p.n, R_s, 0, 0.1)
+    K = w["K"]
+    knots = [0.0, (K_s - 1) / (K - 1) if K > 1 else 0.0]
+    t0 = time.perf_counter()
+    O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0)
+    dt = time.perf_counter() - t0
+    return p.n * R_s * K_s / dt, dt
+
+
+# ----------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self, gpu_index: int = 0) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sms, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    if int(parts[0]) != gpu_index:
+                        continue
+                    sms.append(float(parts[1]))
+                    mx = float(parts[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sms) if sms else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sms)}
+
+
+# ----------------------------------------------------------------------------- our arm
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2501_19221_gb300 import binding as B
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    w = workload(args.workload)
+    n, R, K = w["n"], w["R"], w["K"]
+    stream = torch.cuda.Stream()
+    ctx = create(B, w)
+    B.veloxq_set_stream(ctx, stream.cuda_stream)
+    sched = B.make_schedule(readout_every=w["readout_every"])
+    info = ctx.info
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    seed0 = 1000 * rank
+    with torch.cuda.stream(stream):
+        for i in range(args.warmup):
+            B.veloxq_solve(ctx, R, K, sched, seed=seed0 + i)
+        torch.cuda.synchronize()
+        clocks = ClockSampler()
+        if rank == 0:
+            clocks.start()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        mains, launches, results = [], 0, []
+        wall0 = time.perf_counter()
+        for i in range(args.steps):
+            flush.add_(1.0)                                # write > L2 between timed steps (not timed)
+            ev[i][0].record(stream)
+            out = B.veloxq_solve(ctx, R, K, sched, seed=seed0 + args.warmup + i, want_x=(i == args.steps - 1))
+            ev[i][1].record(stream)
+            t = B.veloxq_last_timing(ctx)
+            mains.append(t.ms_main)
+            launches += t.launches
+            results.append(out["E"])
+            main_launches, path = t.main_launches, t.path
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+        if dist is not None:
+            dist.barrier()
+        clk = clocks.stop(0) if rank == 0 else None
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = sum(step_ms)
+    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+    if dist is not None:
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    total_ms = float(tmax.item())
+    value = world * n * R * K * args.steps / (total_ms / 1e3)
+
+    # ---- end to end through the public API from pinned host buffers ----
+    e2e_iters = max(1, min(args.steps, 5))
+    pinned = []
+    for a in input_arrays(w):
+        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+        pinned.append(t.numpy())
+    h2d = int(sum(a.nbytes for a in pinned))
+    if w["kind"] == "ising_csr":
+        pw = dict(w)
+        pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
+    else:
+        pw = dict(w, Q=pinned[0], c=pinned[1])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(e2e_iters):
+        c2 = create(B, pw)
+        o2 = B.veloxq_solve(c2, R, K, sched, seed=seed0 + 77 + i)
+        c2.destroy()
+    e2e_s = (time.perf_counter() - t0) / e2e_iters
+    d2h = n + 8 * R + 8 * R + 16 + 16     # x, E per replica, device best energies, argmin record, E/E_int
+    e2e = {"value": world * n * R * K / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+           "includes": "context creation (H2D copy, device ingest, power iteration) + solve + D2H of results"}
+
+    # ---- roofline of the dominant kernel ----
+    peaks, src = _peaks()
+    main_ms = statistics.mean(mains)
+    roof = None
+    if path == B.VELOXQ_PATH_RESIDENT:
+        nnz = info.nnz_field
+        smem_bytes = (nnz + 2 * n) * 4 * R * K           # neighbour reads + own read + own write, per launch
+        peak_gbs = SMEM_BYTES_PER_CLK_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        achieved = smem_bytes / (main_ms / 1e3) / 1e9
+        roof = {"kernel": "k_resident", "bound": "smem", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
+                "frac": achieved / peak_gbs, "traffic": None,
+                "peak_source": f"derived: {SMEM_BYTES_PER_CLK_PER_SM} B/clk/SM x {NUM_SMS} SMs x "
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
+                "algorithmic_bytes_per_launch": smem_bytes, "ms_per_launch": main_ms}
+    else:
+        nnz = info.nnz_field
+        hbm_bytes = (16 * n * R + 5 * nnz + 8 * (n + 1)) * K   # state r/w + int8 CSR + rowptr per step
+        achieved = hbm_bytes / (main_ms / 1e3) / 1e9
+        roof = {"kernel": "k_stream_step", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": f"{src} hbm_gbs", "algorithmic_bytes_per_launch": hbm_bytes / K,
+                "ms_per_launch": main_ms / max(1, main_launches)}
+
+    # ---- CPU baseline: the oracle, single thread, bounded sample ----
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # calibrate on a short run, then time about 12 s of oracle work
+        R_s = min(R, 64)
+        rate0, _ = oracle_sample_rate(w, min(R, 4), min(K, 20))
+        K_s2 = int(min(K, max(20, 12.0 * rate0 / (n * R_s))))
+        rate, dt = oracle_sample_rate(w, R_s, K_s2)
+        cpu = {"value": rate, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+               "sample": f"{R_s} replicas x first {K_s2} of {K} steps of the same instance, FP64, one thread "
+                         f"({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w["name"], "instance": w["desc"], "n": n, "nnz_field": info.nnz_field,
+                       "replicas": R, "integration_steps": K, "readout_every": w["readout_every"],
+                       "path": {1: "resident", 2: "stream", 3: "dense"}.get(path, str(path)),
+                       "l2": "flushed by a 256 MiB write before each timed step",
+                       "parallelism": f"replicas-only x{world}"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk,
+            "quality": {"best_energy_last_step": results[-1], "ising_offset": info.ising_offset,
+                        "best_ising_energy_last_step": 2 * results[-1] + info.ising_offset},
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+# ----------------------------------------------------------------------------- reference arm
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args.workload)
+    R_s, K_s = min(w["R"], 32), min(w["K"], 1000)
+    for _ in range(args.warmup):
+        oracle_sample_rate(w, R_s, min(K_s, 20))
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_sample_rate(w, R_s, K_s)
+        times.append(dt)
+    total = sum(times)
+    value = w["n"] * R_s * K_s * args.steps / total
+    sample = f"{R_s} replicas x first {K_s} of {w['K']} steps per step, FP64 oracle, one thread"
+    line = {"impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "instance": w["desc"], "n": w["n"], "replicas": w["R"],
+                       "integration_steps": w["K"], "readout_every": w["readout_every"]},
+            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="chimera_c16")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        world = max(world, 1)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -101,6 +101,16 @@ typedef struct {
     double ising_offset;    /* Ising contexts: H(s) = 2 E(x) + ising_offset; else 0 */
 } veloxq_info;
 
+/* Device timing of the last veloxq_solve on a context, from CUDA events
+ * recorded on the stream the kernels run on. */
+typedef struct {
+    double ms_total;        /* first to last kernel of the solve */
+    double ms_main;         /* the integration itself: the resident kernel, or the captured step loop */
+    int64_t launches;       /* kernels this library launched for the solve */
+    int32_t path;           /* veloxq_path that ran */
+    int32_t main_launches;  /* launches inside ms_main (1 for the resident kernel, else the step kernels) */
+} veloxq_timing;
+
 /* Fill *s with the defaults listed above. */
 void veloxq_schedule_default(veloxq_schedule* s);
 
@@ -151,8 +161,13 @@ const char* veloxq_last_error(void);
 /* Context facts (host struct written). */
 int veloxq_get_info(veloxq_ctx* ctx, veloxq_info* info);
 
-/* Change the stream later calls run on (a cudaStream_t, or NULL). */
+/* Change the stream later calls run on (a cudaStream_t, or NULL). A solve on
+ * a NULL stream runs on a stream the context owns, ordered after the legacy
+ * default stream; on a non-NULL stream it runs (and is graph-captured) there. */
 int veloxq_set_stream(veloxq_ctx* ctx, void* stream);
+
+/* Timing of the last veloxq_solve on ctx (EINVAL if none ran yet). */
+int veloxq_last_timing(veloxq_ctx* ctx, veloxq_timing* timing);
 
 /* ---------------------------------------------------------------------------
  * Solve (App. B dynamics, replicas evolved in parallel and the best kept;

@@ -283,6 +283,26 @@ def field(p: Problem, S: np.ndarray) -> np.ndarray:
     return F
 
 
+def field_dense_rows(Q: np.ndarray, S: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """F[:, rows] = Qoff[rows, :] S^T for a dense Q given as is (Qoff = the
+    off-diagonal part of (Q + Q^T)/2), in FP64 with a library matmul as the
+    product; for sampled rows of large instances. Returns [R][len(rows)]."""
+    Q = np.asarray(Q)
+    rows = np.asarray(rows)
+    Qs = 0.5 * (Q[rows, :].astype(np.float64) + Q[:, rows].T.astype(np.float64))
+    Qs[np.arange(rows.shape[0]), rows] = 0.0
+    return np.asarray(S, dtype=np.float64) @ Qs.T
+
+
+def abs_field_dense_rows(Q: np.ndarray, S: np.ndarray, rows: np.ndarray) -> np.ndarray:
+    """|Qoff|[rows, :] |S|^T, the scale of the rounding bound for field_dense_rows."""
+    Q = np.asarray(Q)
+    rows = np.asarray(rows)
+    Qs = 0.5 * np.abs(Q[rows, :].astype(np.float64) + Q[:, rows].T.astype(np.float64))
+    Qs[np.arange(rows.shape[0]), rows] = 0.0
+    return np.abs(np.asarray(S, dtype=np.float64)) @ Qs.T
+
+
 def abs_field(p: Problem, S: np.ndarray) -> np.ndarray:
     """|Qoff| |S|: the scale of the rounding error bound of F (same loop on |.|)."""
     q = Problem(p.n, p.er, p.ec, np.abs(p.ev), p.c)

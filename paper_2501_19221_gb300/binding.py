@@ -31,7 +31,7 @@ EXPORTED = [
     "veloxq_schedule_default", "veloxq_create_dense", "veloxq_create_csr", "veloxq_create_ising_dense",
     "veloxq_create_ising_csr", "veloxq_destroy", "veloxq_last_error", "veloxq_get_info", "veloxq_set_stream",
     "veloxq_solve", "veloxq_solve_batch", "veloxq_energy", "veloxq_energy_dev", "veloxq_init_state_dev",
-    "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad",
+    "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad", "veloxq_last_timing",
 ]
 
 
@@ -46,6 +46,11 @@ class Info(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int64), ("nnz_field", ctypes.c_int64), ("is_dense", ctypes.c_int32),
                 ("is_integer", ctypes.c_int32), ("rho", ctypes.c_double), ("K0", ctypes.c_double),
                 ("ising_offset", ctypes.c_double)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("ms_total", ctypes.c_double), ("ms_main", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("path", ctypes.c_int32), ("main_launches", ctypes.c_int32)]
 
 
 class VeloxqError(RuntimeError):
@@ -80,6 +85,7 @@ def _load():
         "veloxq_steps_dev": (I, [P, I32, I32, I32, I32, S, P, P, P]),
         "veloxq_spectral_radius": (I, [P, ctypes.POINTER(D)]),
         "veloxq_grad": (I, [P, I32, I32, S, U64, I32, P, P, P, P]),
+        "veloxq_last_timing": (I, [P, ctypes.POINTER(Timing)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -237,6 +243,12 @@ def veloxq_get_info(ctx: Context) -> Info:
 
 def veloxq_set_stream(ctx: Context, stream) -> None:
     _check(_lib.veloxq_set_stream(ctx.handle, stream))
+
+
+def veloxq_last_timing(ctx: Context) -> Timing:
+    t = Timing()
+    _check(_lib.veloxq_last_timing(ctx.handle, ctypes.byref(t)))
+    return t
 
 
 def veloxq_spectral_radius(ctx: Context) -> float:

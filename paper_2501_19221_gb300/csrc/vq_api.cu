@@ -51,11 +51,16 @@ int DevBuf::ensure(size_t b) {
 struct CtxExtra {
     cudaStream_t work = nullptr;
     cudaEvent_t ev = nullptr;
+    cudaEvent_t t0 = nullptr, t1 = nullptr, t2 = nullptr, t3 = nullptr;   // timing of the last solve
     std::vector<uint64_t> graph_key;
     cudaGraphExec_t graph = nullptr;
+    int64_t graph_launches = 0;
+    veloxq_timing timing{};
+    bool timed = false;
     ~CtxExtra() {
         if (graph) cudaGraphExecDestroy(graph);
-        if (ev) cudaEventDestroy(ev);
+        for (cudaEvent_t e : {ev, t0, t1, t2, t3})
+            if (e) cudaEventDestroy(e);
         if (work) cudaStreamDestroy(work);
     }
 };
@@ -128,21 +133,53 @@ int upload_schedule(veloxq_ctx* ctx, const RunParams& p) {
     return VELOXQ_OK;
 }
 
-veloxq_path choose_path(const veloxq_ctx* ctx, veloxq_path want, int32_t R) {
-    if (ctx->dense) return VELOXQ_PATH_DENSE;
-    if (want == VELOXQ_PATH_STREAM || want == VELOXQ_PATH_RESIDENT) return want;
-    return resident_fits(ctx, R, nullptr, nullptr, nullptr) ? VELOXQ_PATH_RESIDENT : VELOXQ_PATH_STREAM;
+veloxq_path choose_path(const veloxq_ctx* ctx, veloxq_path want, veloxq_prec prec, int32_t R) {
+    if (want != VELOXQ_PATH_AUTO) return want;
+    if (ctx->dense && prec != VELOXQ_PREC_FP32) return VELOXQ_PATH_DENSE;
+    if (resident_fits(ctx, R, nullptr, nullptr, nullptr)) return VELOXQ_PATH_RESIDENT;
+    return ctx->dense ? VELOXQ_PATH_DENSE : VELOXQ_PATH_STREAM;
 }
 
 int check_path(const veloxq_ctx* ctx, veloxq_path path, veloxq_prec prec, int32_t R) {
     if (path == VELOXQ_PATH_DENSE && !ctx->dense) return fail(VELOXQ_EUNSUPPORTED, "dense path requested for a sparse context");
-    if (ctx->dense && path != VELOXQ_PATH_DENSE && path != VELOXQ_PATH_AUTO)
-        return fail(VELOXQ_EUNSUPPORTED, "sparse path requested for a dense context");
+    if ((path == VELOXQ_PATH_STREAM || path == VELOXQ_PATH_RESIDENT) && !ctx->has_csr)
+        return fail(VELOXQ_EUNSUPPORTED, "sparse-row path requested for a dense context without CSR rows (n > 512)");
+    if ((path == VELOXQ_PATH_STREAM || path == VELOXQ_PATH_RESIDENT) && prec != VELOXQ_PREC_FP32)
+        return fail(VELOXQ_EUNSUPPORTED, "the sparse-row kernels run the field in FP32");
     if (path == VELOXQ_PATH_RESIDENT && !resident_fits(ctx, R, nullptr, nullptr, nullptr))
         return fail(VELOXQ_EUNSUPPORTED, "instance does not fit the resident kernel");
-    if (prec != VELOXQ_PREC_FP32)
-        return fail(VELOXQ_EUNSUPPORTED, ctx->dense ? "BF16/FP8 dense field is not available in this build"
-                                                    : "sparse contexts run the field in FP32 (or exact int8)");
+    if (prec != VELOXQ_PREC_FP32 && !ctx->dense)
+        return fail(VELOXQ_EUNSUPPORTED, "sparse contexts run the field in FP32 (or exact int8)");
+    return VELOXQ_OK;
+}
+
+// Tensor-core operands of one run: quantised Q, two S operand buffers, maps.
+struct TcRun {
+    CUtensorMap mq, ms[2];
+    void* sop[2];
+};
+
+int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t) {
+    VQ_TRY(tc_prepare_q(ctx, prec));
+    const size_t b = tc_sop_bytes(ctx, prec, R);
+    VQ_TRY(ctx->sop_a.ensure(b));
+    VQ_TRY(ctx->sop_b.ensure(b));
+    VQ_TRY(ctx->errw.ensure(sizeof(int) * 4));
+    // the K padding columns [n, n_pad) of both operand buffers must stay zero:
+    // the epilogue never writes them
+    VQ_CUDA(cudaMemsetAsync(ctx->sop_a.p, 0, b, ctx->stream));
+    VQ_CUDA(cudaMemsetAsync(ctx->sop_b.p, 0, b, ctx->stream));
+    t->sop[0] = ctx->sop_a.p;
+    t->sop[1] = ctx->sop_b.p;
+    return tc_maps(ctx, prec, R, t->sop[0], t->sop[1], &t->mq, &t->ms[0], &t->ms[1]);
+}
+
+int check_err_word(veloxq_ctx* ctx) {
+    int h = 0;
+    VQ_CUDA(cudaMemcpyAsync(&h, ctx->errw.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    VQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h) return fail(VELOXQ_ETIMEDOUT, "a bounded device wait in the tensor-core kernel gave up (code " +
+                                             std::to_string(h) + ")");
     return VELOXQ_OK;
 }
 
@@ -151,7 +188,7 @@ bool is_readout(const RunParams& p, int k) {
 }
 
 // Enqueue the step loop (steps, readouts, argmin) on ctx->stream.
-int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts) {
+int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts, const TcRun* tc) {
     const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
     float* cur = ctx->s_a.as<float>();
     float* nxt = ctx->s_b.as<float>();
@@ -159,8 +196,15 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
     const float* at = ctx->a_table.as<float>();
     int np = nparts;
     for (int k = 0; k < p.K; ++k) {
-        if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
-        else VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+        if (tc) {
+            const int c = k & 1;   // operand of this step in sop[c], next one into sop[c ^ 1]
+            VQ_TRY(tc_step(ctx, p.prec, R, tc->mq, tc->ms[c], cur, nxt, Y, tc->sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
+                           nullptr, ctx->errw.as<int>()));
+        } else if (path == VELOXQ_PATH_DENSE) {
+            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+        } else {
+            VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+        }
         std::swap(cur, nxt);
         if (!is_readout(p, k)) continue;
         int64_t* parts = ctx->ework.as<int64_t>();
@@ -222,6 +266,10 @@ static int new_ctx(veloxq_ctx** out, int64_t n, void* stream, veloxq_ctx** made)
     auto ex = std::make_unique<CtxExtra>();
     e = cudaStreamCreateWithFlags(&ex->work, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ex->ev, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreate(&ex->t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ex->t1);
+    if (e == cudaSuccess) e = cudaEventCreate(&ex->t2);
+    if (e == cudaSuccess) e = cudaEventCreate(&ex->t3);
     if (e != cudaSuccess) {
         delete ctx;
         return cuda_fail(e, "stream creation");
@@ -300,6 +348,14 @@ int veloxq_set_stream(veloxq_ctx* ctx, void* stream) {
     return VELOXQ_OK;
 }
 
+int veloxq_last_timing(veloxq_ctx* ctx, veloxq_timing* timing) {
+    if (!ctx || !timing) return fail(VELOXQ_EINVAL, "ctx and timing must not be NULL");
+    CtxExtra* ex = extra(ctx);
+    if (!ex || !ex->timed) return fail(VELOXQ_EINVAL, "no solve has completed on this context");
+    *timing = ex->timing;
+    return VELOXQ_OK;
+}
+
 int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho) {
     if (!ctx || !rho) return fail(VELOXQ_EINVAL, "ctx and rho must not be NULL");
     *rho = ctx->rho;
@@ -314,31 +370,42 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
     if (E_best_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_best_int requires an integer-valued context");
     RunParams p;
     VQ_TRY(resolve(ctx, sched, steps, &p));
-    const veloxq_path path = choose_path(ctx, p.path, replicas);
+    const veloxq_path path = choose_path(ctx, p.path, p.prec, replicas);
     VQ_TRY(check_path(ctx, path, p.prec, replicas));
     CtxExtra* ex = extra(ctx);
     const int64_t n = ctx->n, R = replicas, nw = div_up(n, 32);
-    // run on the context's private stream, ordered after the caller's stream
+    // a NULL (legacy default) stream cannot be captured: run on the context's
+    // private stream, ordered after it
     cudaStream_t user = ctx->stream;
-    VQ_CUDA(cudaEventRecord(ex->ev, user));
-    VQ_CUDA(cudaStreamWaitEvent(ex->work, ex->ev, 0));
-    ctx->stream = ex->work;
+    if (user == nullptr) {
+        VQ_CUDA(cudaEventRecord(ex->ev, user));
+        VQ_CUDA(cudaStreamWaitEvent(ex->work, ex->ev, 0));
+        ctx->stream = ex->work;
+    }
     struct Restore {
         veloxq_ctx* c;
         cudaStream_t s;
         ~Restore() { c->stream = s; }
     } restore{ctx, user};
+    ex->timed = false;
+    int64_t launches = 0;
 
     VQ_TRY(upload_schedule(ctx, p));
     VQ_TRY(ctx->best_e.ensure(sizeof(int64_t) * R));
     VQ_TRY(ctx->best_bits.ensure(sizeof(uint32_t) * R * nw));
     VQ_TRY(ctx->misc.ensure(sizeof(int64_t) * 16));
     VQ_TRY(ctx->xout.ensure((size_t)n));
+    int32_t main_launches = 1;
     if (path == VELOXQ_PATH_RESIDENT) {
+        VQ_CUDA(cudaEventRecord(ex->t0, ctx->stream));
+        VQ_CUDA(cudaEventRecord(ex->t1, ctx->stream));
         VQ_TRY(resident_run(ctx, replicas, p, seed, 0, steps, nullptr, nullptr, nullptr, nullptr, nullptr,
                             ctx->best_e.as<int64_t>(), ctx->best_bits.as<uint32_t>()));
+        VQ_CUDA(cudaEventRecord(ex->t2, ctx->stream));
         VQ_TRY(launch_argmin_unpack(ctx, replicas, ctx->best_e.as<int64_t>(), ctx->best_bits.as<uint32_t>(),
                                     ctx->misc.as<int64_t>(), ctx->xout.as<uint8_t>()));
+        VQ_CUDA(cudaEventRecord(ex->t3, ctx->stream));
+        launches = 3;
     } else {
         const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
         const int nparts = stream_energy_parts_count(ctx, path, replicas);
@@ -347,11 +414,21 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         VQ_TRY(ctx->y.ensure(sizeof(float) * n * R));
         VQ_TRY(ctx->ework.ensure(sizeof(int64_t) * (size_t)nparts * R));
         VQ_TRY(ctx->flags.ensure((size_t)R));
+        TcRun tc;
+        const bool use_tc = path == VELOXQ_PATH_DENSE && p.prec != VELOXQ_PREC_FP32;
+        if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc));
+        VQ_CUDA(cudaEventRecord(ex->t0, ctx->stream));
         VQ_TRY(launch_init_state(ctx, replicas, seed, p.sigma0, lay, ctx->s_a.as<float>(), ctx->y.as<float>()));
+        if (use_tc) {
+            VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
+            VQ_TRY(tc_quant_s(ctx, p.prec, replicas, ctx->s_a.as<float>(), tc.sop[0]));
+        }
         VQ_CUDA(cudaMemsetAsync(ctx->best_e.p, 0x7f, sizeof(int64_t) * R, ctx->stream));
         VQ_CUDA(cudaMemsetAsync(ctx->best_bits.p, 0, sizeof(uint32_t) * R * nw, ctx->stream));
         // the captured loop depends on every pointer and parameter below
-        std::vector<uint64_t> key = {(uint64_t)path, (uint64_t)R, (uint64_t)steps, (uint64_t)p.readout_every,
+        std::vector<uint64_t> key = {(uint64_t)path, (uint64_t)p.prec, (uint64_t)(uintptr_t)ctx->sop_a.p,
+                                     (uint64_t)(uintptr_t)ctx->sop_b.p, (uint64_t)(uintptr_t)ctx->errw.p,
+                                     (uint64_t)R, (uint64_t)steps, (uint64_t)p.readout_every,
                                      (uint64_t)(uintptr_t)ctx->s_a.p, (uint64_t)(uintptr_t)ctx->s_b.p,
                                      (uint64_t)(uintptr_t)ctx->y.p, (uint64_t)(uintptr_t)ctx->ework.p,
                                      (uint64_t)(uintptr_t)ctx->best_e.p, (uint64_t)(uintptr_t)ctx->best_bits.p,
@@ -370,13 +447,15 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
             }
             cudaGraph_t g = nullptr;
             VQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            int st = enqueue_loop(ctx, path, replicas, p, nparts);
+            int st = enqueue_loop(ctx, path, replicas, p, nparts, use_tc ? &tc : nullptr);
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
             if (st != VELOXQ_OK) {
                 if (g) cudaGraphDestroy(g);
                 return st;
             }
             if (ce != cudaSuccess) return cuda_fail(ce, "graph capture");
+            size_t nodes = 0;
+            cudaGraphGetNodes(g, nullptr, &nodes);
             ce = cudaGraphInstantiate(&ex->graph, g, 0);
             cudaGraphDestroy(g);
             if (ce != cudaSuccess) {
@@ -384,8 +463,15 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
                 return cuda_fail(ce, "graph instantiate");
             }
             ex->graph_key = key;
+            ex->graph_launches = (int64_t)nodes;
         }
+        VQ_CUDA(cudaEventRecord(ex->t1, ctx->stream));
         VQ_CUDA(cudaGraphLaunch(ex->graph, ctx->stream));
+        VQ_CUDA(cudaEventRecord(ex->t2, ctx->stream));
+        VQ_CUDA(cudaEventRecord(ex->t3, ctx->stream));
+        launches = 1 + (use_tc ? 1 : 0) + ex->graph_launches;   // init (+ operand) kernels + graph nodes
+        main_launches = steps;
+        if (use_tc) VQ_TRY(check_err_word(ctx));
     }
     std::vector<int64_t> be((size_t)R);
     int64_t misc[2] = {0, 0};
@@ -394,6 +480,17 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
     if (x_best) VQ_CUDA(cudaMemcpyAsync(x_best, ctx->xout.p, (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
     VQ_CUDA(cudaStreamSynchronize(ctx->stream));
     VQ_LAUNCH_CHECK("solve");
+    {
+        float a = 0.f, b = 0.f;
+        VQ_CUDA(cudaEventElapsedTime(&a, ex->t0, ex->t3));
+        VQ_CUDA(cudaEventElapsedTime(&b, ex->t1, ex->t2));
+        ex->timing.ms_total = a;
+        ex->timing.ms_main = b;
+        ex->timing.launches = launches;
+        ex->timing.path = (int32_t)path;
+        ex->timing.main_launches = main_launches;
+        ex->timed = true;
+    }
     const int sh = ctx->energy_shift;
     if (E_best) *E_best = std::ldexp((double)misc[1], -sh);
     if (E_best_int) *E_best_int = misc[1] >> sh;
@@ -467,8 +564,14 @@ int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* 
     if (R < 1 || !S || !F) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, F required");
     if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
     if (ctx->dense) {
-        if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "BF16/FP8 dense field is not available in this build");
-        return dense_field(ctx, R, S, F);
+        if (prec == VELOXQ_PREC_FP32) return dense_field(ctx, R, S, F);
+        TcRun tc;
+        VQ_TRY(tc_setup(ctx, prec, R, &tc));
+        VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
+        VQ_TRY(tc_quant_s(ctx, prec, R, S, tc.sop[0]));
+        VQ_TRY(tc_step(ctx, prec, R, tc.mq, tc.ms[0], S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F,
+                       ctx->errw.as<int>()));
+        return check_err_word(ctx);
     }
     if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "sparse contexts run the field in FP32 (or exact int8)");
     const int64_t nR = ctx->n * (int64_t)R;
@@ -488,7 +591,7 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
     if (k_count == 0) return VELOXQ_OK;
     RunParams p;
     VQ_TRY(resolve(ctx, sched, K, &p));
-    const veloxq_path path = choose_path(ctx, p.path, R);
+    const veloxq_path path = choose_path(ctx, p.path, p.prec, R);
     VQ_TRY(check_path(ctx, path, p.prec, R));
     VQ_TRY(upload_schedule(ctx, p));
     const int64_t n = ctx->n, nR = n * (int64_t)R;
@@ -502,6 +605,21 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
     float* nxt = ctx->s_b.as<float>();
     if (path == VELOXQ_PATH_DENSE) {
         VQ_CUDA(cudaMemcpyAsync(cur, S, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
+        if (p.prec != VELOXQ_PREC_FP32) {
+            TcRun tc;
+            VQ_TRY(tc_setup(ctx, p.prec, R, &tc));
+            VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
+            VQ_TRY(tc_quant_s(ctx, p.prec, R, cur, tc.sop[0]));
+            int c = 0;
+            for (int k = k_begin; k < k_end; ++k) {
+                VQ_TRY(tc_step(ctx, p.prec, R, tc.mq, tc.ms[c], cur, nxt, Y, tc.sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
+                               k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>()));
+                std::swap(cur, nxt);
+                c ^= 1;
+            }
+            VQ_CUDA(cudaMemcpyAsync(S, cur, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
+            return check_err_word(ctx);
+        }
         for (int k = k_begin; k < k_end; ++k) {
             VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, k == k_end - 1 ? F_last : nullptr));
             std::swap(cur, nxt);

@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
 }
 
 template <typename QT> __device__ __forceinline__ int64_t qfix(QT q, int shift);
-template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int) { return (int64_t)q; }
-template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int) { return (int64_t)q; }
+template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int shift) { return (int64_t)q * (1ll << shift); }
+template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int shift) { return (int64_t)q * (1ll << shift); }
 template <> __device__ __forceinline__ int64_t qfix<float>(float q, int shift) {
     return __double2ll_rn((double)q * ldexp(1.0, shift));
 }

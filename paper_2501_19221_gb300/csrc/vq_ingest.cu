@@ -23,6 +23,7 @@ namespace vq {
 namespace {
 
 constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int64_t kDenseCsrMax = 512;   // dense instances up to this size also keep CSR rows
 constexpr int kRedThreads = 512;
 
 template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
@@ -148,6 +149,28 @@ __global__ void k_dense_qoff(const T* __restrict__ q, int64_t n, float* __restri
             const double v = 0.5 * (to_d(q[gi * n + gj]) + tile[threadIdx.x][r]);
             out[gi * n + gj] = (gi == gj) ? 0.0f : (float)v;
         }
+    }
+}
+
+// Rows of Qoff of a small dense instance as CSR (every off-diagonal entry):
+// wf = Qoff_ij (field operand), wfix = round((Q_ij + Q_ji)/2 2^S) (real energies).
+template <typename T>
+__global__ void k_dense_to_csr(const T* __restrict__ q, int64_t n, const float* __restrict__ qoff, int shift,
+                               int64_t* rp, int32_t* col, float* wf, int64_t* wfix, unsigned long long* maxw2) {
+    const int64_t i = blockIdx.x;
+    if (threadIdx.x == 0) {
+        rp[i] = i * (n - 1);
+        if (i == n - 1) rp[n] = n * (n - 1);
+    }
+    const double scale = ldexp(1.0, shift);
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
+        if (j == i) continue;
+        const int64_t o = i * (n - 1) + (j < i ? j : j - 1);
+        col[o] = (int32_t)j;
+        wf[o] = qoff[i * n + j];
+        const double w2 = to_d(q[i * n + j]) + to_d(q[j * n + i]);
+        if (wfix) wfix[o] = __double2ll_rn(0.5 * w2 * scale);
+        else atomicMax(maxw2, (unsigned long long)fabs(w2));
     }
 }
 
@@ -387,8 +410,8 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     ctx->ising_offset = ising ? 0.5 * hs[0] - hs[4] : 0.0;
     const double Tsum = hs[2] + hs[3];
     if (integer) {
-        if (Tsum >= 9.0e18) return fail(VELOXQ_EUNSUPPORTED, "integer couplings too large for int64 energies");
-        ctx->energy_shift = 0;
+        if (Tsum >= 4.0e18) return fail(VELOXQ_EUNSUPPORTED, "integer couplings too large for int64 energies");
+        ctx->energy_shift = 1;            // energies held as 2E, like sparse contexts (2 Qs is an integer)
     } else {
         int e = 0;
         std::frexp(Tsum > 0 ? Tsum : 1.0, &e);     // Tsum < 2^e
@@ -400,6 +423,27 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     VQ_CUDA(cudaStreamSynchronize(st));
     ctx->nnz = n * (n - 1);
     ctx->max_row = (int)(n - 1);
+    if (n <= kDenseCsrMax && n > 1) {
+        // small dense instances also get the rows of Qoff in CSR form so that
+        // the one-launch resident kernel can run them
+        const int64_t nnz = n * (n - 1);
+        VQ_TRY(ctx->rowptr.ensure(sizeof(int64_t) * (n + 1)));
+        VQ_TRY(ctx->col.ensure(sizeof(int32_t) * nnz));
+        VQ_TRY(ctx->wf.ensure(sizeof(float) * nnz));
+        if (!integer) VQ_TRY(ctx->wfix.ensure(sizeof(int64_t) * nnz));
+        unsigned long long* dmax = (unsigned long long*)(scal + 6);
+        VQ_CUDA(cudaMemsetAsync(dmax, 0, sizeof(unsigned long long), st));
+        k_dense_to_csr<T><<<(unsigned)n, 256, 0, st>>>(q, n, ctx->qoff32.as<float>(), ctx->energy_shift,
+                                                        ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                        ctx->wf.as<float>(), integer ? nullptr : ctx->wfix.as<int64_t>(),
+                                                        dmax);
+        VQ_LAUNCH_CHECK("dense to csr");
+        unsigned long long hm = 0;
+        VQ_CUDA(cudaMemcpyAsync(&hm, dmax, sizeof(hm), cudaMemcpyDeviceToHost, st));
+        VQ_CUDA(cudaStreamSynchronize(st));
+        ctx->has_csr = true;
+        ctx->wf_half_exact = integer && hm <= 2047;
+    }
     return VELOXQ_OK;
 }
 
@@ -506,6 +550,7 @@ int ingest_csr_t(veloxq_ctx* ctx, const int64_t* rph, const int32_t* colh, const
         ctx->energy_shift = std::max(0, std::min(200, 61 - e));
     }
     const bool use8 = integer && hmaxw <= 127;
+    ctx->wf_half_exact = integer && hmaxw <= 2047;
     VQ_TRY(ctx->col.ensure(sizeof(int32_t) * std::max<int64_t>(nnz_f, 1)));
     VQ_TRY(ctx->wf.ensure(sizeof(float) * std::max<int64_t>(nnz_f, 1)));
     if (use8) {
@@ -565,6 +610,7 @@ int ingest_dense(veloxq_ctx* ctx, veloxq_vtype vt, const void* Qh, const double*
 int ingest_csr(veloxq_ctx* ctx, const int64_t* rowptr, const int32_t* col, veloxq_vtype vt, const void* val,
                const double* ch, bool ising) {
     ctx->dense = false;
+    ctx->has_csr = true;
     bool integer = (vt == VELOXQ_I8 || vt == VELOXQ_I32);
     if (integer && ch)
         for (int64_t i = 0; i < ctx->n; ++i)

@@ -1,6 +1,7 @@
 // vq_internal.cuh -- internal declarations of libveloxq (not part of the ABI).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -75,6 +76,7 @@ struct veloxq_ctx {
     cudaStream_t stream = nullptr;
     int64_t n = 0;
     bool dense = false;
+    bool has_csr = false;         // sparse rows of Qoff present (sparse contexts, small dense ones)
     bool integer = false;
     double K0 = 0.0;
     double rho = 0.0;
@@ -89,6 +91,7 @@ struct veloxq_ctx {
     vq::DevBuf w8;                // int8  [nnz]   2 Qs_ij when integer and |2Qs| <= 127
     vq::DevBuf wfix;              // int64 [nnz]   round(Qs_ij 2^S) (energy), when w8 is absent
     int max_row = 0;              // longest row of the field structure
+    bool wf_half_exact = false;   // every Qs_ij is an exact half (integer |2 Qs| <= 2047)
 
     // ---- dense ----
     veloxq_vtype qx_type = VELOXQ_F32;
@@ -104,6 +107,8 @@ struct veloxq_ctx {
 
     // ---- scratch reused across calls ----
     vq::DevBuf s_a, s_b, y, f, ework, best_e, best_bits, flags, a_table, xout, misc;
+    vq::DevBuf sop_a, sop_b;      // tensor-core operand copies of S (ping-pong)
+    vq::DevBuf errw;              // device error word of bounded waits
 };
 
 namespace vq {
@@ -147,6 +152,17 @@ int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
 int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+
+// dense tensor-core kernels (vq_tc.cu)
+int64_t tc_pad(int64_t n);
+int tc_prepare_q(veloxq_ctx* ctx, int prec);
+int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtensorMap* mq, CUtensorMap* ms0,
+            CUtensorMap* ms1);
+int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop);
+size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R);
+int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
+            float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
+            float* F_out, int* err);
 int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
 
 }  // namespace vq

@@ -8,6 +8,8 @@
 // walls, readout, exact energy and best-so-far all stay on chip, with one
 // __syncthreads per step. Only the final best energies and bit vectors are
 // written to global memory.
+#include <cuda_fp16.h>
+
 #include <algorithm>
 
 #include "vq_internal.cuh"
@@ -38,33 +40,54 @@ struct ResArgs {
     uint32_t* best_bits;   // [R][nwords]
 };
 
-template <int RC> __device__ __forceinline__ void ld_vec(const float* p, float (&v)[RC]) {
-    if constexpr (RC == 8) {
-        const float4 a = *reinterpret_cast<const float4*>(p);
-        const float4 b = *reinterpret_cast<const float4*>(p + 4);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-    } else if constexpr (RC == 4) {
-        const float4 a = *reinterpret_cast<const float4*>(p);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+// Shared-memory layout of the positions: variable-major, RC replicas per
+// variable. For RC >= 4 the 16-byte chunks of a row are XOR-swizzled across
+// the 128-byte line by the line index, so rows 4 or 8 apart (the same
+// in-line position, as in Chimera cells) land on different banks.
+template <int RC> __device__ __forceinline__ int soff(int j, int h) {
+    if constexpr (RC >= 4) {
+        const int line = (j * RC) >> 5;
+        const int c = ((j * RC) >> 2) & 7;
+        return (line << 5) + ((((c + h) ^ line) & 7) << 2);
+    } else {
+        return j * RC;
+    }
+}
+template <int RC> __device__ __forceinline__ int selem(int j, int r) {
+    if constexpr (RC >= 4) return soff<RC>(j, r >> 2) + (r & 3);
+    else return j * RC + r;
+}
+template <int RC> __device__ __forceinline__ void ld_row(const float* s, int j, float (&v)[RC]) {
+    if constexpr (RC >= 4) {
+#pragma unroll
+        for (int h = 0; h < RC / 4; ++h) {
+            const float4 a = *reinterpret_cast<const float4*>(s + soff<RC>(j, h));
+            v[4 * h] = a.x; v[4 * h + 1] = a.y; v[4 * h + 2] = a.z; v[4 * h + 3] = a.w;
+        }
     } else if constexpr (RC == 2) {
-        const float2 a = *reinterpret_cast<const float2*>(p);
+        const float2 a = *reinterpret_cast<const float2*>(s + 2 * j);
         v[0] = a.x; v[1] = a.y;
     } else {
-        v[0] = *p;
+        v[0] = s[j];
     }
 }
-template <int RC> __device__ __forceinline__ void st_vec(float* p, const float (&v)[RC]) {
-    if constexpr (RC == 8) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-        *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
-    } else if constexpr (RC == 4) {
-        *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+template <int RC> __device__ __forceinline__ void st_row(float* s, int j, const float (&v)[RC]) {
+    if constexpr (RC >= 4) {
+#pragma unroll
+        for (int h = 0; h < RC / 4; ++h)
+            *reinterpret_cast<float4*>(s + soff<RC>(j, h)) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
     } else if constexpr (RC == 2) {
-        *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+        *reinterpret_cast<float2*>(s + 2 * j) = make_float2(v[0], v[1]);
     } else {
-        *p = v[0];
+        s[j] = v[0];
     }
 }
+
+// A coupling in shared memory: column (16 bits) and value. PACKED stores the
+// value as an exact half in the upper 16 bits of one word.
+template <bool PACKED> struct Ent;
+template <> struct Ent<true> { uint32_t w; };
+template <> struct Ent<false> { uint16_t c; };
 
 struct SmemPlan {
     size_t s0, s1, b, rp, col, val, bits, red, best, flag, total;
@@ -72,15 +95,17 @@ struct SmemPlan {
 
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 
-__host__ __device__ inline SmemPlan plan_smem(int n, int64_t nnz, int RC, int threads, int nwords, bool csr_smem) {
+__host__ __device__ inline SmemPlan plan_smem(int n, int64_t nnz, int RC, int threads, int nwords, bool csr_smem,
+                                              bool packed) {
     SmemPlan p;
     size_t o = 0;
-    p.s0 = o; o = align16(o + sizeof(float) * (size_t)n * RC);
-    p.s1 = o; o = align16(o + sizeof(float) * (size_t)n * RC);
+    const size_t rows = (size_t)((n * RC + 31) / 32 * 32);   // whole 128-byte lines (swizzle)
+    p.s0 = o; o = align16(o + sizeof(float) * rows);
+    p.s1 = o; o = align16(o + sizeof(float) * rows);
     p.b = o; o = align16(o + sizeof(float) * (size_t)n);
     p.rp = o; o = align16(o + (csr_smem ? sizeof(int32_t) * (size_t)(n + 1) : 0));
-    p.col = o; o = align16(o + (csr_smem ? sizeof(uint16_t) * (size_t)nnz : 0));
-    p.val = o; o = align16(o + (csr_smem ? sizeof(float) * (size_t)nnz : 0));
+    p.col = o; o = align16(o + (csr_smem ? (packed ? 4 : 2) * (size_t)nnz : 0));
+    p.val = o; o = align16(o + (csr_smem && !packed ? sizeof(float) * (size_t)nnz : 0));
     p.bits = o; o = align16(o + sizeof(uint32_t) * (size_t)RC * nwords);
     p.red = o; o = align16(o + sizeof(int64_t) * (size_t)(threads / 32) * RC);
     p.best = o; o = align16(o + sizeof(int64_t) * RC);
@@ -89,7 +114,7 @@ __host__ __device__ inline SmemPlan plan_smem(int n, int64_t nnz, int RC, int th
     return p;
 }
 
-template <int RC, int RPT, bool CSR_SMEM, int MAXT>
+template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT>
 __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n;
@@ -97,12 +122,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     const int r0 = blockIdx.x * RC;
-    const SmemPlan pl = plan_smem(n, CSR_SMEM ? a.rowptr[n] : 0, RC, T, a.nwords, CSR_SMEM);
+    const SmemPlan pl = plan_smem(n, CSR_SMEM ? a.rowptr[n] : 0, RC, T, a.nwords, CSR_SMEM, PACKED);
     float* sA = reinterpret_cast<float*>(smem + pl.s0);
     float* sB = reinterpret_cast<float*>(smem + pl.s1);
     float* bsh = reinterpret_cast<float*>(smem + pl.b);
     int32_t* rps = reinterpret_cast<int32_t*>(smem + pl.rp);
     uint16_t* cols = reinterpret_cast<uint16_t*>(smem + pl.col);
+    uint32_t* packs = reinterpret_cast<uint32_t*>(smem + pl.col);
     float* vals = reinterpret_cast<float*>(smem + pl.val);
     uint32_t* bits = reinterpret_cast<uint32_t*>(smem + pl.bits);
     int64_t* red = reinterpret_cast<int64_t*>(smem + pl.red);
@@ -115,8 +141,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
         const int64_t nnz = a.rowptr[n];
         for (int i = tid; i <= n; i += T) rps[i] = (int32_t)a.rowptr[i];
         for (int64_t p = tid; p < nnz; p += T) {
-            cols[p] = (uint16_t)a.col[p];
-            vals[p] = a.wf[p];
+            if constexpr (PACKED) {
+                packs[p] = (uint32_t)a.col[p] | ((uint32_t)__half_as_ushort(__float2half_rn(a.wf[p])) << 16);
+            } else {
+                cols[p] = (uint16_t)a.col[p];
+                vals[p] = a.wf[p];
+            }
         }
     }
     for (int w = tid; w < RC * a.nwords; w += T) bits[w] = 0u;
@@ -138,7 +168,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     vqd::init_pair(i, r0 + r, a.seed, a.sigma0, &s, &yv);
                 }
             }
-            if (i < n) sA[i * RC + r] = s;
+            if (i < n) sA[selem<RC>(i, r)] = s;
             y[q][r] = yv;
         }
     }
@@ -162,19 +192,28 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                 for (int p = p0; p < p1; ++p) {
                     int j;
                     float w;
-                    if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
-                    else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                    if constexpr (CSR_SMEM && PACKED) {
+                        const uint32_t e = packs[p];
+                        j = (int)(e & 0xFFFFu);
+                        w = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+                    } else if constexpr (CSR_SMEM) {
+                        j = cols[p];
+                        w = vals[p];
+                    } else {
+                        j = __ldg(a.col + p);
+                        w = __ldg(a.wf + p);
+                    }
                     float sj[RC];
-                    ld_vec<RC>(sc + j * RC, sj);
+                    ld_row<RC>(sc, j, sj);
 #pragma unroll
                     for (int r = 0; r < RC; ++r) acc[r] = fmaf(w, sj[r], acc[r]);
                 }
                 float s[RC];
-                ld_vec<RC>(sc + i * RC, s);
+                ld_row<RC>(sc, i, s);
                 const float b = bsh[i];
 #pragma unroll
                 for (int r = 0; r < RC; ++r) vqd::bsb_update(acc[r], b, a_k, a.dt, a.a0, a.c0, s[r], y[q][r]);
-                st_vec<RC>(sn + i * RC, s);
+                st_row<RC>(sn, i, s);
                 if (last && a.F_out) {
 #pragma unroll
                     for (int r = 0; r < RC; ++r)
@@ -197,7 +236,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             const int i = tid + q * T;
             if (i < n) {
                 float si[RC];
-                ld_vec<RC>(sc + i * RC, si);
+                ld_row<RC>(sc, i, si);
                 bool any = false;
 #pragma unroll
                 for (int r = 0; r < RC; ++r) any |= si[r] > 0.0f;
@@ -210,16 +249,22 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
                     for (int p = p0; p < p1; ++p) {
                         int j;
-                        int64_t wq;
-                        if constexpr (CSR_SMEM) j = cols[p]; else j = __ldg(a.col + p);
-                        if (a.wfix) wq = __ldg(a.wfix + p);
-                        else {
-                            float w;
-                            if constexpr (CSR_SMEM) w = vals[p]; else w = __ldg(a.wf + p);
-                            wq = (int64_t)__float2int_rn(2.0f * w);   // 2 Qs, exact for integer instances
+                        float w;
+                        if constexpr (CSR_SMEM && PACKED) {
+                            const uint32_t e = packs[p];
+                            j = (int)(e & 0xFFFFu);
+                            w = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
+                        } else if constexpr (CSR_SMEM) {
+                            j = cols[p];
+                            w = vals[p];
+                        } else {
+                            j = __ldg(a.col + p);
+                            w = __ldg(a.wf + p);
                         }
+                        // 2 Qs for integer instances (exact), the fixed-point weight otherwise
+                        const int64_t wq = a.wfix ? __ldg(a.wfix + p) : (int64_t)__float2int_rn(2.0f * w);
                         float sj[RC];
-                        ld_vec<RC>(sc + j * RC, sj);
+                        ld_row<RC>(sc, j, sj);
 #pragma unroll
                         for (int r = 0; r < RC; ++r) row[r] += sj[r] > 0.0f ? wq : 0;
                     }
@@ -254,7 +299,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r) {
                     if (!flag[r]) continue;
-                    const bool bit = (i < n) && sc[i * RC + r] > 0.0f;
+                    const bool bit = (i < n) && sc[selem<RC>(i, r)] > 0.0f;
                     const uint32_t word = __ballot_sync(0xffffffffu, bit);
                     if (lane == 0) bits[r * a.nwords + (base >> 5)] = word;
                 }
@@ -279,7 +324,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
 #pragma unroll
             for (int r = 0; r < RC; ++r)
                 if (r0 + r < a.R) {
-                    a.S_out[(int64_t)(r0 + r) * n + i] = sc[i * RC + r];
+                    a.S_out[(int64_t)(r0 + r) * n + i] = sc[selem<RC>(i, r)];
                     a.Y_out[(int64_t)(r0 + r) * n + i] = y[q][r];
                 }
         }
@@ -290,33 +335,34 @@ using KFn = void (*)(const ResArgs);
 
 // 1024-thread CTAs keep at most 8 momenta per thread in registers (64-register
 // cap); 512-thread CTAs up to 32.
-template <int RC, int RPT> KFn pick_csr(bool csr_smem) {
+template <int RC, int RPT> KFn pick_csr(bool csr_smem, bool packed) {
     constexpr int MAXT = (RC * RPT <= 8) ? 1024 : 512;
-    return csr_smem ? k_resident<RC, RPT, true, MAXT> : k_resident<RC, RPT, false, MAXT>;
+    if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT>;
+    return packed ? k_resident<RC, RPT, true, true, MAXT> : k_resident<RC, RPT, true, false, MAXT>;
 }
 
-template <int RC> KFn pick_rpt(int rpt, bool csr_smem) {
+template <int RC> KFn pick_rpt(int rpt, bool csr_smem, bool packed) {
     switch (rpt) {
-        case 1: return pick_csr<RC, 1>(csr_smem);
-        case 2: return pick_csr<RC, 2>(csr_smem);
-        case 4: return pick_csr<RC, 4>(csr_smem);
-        case 8: return pick_csr<RC, 8>(csr_smem);
-        default: return pick_csr<RC, 16>(csr_smem);
+        case 1: return pick_csr<RC, 1>(csr_smem, packed);
+        case 2: return pick_csr<RC, 2>(csr_smem, packed);
+        case 4: return pick_csr<RC, 4>(csr_smem, packed);
+        case 8: return pick_csr<RC, 8>(csr_smem, packed);
+        default: return pick_csr<RC, 16>(csr_smem, packed);
     }
 }
 
-KFn pick_kernel(int rc, int rpt, bool csr_smem) {
+KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed) {
     switch (rc) {
-        case 1: return pick_rpt<1>(rpt, csr_smem);
-        case 2: return pick_rpt<2>(rpt, csr_smem);
-        case 4: return pick_rpt<4>(rpt, csr_smem);
-        default: return pick_rpt<8>(rpt, csr_smem);
+        case 1: return pick_rpt<1>(rpt, csr_smem, packed);
+        case 2: return pick_rpt<2>(rpt, csr_smem, packed);
+        case 4: return pick_rpt<4>(rpt, csr_smem, packed);
+        default: return pick_rpt<8>(rpt, csr_smem, packed);
     }
 }
 
 struct ResPlan {
     int rc, threads, rpt;
-    bool csr_smem;
+    bool csr_smem, packed;
     size_t smem;
     bool ok;
 };
@@ -327,11 +373,15 @@ static int pow2_at_least(int v) {
     return p;
 }
 
+// Cost model: every SM runs ceil(CTAs / SMs) CTAs one after another or
+// interleaved, and a CTA step costs about (3 + RC) instructions per coupling
+// (the column and value loads are shared by its RC replicas).
 ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
-    ResPlan best{0, 0, 0, false, 0, false};
-    if (ctx->dense || ctx->n > 8192 || ctx->n < 1 || ctx->nnz >= (int64_t)1 << 31) return best;
+    ResPlan best{0, 0, 0, false, false, 0, false};
+    if (!ctx->has_csr || ctx->n > 8192 || ctx->n < 1 || ctx->nnz >= (int64_t)1 << 31) return best;
     const int n = (int)ctx->n;
     const int nwords = (int)div_up(n, 32);
+    const bool packed = ctx->wf_half_exact;
     double best_cost = 1e300;
     for (int rc : {8, 4, 2, 1}) {
         // threads: 1024 if each keeps <= 8 momenta, else 512 with <= 32
@@ -345,16 +395,13 @@ ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
         for (int cs = 1; cs >= 0; --cs) {
             const bool csr_smem = cs == 1 && ctx->n <= 65535;
             if (cs == 1 && !csr_smem) continue;
-            const SmemPlan p = plan_smem(n, csr_smem ? ctx->nnz : 0, rc, threads, nwords, csr_smem);
+            const SmemPlan p = plan_smem(n, csr_smem ? ctx->nnz : 0, rc, threads, nwords, csr_smem, csr_smem && packed);
             if (p.total > (size_t)kSmemMax) continue;
-            // cost ~ waves x replicas per CTA (one CTA per SM at these sizes)
             const int64_t ctas = div_up(R, rc);
-            const int per_sm = std::max(1, std::min((int)(kSmemMax / std::max<size_t>(p.total, 1)), 2048 / threads));
-            const int64_t waves = div_up(ctas, (int64_t)152 * per_sm);
-            const double cost = (double)waves * rc * (csr_smem ? 1.0 : 1.15);
+            const double cost = (double)div_up(ctas, 152) * (3.0 + rc) * (csr_smem ? 1.0 : 1.3);
             if (cost < best_cost - 1e-9) {
                 best_cost = cost;
-                best = ResPlan{rc, threads, rpt, csr_smem, p.total, true};
+                best = ResPlan{rc, threads, rpt, csr_smem, csr_smem && packed, p.total, true};
             }
             break;   // the CSR-in-shared-memory variant fits: prefer it for this rc
         }
@@ -404,7 +451,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed,
     a.F_out = F_out;
     a.best_e = best_e;
     a.best_bits = best_bits;
-    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem);
+    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed);
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     fn<<<(unsigned)div_up(R, p.rc), p.threads, p.smem, ctx->stream>>>(a);
     VQ_LAUNCH_CHECK("resident kernel");

@@ -49,29 +49,43 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
     if (i >= n) return;
     const int32_t v = (int32_t)(t - i * nvec);
     const int64_t off = (int64_t)v * V;
+    const int64_t me = i * R + off;
+    // the variable's own state first: independent of the couplings, in flight during the gathers
+    float s[V], y[V], b = 0.0f, a_k = 0.0f;
+    if constexpr (!FIELD_ONLY) {
+        vload<V>(S_cur + me, s);
+        vload_plain<V>(Y + me, y);
+        b = __ldg(bf + i);
+        a_k = __ldg(a_table + k);
+    }
     float acc[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) acc[l] = 0.0f;
-    const int64_t p1 = __ldg(rp + i + 1);
-    for (int64_t p = __ldg(rp + i); p < p1; ++p) {
-        const int64_t j = __ldg(col + p);
-        const float wv = wval(__ldg(w + p));
-        float sj[V];
-        vload<V>(S_cur + j * R + off, sj);
+    const int64_t p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    // four couplings per round: their gathers are issued together; a slot past
+    // the row end reads the variable itself with weight 0 (adds an exact 0)
+    for (int64_t p = p0; p < p1; p += 4) {
+        int64_t j[4];
+        float wv[4];
 #pragma unroll
-        for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
+        for (int u = 0; u < 4; ++u) {
+            const bool on = p + u < p1;
+            j[u] = on ? (int64_t)__ldg(col + p + u) : i;
+            wv[u] = on ? wval(__ldg(w + p + u)) : 0.0f;
+        }
+        float sj[4][V];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vload<V>(S_cur + j[u] * R + off, sj[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
     }
     float F[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) F[l] = acc[l] * wscale;     // wscale is 1 or 1/2: exact
-    const int64_t me = i * R + off;
     if (F_out) vstore<V>(F_out + me, F);
     if constexpr (FIELD_ONLY) return;
-    float s[V], y[V];
-    vload<V>(S_cur + me, s);
-    vload_plain<V>(Y + me, y);
-    const float b = __ldg(bf + i);
-    const float a_k = __ldg(a_table + k);
 #pragma unroll
     for (int l = 0; l < V; ++l) vqd::bsb_update(F[l], b, a_k, dt, a0, c0, s[l], y[l]);
     vstore<V>(S_nxt + me, s);

@@ -1,0 +1,430 @@
+// vq_tc.cu -- dense local field F = Qoff S on the 5th-generation tensor cores
+// (tcgen05, accumulators in tensor memory), operands staged by TMA, with the
+// ballistic-SB update fused into the epilogue.
+//
+// D[i][r] = sum_j Qop[i][j] Sop[r][j]: M = variables (rows of Qoff), N =
+// replicas, K = variables. Both operands are K-major (Qoff row-major, S
+// replica-major), tiles of 128 x 256 per CTA, 128-byte K blocks with the
+// 128-byte swizzle, a 4-stage TMA -> MMA pipeline.
+//   BF16: Qop = bf16(Qoff), Sop = bf16(s)                (kind::f16)
+//   FP8 : Qop = e4m3(Qoff_ij / q_i), q_i = amax_i / 448,
+//         Sop = e4m3(448 s)  (|s| <= 1 by the walls)       (kind::f8f6f4)
+//         F_i = acc q_i / 448
+// Warp roles: warp 0 issues TMA, warp 1 allocates tensor memory and issues
+// the MMAs, warps 2-5 read the accumulator tile (one 32-lane quarter each)
+// and run the update for their rows. Every wait is bounded: on timeout the
+// kernel records a code in the error word and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+#include <cuda_fp8.h>
+
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace {
+
+constexpr int BM = 128, BN = 256, BKB = 128, STAGES = 4;
+constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BN * BKB, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
+
+enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait: false (and the error word set) if the phase does not complete
+// within the budget or another thread already gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+    const long long t0 = clock64();
+    uint32_t spins = 0;
+    while (!mbar_try_wait(bar, parity)) {
+        if ((++spins & 1023u) == 0) {
+            if (*(volatile int*)err) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                atomicOr(err, code);
+                return false;
+            }
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
+// core groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+    const uint32_t a = smem_u32(p);
+    uint64_t d = 0;
+    d |= (uint64_t)((a & 0x3FFFFu) >> 4);          // start address
+    d |= (uint64_t)1 << 16;                         // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;               // stride byte offset
+    d |= (uint64_t)1 << 46;                         // descriptor version
+    d |= (uint64_t)2 << 61;                         // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor: FP32 accumulator, A/B format, K-major, N, M.
+template <int PREC> __host__ __device__ constexpr uint32_t instr_desc() {
+    return (1u << 4)                                   // D format F32
+           | ((PREC == 1 ? 1u : 0u) << 7)              // A: BF16 (f16 kind) / E4M3 (f8f6f4 kind)
+           | ((PREC == 1 ? 1u : 0u) << 10)             // B: same
+           | ((uint32_t)(BN >> 3) << 17)               // N
+           | ((uint32_t)(BM >> 4) << 24);              // M
+}
+
+template <int PREC>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
+    if constexpr (PREC == 1) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
+            ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
+            : "memory");
+    }
+}
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+struct TcArgs {
+    int32_t n, R, n_pad, k;
+    float dt, a0, c0;
+    const float* S_cur;      // [R][n] fp32
+    float* S_nxt;            // [R][n] fp32 (null: field only)
+    float* Y;                // [R][n]
+    void* sop_nxt;           // [R][n_pad] operand of the next step (null: do not write)
+    const float* bf;         // [n]
+    const float* qscale;     // [n] FP8 row scales (FP8 only)
+    const float* a_table;
+    float* F_out;            // [R][n] or null
+    int* err;
+};
+
+template <int PREC> __device__ __forceinline__ void store_op(void* base, int64_t idx, float s) {
+    if constexpr (PREC == 1) {
+        reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(s);
+    } else {
+        reinterpret_cast<__nv_fp8_storage_t*>(base)[idx] =
+            __nv_cvt_float_to_fp8(448.0f * s, __NV_SATFINITE, __NV_E4M3);
+    }
+}
+
+template <int PREC, bool FIELD_ONLY>
+__global__ void __launch_bounds__(192, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    constexpr int EB = PREC == 1 ? 2 : 1;
+    constexpr int BK = BKB / EB;                 // elements per K block
+    constexpr int KSTEP_B = 32;                  // bytes of K per MMA (16 bf16 / 32 e4m3)
+    const int num_kb = (a.n_pad + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accf, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (warp == 1) tmem_alloc(tmem_slot, BN);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kb = 0; kb < num_kb; ++kb) {
+                const int s = kb % STAGES, u = kb / STAGES;
+                if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) break;
+                uint8_t* sa = smem + s * STAGE_BYTES;
+                mbar_expect_tx(&full[s], STAGE_BYTES);
+                tma_load_2d(sa, &tmA, kb * BK, m0, &full[s]);
+                tma_load_2d(sa + A_BYTES, &tmB, kb * BK, n0, &full[s]);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc<PREC>();
+            bool ok = true;
+            for (int kb = 0; kb < num_kb; ++kb) {
+                const int s = kb % STAGES, u = kb / STAGES;
+                if (!mbar_wait(&full[s], u & 1, a.err, TC_ERR_MMA)) { ok = false; break; }
+                tc_fence_after();
+                const uint8_t* sa = smem + s * STAGE_BYTES;
+#pragma unroll
+                for (int kk = 0; kk < BKB / KSTEP_B; ++kk)
+                    umma<PREC>(tmem, smem_desc(sa + kk * KSTEP_B), smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc,
+                               (kb | kk) != 0 ? 1u : 0u);
+                umma_commit(&empty[s]);
+            }
+            if (ok) umma_commit(accf);
+        }
+    } else {
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31
+        const int q = warp & 3;
+        const int row = m0 + q * 32 + lane;
+        if (mbar_wait(accf, 0, a.err, TC_ERR_EPILOGUE)) {
+            tc_fence_after();
+            const bool row_ok = row < a.n;
+            float fscale = 1.0f, b = 0.0f;
+            if (row_ok) {
+                if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
+                if constexpr (!FIELD_ONLY) b = __ldg(a.bf + row);
+            }
+            const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
+#pragma unroll 1
+            for (int c = 0; c < BN / 32; ++c) {
+                uint32_t v[32];
+                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
+                if (!row_ok) continue;
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int r = n0 + c * 32 + j;
+                    if (r >= a.R) break;
+                    const int64_t p = (int64_t)r * a.n + row;
+                    const float F = __uint_as_float(v[j]) * fscale;
+                    if (a.F_out) a.F_out[p] = F;
+                    if constexpr (!FIELD_ONLY) {
+                        float s = a.S_cur[p], y = a.Y[p];
+                        vqd::bsb_update(F, b, a_k, a.dt, a.a0, a.c0, s, y);
+                        a.S_nxt[p] = s;
+                        a.Y[p] = y;
+                        store_op<PREC>(a.sop_nxt, (int64_t)r * a.n_pad + row, s);
+                    }
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1) tmem_dealloc(tmem, BN);
+}
+
+// ---- operand preparation --------------------------------------------------
+__global__ void k_quant_q_bf16(int64_t n, int64_t n_pad, const float* __restrict__ q, __nv_bfloat16* out) {
+    const int64_t i = blockIdx.x;
+    for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x)
+        out[i * n_pad + j] = __float2bfloat16_rn(j < n ? q[i * n + j] : 0.0f);
+}
+
+// per-row scale q_i = amax_i / 448 (1 for an all-zero row), e4m3(Qoff_ij / q_i)
+__global__ void k_quant_q_fp8(int64_t n, int64_t n_pad, const float* __restrict__ q, __nv_fp8_storage_t* out,
+                              float* scale) {
+    __shared__ float sh[256];
+    const int64_t i = blockIdx.x;
+    float m = 0.0f;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) m = fmaxf(m, fabsf(q[i * n + j]));
+    sh[threadIdx.x] = m;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] = fmaxf(sh[threadIdx.x], sh[threadIdx.x + s]);
+        __syncthreads();
+    }
+    const float amax = sh[0];
+    const float sc = amax > 0.0f ? amax / 448.0f : 1.0f;
+    const float inv = 1.0f / sc;
+    for (int64_t j = threadIdx.x; j < n_pad; j += blockDim.x)
+        out[i * n_pad + j] = __nv_cvt_float_to_fp8(j < n ? q[i * n + j] * inv : 0.0f, __NV_SATFINITE, __NV_E4M3);
+    if (threadIdx.x == 0) scale[i] = sc;
+}
+
+template <int PREC>
+__global__ void k_quant_s(int64_t R, int64_t n, int64_t n_pad, const float* __restrict__ S, void* out) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= R * n_pad) return;
+    const int64_t r = t / n_pad, j = t - r * n_pad;
+    store_op<PREC>(out, t, j < n ? S[r * n + j] : 0.0f);
+}
+
+// ---- tensor maps ------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void* p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 2-D K-major operand [rows][n_pad], box {128 bytes of K, box_rows}
+int make_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, int box_rows) {
+    auto fn = encode_fn();
+    if (!fn) return fail(VELOXQ_EUNSUPPORTED, "cuTensorMapEncodeTiled is not available from the driver");
+    const int eb = prec == 1 ? 2 : 1;
+    cuuint64_t dims[2] = {(cuuint64_t)n_pad, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)(n_pad * eb)};
+    cuuint32_t box[2] = {(cuuint32_t)(BKB / eb), (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = fn(m, prec == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, base, dims,
+                    strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(VELOXQ_ECUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+    return VELOXQ_OK;
+}
+
+}  // namespace
+
+// ---- state kept per context ------------------------------------------------
+struct TcState {
+    int prec = 0;
+    int64_t n_pad = 0;
+    CUtensorMap mapQ;
+    int32_t R = 0;
+    void* sop[2] = {nullptr, nullptr};
+    CUtensorMap mapS[2];
+};
+
+int64_t tc_pad(int64_t n) { return (n + 15) / 16 * 16; }
+
+// Quantise Qoff once per precision (kept in the context).
+int tc_prepare_q(veloxq_ctx* ctx, int prec) {
+    const int64_t n = ctx->n, np = tc_pad(n);
+    cudaStream_t st = ctx->stream;
+    if (prec == VELOXQ_PREC_BF16) {
+        if (!ctx->qoff16.p) {
+            VQ_TRY(ctx->qoff16.ensure(sizeof(__nv_bfloat16) * (size_t)(n * np)));
+            k_quant_q_bf16<<<(unsigned)n, 256, 0, st>>>(n, np, ctx->qoff32.as<float>(), ctx->qoff16.as<__nv_bfloat16>());
+        }
+    } else {
+        if (!ctx->qoff8.p) {
+            VQ_TRY(ctx->qoff8.ensure((size_t)(n * np)));
+            VQ_TRY(ctx->qscale8.ensure(sizeof(float) * (size_t)n));
+            k_quant_q_fp8<<<(unsigned)n, 256, 0, st>>>(n, np, ctx->qoff32.as<float>(), ctx->qoff8.as<__nv_fp8_storage_t>(),
+                                                       ctx->qscale8.as<float>());
+        }
+    }
+    VQ_LAUNCH_CHECK("tc quantize Q");
+    return VELOXQ_OK;
+}
+
+// Tensor maps for Q and for the two S operand buffers (bufs: 2 x R x n_pad).
+int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtensorMap* mq, CUtensorMap* ms0,
+            CUtensorMap* ms1) {
+    const int64_t n = ctx->n, np = tc_pad(n);
+    void* qb = prec == VELOXQ_PREC_BF16 ? ctx->qoff16.p : ctx->qoff8.p;
+    VQ_TRY(make_map(mq, qb, prec, n, np, BM));
+    VQ_TRY(make_map(ms0, sop0, prec, R, np, BN));
+    if (sop1) VQ_TRY(make_map(ms1, sop1, prec, R, np, BN));
+    return VELOXQ_OK;
+}
+
+int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop) {
+    const int64_t n = ctx->n, np = tc_pad(n);
+    const int64_t total = (int64_t)R * np;
+    if (prec == VELOXQ_PREC_BF16)
+        k_quant_s<1><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop);
+    else
+        k_quant_s<2><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop);
+    VQ_LAUNCH_CHECK("tc quantize S");
+    return VELOXQ_OK;
+}
+
+size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R) {
+    return (size_t)R * (size_t)tc_pad(ctx->n) * (prec == VELOXQ_PREC_BF16 ? 2 : 1);
+}
+
+// One fused step (or the field only when S_nxt is null): reads Sop through
+// mapS_cur, writes the next operand into sop_nxt.
+int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
+            float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
+            float* F_out, int* err) {
+    TcArgs a;
+    a.n = (int32_t)ctx->n;
+    a.R = R;
+    a.n_pad = (int32_t)tc_pad(ctx->n);
+    a.k = k;
+    a.dt = dt;
+    a.a0 = a0;
+    a.c0 = c0;
+    a.S_cur = S_cur;
+    a.S_nxt = S_nxt;
+    a.Y = Y;
+    a.sop_nxt = sop_nxt;
+    a.bf = ctx->bf.as<float>();
+    a.qscale = ctx->qscale8.as<float>();
+    a.a_table = a_table;
+    a.F_out = F_out;
+    a.err = err;
+    dim3 grid((unsigned)div_up(ctx->n, BM), (unsigned)div_up(R, BN));
+    const bool field_only = S_nxt == nullptr;
+    void (*fn)(const CUtensorMap, const CUtensorMap, const TcArgs);
+    if (prec == VELOXQ_PREC_BF16) fn = field_only ? k_tc_step<1, true> : k_tc_step<1, false>;
+    else fn = field_only ? k_tc_step<2, true> : k_tc_step<2, false>;
+    VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
+    fn<<<grid, 192, TC_SMEM, ctx->stream>>>(mq, ms_cur, a);
+    VQ_LAUNCH_CHECK("tc step");
+    return VELOXQ_OK;
+}
+
+}  // namespace vq

@@ -347,7 +347,7 @@ def test_malformed_inputs_rejected(B):
     with pytest.raises(B.VeloxqError) as e:
         B.veloxq_create_csr(3, rp, bad_order, np.ones(4, np.int32))
     assert e.value.status == B.VELOXQ_EINVAL and "increasing" in e.value.message
-    asym = np.array([1, 2, 0, 0], dtype=np.int32)          # (0,2) has no (2,0)
+    asym = np.array([1, 2, 0, 1], dtype=np.int32)          # rows {1,2}, {0}, {1}: (0,2) has no (2,0)
     rp2 = np.array([0, 2, 3, 4], dtype=np.int64)
     with pytest.raises(B.VeloxqError) as e:
         B.veloxq_create_csr(3, rp2, asym, np.ones(4, np.int32))

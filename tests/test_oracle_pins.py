@@ -414,3 +414,17 @@ def test_sparse_ising_conversion_matches_dense_and_identity():
     H = np.array([O.ising_energy(np.triu(J, 1), h, s) for s in S])
     assert np.allclose(H, 2 * O.energy(p, X) + C, atol=1e-9)
     assert p.integer and O.energy(p, X).dtype == np.int64
+
+
+def test_field_dense_rows_equals_full_field():
+    """The sampled-rows form (library matmul) equals the full coordinate-list
+    field on a non-symmetric matrix (catches a transposed or undiagonalised
+    operand in either)."""
+    rng = np.random.default_rng(9)
+    n = 40
+    Q = rng.normal(size=(n, n))
+    S = rng.uniform(-1, 1, size=(5, n))
+    rows = np.array([0, 7, 39, 12])
+    full = O.field(O.problem_from_dense(Q), S)
+    assert np.allclose(O.field_dense_rows(Q, S, rows), full[:, rows], atol=1e-12)
+    assert np.all(O.abs_field_dense_rows(Q, S, rows) >= np.abs(full[:, rows]) - 1e-12)
