@@ -246,6 +246,10 @@ int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho);
 int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched,
                 uint64_t seed, int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa,
                 double* d_knots);
+/* (veloxq_grad, continued) Runs on the sparse-row path (CSR contexts);
+ * device memory: (ceil(steps/ckpt_every) + ckpt_every + 2) x 2 x replicas x n
+ * floats. Errors: EINVAL (replicas, steps or ckpt_every < 1, more than 64
+ * knots), EUNSUPPORTED (dense context), ENOMEM. */
 
 #ifdef __cplusplus
 }

@@ -414,6 +414,8 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         VQ_TRY(ctx->y.ensure(sizeof(float) * n * R));
         VQ_TRY(ctx->ework.ensure(sizeof(int64_t) * (size_t)nparts * R));
         VQ_TRY(ctx->flags.ensure((size_t)R));
+        if (path == VELOXQ_PATH_STREAM)
+            VQ_TRY(stream_autotune(ctx, replicas, ctx->s_a.as<float>(), ctx->s_b.as<float>(), ctx->y.as<float>()));
         TcRun tc;
         const bool use_tc = path == VELOXQ_PATH_DENSE && p.prec != VELOXQ_PREC_FP32;
         if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc));
@@ -644,10 +646,44 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
 
 int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                 int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa, double* d_knots) {
-    (void)replicas; (void)steps; (void)sched; (void)seed; (void)ckpt_every;
-    (void)loss; (void)d_dt; (void)d_kappa; (void)d_knots;
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    return fail(VELOXQ_EUNSUPPORTED, "gradient kernels are not available in this build");
+    if (replicas < 1 || steps < 1) return fail(VELOXQ_EINVAL, "replicas and steps must be >= 1");
+    if (ckpt_every < 1) return fail(VELOXQ_EINVAL, "ckpt_every must be >= 1");
+    RunParams p;
+    VQ_TRY(resolve(ctx, sched, steps, &p));
+    if (ctx->dense || !ctx->has_csr)
+        return fail(VELOXQ_EUNSUPPORTED, "the adjoint kernels run on sparse (CSR) contexts");
+    const int nk = (int)p.knots.size();
+    if (nk > 64) return fail(VELOXQ_EINVAL, "at most 64 schedule knots");
+    CtxExtra* ex = extra(ctx);
+    cudaStream_t user = ctx->stream;
+    if (user == nullptr) {
+        VQ_CUDA(cudaEventRecord(ex->ev, user));
+        VQ_CUDA(cudaStreamWaitEvent(ex->work, ex->ev, 0));
+        ctx->stream = ex->work;
+    }
+    struct Restore {
+        veloxq_ctx* c;
+        cudaStream_t s;
+        ~Restore() { c->stream = s; }
+    } restore{ctx, user};
+    VQ_TRY(upload_schedule(ctx, p));
+    const std::vector<float> a_host = schedule_table(p);
+    {
+        const size_t blk = sizeof(float) * (size_t)(ctx->n * (int64_t)replicas);
+        DevBuf t;
+        VQ_TRY(t.ensure(3 * blk));
+        VQ_TRY(stream_autotune(ctx, replicas, t.as<float>(), t.as<float>() + ctx->n * (int64_t)replicas,
+                               t.as<float>() + 2 * ctx->n * (int64_t)replicas));
+    }
+    double dc0 = 0.0;
+    VQ_TRY(adjoint_run(ctx, replicas, p, a_host, seed, ckpt_every, loss, d_dt, &dc0, d_knots, nk));
+    if (d_kappa) {
+        // c0 = kappa / rho(J) = 2 kappa / rho(Qoff) unless c0 was given
+        const bool given = sched && sched->c0 > 0;
+        *d_kappa = given ? dc0 : (ctx->rho > 1e-12 ? dc0 * 2.0 / ctx->rho : dc0);
+    }
+    return VELOXQ_OK;
 }
 
 }  // extern "C"

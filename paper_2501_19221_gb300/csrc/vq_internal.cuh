@@ -109,6 +109,8 @@ struct veloxq_ctx {
     vq::DevBuf s_a, s_b, y, f, ework, best_e, best_bits, flags, a_table, xout, misc;
     vq::DevBuf sop_a, sop_b;      // tensor-core operand copies of S (ping-pong)
     vq::DevBuf errw;              // device error word of bounded waits
+    int stream_unroll = 0;        // gather variant of the streaming kernels (0: not tuned yet)
+    int32_t stream_tuned_R = -1;  // replica count the variant was tuned for
 };
 
 namespace vq {
@@ -138,6 +140,10 @@ int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, fl
                 const float* a_table, int k, float dt, float a0, float c0, float* F_out);
 int stream_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
+int stream_step_y(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
+                  const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+int vec_width(int32_t R);
+int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y);
 
 // sparse resident kernel (vq_resident.cu)
 bool resident_fits(const veloxq_ctx* ctx, int32_t R, int* rc, int* threads, size_t* smem);
@@ -152,6 +158,10 @@ int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
 int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+
+// adjoint of the step (vq_adjoint.cu)
+int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vector<float>& a_host, uint64_t seed,
+                int32_t C, double* loss, double* d_dt, double* d_c0, double* d_knots, int n_knots);
 
 // dense tensor-core kernels (vq_tc.cu)
 int64_t tc_pad(int64_t n);
@@ -199,21 +209,100 @@ __device__ __forceinline__ void init_pair(int64_t i, int32_t r, uint64_t seed, f
     *y = __fmul_rn(sigma0, __fsub_rn(__fmul_rn(2.0f, uy), 1.0f));
 }
 
-// One ballistic-SB update of a single (variable, replica) given its field F.
-// Rounded operation by operation (no contraction) so that it is the same
-// arithmetic in every kernel that uses it.
+// The pieces of one ballistic-SB update before the wall: phi, the drive,
+// y-hat and s-hat. Rounded operation by operation (no contraction) so that
+// every kernel, the adjoint included, sees the same values.
+struct BsbPre {
+    float phi, drive, yh, sh;
+};
+// With t = F + b: drive = -(c0/2) t - (a0 - a_k) s as one fused multiply-add,
+// yh = y + dt drive and sh = s + (dt a0) yh likewise (explicit fmaf, the same
+// in every kernel).
+__device__ __forceinline__ BsbPre bsb_pre(float F, float b, float a_k, float dt, float a0, float c0, float s, float y) {
+    BsbPre o;
+    const float t = __fadd_rn(F, b);
+    o.phi = __fmul_rn(-0.5f, t);
+    const float nak = -__fsub_rn(a0, a_k);
+    o.drive = fmaf(__fmul_rn(-0.5f, c0), t, __fmul_rn(nak, s));
+    o.yh = fmaf(dt, o.drive, y);
+    o.sh = fmaf(__fmul_rn(dt, a0), o.yh, s);
+    return o;
+}
+
+// One ballistic-SB update of a single (variable, replica) given its field F:
+// y <- y + dt(-(a0 - a_k) s + c0 phi), s <- s + dt a0 y, wall at |s| > 1.
 __device__ __forceinline__ void bsb_update(float F, float b, float a_k, float dt, float a0, float c0,
                                            float& s, float& y) {
-    const float phi = __fmul_rn(-0.5f, __fadd_rn(F, b));
-    const float drive = __fadd_rn(__fmul_rn(-__fsub_rn(a0, a_k), s), __fmul_rn(c0, phi));
-    float yn = __fadd_rn(y, __fmul_rn(dt, drive));
-    float sn = __fadd_rn(s, __fmul_rn(__fmul_rn(dt, a0), yn));
-    if (fabsf(sn) > 1.0f) {
-        sn = copysignf(1.0f, sn);
-        yn = 0.0f;
+    const BsbPre o = bsb_pre(F, b, a_k, dt, a0, c0, s, y);
+    if (fabsf(o.sh) > 1.0f) {
+        s = copysignf(1.0f, o.sh);
+        y = 0.0f;
+    } else {
+        s = o.sh;
+        y = o.yh;
     }
-    s = sn;
-    y = yn;
+}
+
+// Vector loads/stores of V consecutive replicas.
+template <int V> __device__ __forceinline__ void vload(const float* p, float (&v)[V]) {
+    if constexpr (V == 4) { const float4 t = __ldg(reinterpret_cast<const float4*>(p)); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (V == 2) { const float2 t = __ldg(reinterpret_cast<const float2*>(p)); v[0] = t.x; v[1] = t.y; }
+    else { v[0] = __ldg(p); }
+}
+template <int V> __device__ __forceinline__ void vload_plain(const float* p, float (&v)[V]) {
+    if constexpr (V == 4) { const float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (V == 2) { const float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y; }
+    else { v[0] = *p; }
+}
+template <int V> __device__ __forceinline__ void vstore(float* p, const float (&v)[V]) {
+    if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    else if constexpr (V == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
+    else *p = v[0];
+}
+
+__device__ __forceinline__ float wval(float w) { return w; }
+__device__ __forceinline__ float wval(int8_t w) { return (float)w; }
+
+// acc_l = sum over the CSR row of i of w_p X[col_p][off + l] (variable-major
+// [n][R] block), accumulated in CSR order with fmaf. UNROLL = 4 takes four
+// couplings per round so that their gathers are in flight together (a slot
+// past the row end reads row i itself with weight 0 and adds an exact 0);
+// UNROLL = 1 is the plain loop. Both give the same sums.
+template <int V, typename WT, int UNROLL>
+__device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                                            const WT* __restrict__ w, const float* X, int32_t R, int64_t off,
+                                            int64_t i, float (&acc)[V]) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) acc[l] = 0.0f;
+    const int64_t p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    if constexpr (UNROLL == 1) {
+        for (int64_t p = p0; p < p1; ++p) {
+            const int64_t j = __ldg(col + p);
+            const float wv = wval(__ldg(w + p));
+            float sj[V];
+            vload<V>(X + j * R + off, sj);
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
+        }
+        return;
+    }
+    for (int64_t p = p0; p < p1; p += 4) {
+        int64_t j[4];
+        float wv[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool on = p + u < p1;
+            j[u] = on ? (int64_t)__ldg(col + p + u) : i;
+            wv[u] = on ? wval(__ldg(w + p + u)) : 0.0f;
+        }
+        float sj[4][V];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) vload<V>(X + j[u] * R + off, sj[u]);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
+    }
 }
 
 }  // namespace vqd

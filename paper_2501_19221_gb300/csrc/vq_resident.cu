@@ -71,6 +71,24 @@ template <int RC> __device__ __forceinline__ void ld_row(const float* s, int j, 
         v[0] = s[j];
     }
 }
+// The same load given the float offset of the row's first chunk (the second
+// chunk of an 8-replica row is at offset ^ 4: the chunk pair is XOR-swizzled
+// together).
+template <int RC> __device__ __forceinline__ void ld_row_at(const float* s, int o, float (&v)[RC]) {
+    if constexpr (RC == 8) {
+        const float4 a = *reinterpret_cast<const float4*>(s + o);
+        const float4 b = *reinterpret_cast<const float4*>(s + (o ^ 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (RC == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(s + o);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (RC == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(s + o);
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = s[o];
+    }
+}
 template <int RC> __device__ __forceinline__ void st_row(float* s, int j, const float (&v)[RC]) {
     if constexpr (RC >= 4) {
 #pragma unroll
@@ -142,7 +160,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
         for (int i = tid; i <= n; i += T) rps[i] = (int32_t)a.rowptr[i];
         for (int64_t p = tid; p < nnz; p += T) {
             if constexpr (PACKED) {
-                packs[p] = (uint32_t)a.col[p] | ((uint32_t)__half_as_ushort(__float2half_rn(a.wf[p])) << 16);
+                // low half: the float offset of the neighbour's first chunk in the state layout
+                packs[p] = (uint32_t)soff<RC>(a.col[p], 0) | ((uint32_t)__half_as_ushort(__float2half_rn(a.wf[p])) << 16);
             } else {
                 cols[p] = (uint16_t)a.col[p];
                 vals[p] = a.wf[p];
@@ -190,21 +209,18 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                 if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
                 else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
                 for (int p = p0; p < p1; ++p) {
-                    int j;
                     float w;
+                    float sj[RC];
                     if constexpr (CSR_SMEM && PACKED) {
                         const uint32_t e = packs[p];
-                        j = (int)(e & 0xFFFFu);
                         w = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
-                    } else if constexpr (CSR_SMEM) {
-                        j = cols[p];
-                        w = vals[p];
+                        ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
                     } else {
-                        j = __ldg(a.col + p);
-                        w = __ldg(a.wf + p);
+                        int j;
+                        if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
+                        else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                        ld_row<RC>(sc, j, sj);
                     }
-                    float sj[RC];
-                    ld_row<RC>(sc, j, sj);
 #pragma unroll
                     for (int r = 0; r < RC; ++r) acc[r] = fmaf(w, sj[r], acc[r]);
                 }
@@ -248,23 +264,20 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
                     else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
                     for (int p = p0; p < p1; ++p) {
-                        int j;
                         float w;
+                        float sj[RC];
                         if constexpr (CSR_SMEM && PACKED) {
                             const uint32_t e = packs[p];
-                            j = (int)(e & 0xFFFFu);
                             w = __half2float(__ushort_as_half((unsigned short)(e >> 16)));
-                        } else if constexpr (CSR_SMEM) {
-                            j = cols[p];
-                            w = vals[p];
+                            ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
                         } else {
-                            j = __ldg(a.col + p);
-                            w = __ldg(a.wf + p);
+                            int j;
+                            if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
+                            else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                            ld_row<RC>(sc, j, sj);
                         }
                         // 2 Qs for integer instances (exact), the fixed-point weight otherwise
                         const int64_t wq = a.wfix ? __ldg(a.wfix + p) : (int64_t)__float2int_rn(2.0f * w);
-                        float sj[RC];
-                        ld_row<RC>(sc, j, sj);
 #pragma unroll
                         for (int r = 0; r < RC; ++r) row[r] += sj[r] > 0.0f ? wq : 0;
                     }
@@ -381,7 +394,7 @@ ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
     if (!ctx->has_csr || ctx->n > 8192 || ctx->n < 1 || ctx->nnz >= (int64_t)1 << 31) return best;
     const int n = (int)ctx->n;
     const int nwords = (int)div_up(n, 32);
-    const bool packed = ctx->wf_half_exact;
+    const bool packed0 = ctx->wf_half_exact;
     double best_cost = 1e300;
     for (int rc : {8, 4, 2, 1}) {
         // threads: 1024 if each keeps <= 8 momenta, else 512 with <= 32
@@ -392,6 +405,8 @@ ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
             rpt = pow2_at_least((int)div_up(n, threads));
             if (rc * rpt > 32 || rpt > 16) continue;
         }
+        // packed words hold the row's float offset in 16 bits
+        const bool packed = packed0 && (int64_t)div_up((int64_t)n * rc, 32) * 32 <= 65536;
         for (int cs = 1; cs >= 0; --cs) {
             const bool csr_smem = cs == 1 && ctx->n <= 65535;
             if (cs == 1 && !csr_smem) continue;

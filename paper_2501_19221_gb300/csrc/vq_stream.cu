@@ -12,36 +12,18 @@ namespace vq {
 
 namespace {
 
-template <int V> struct VecT;
-template <> struct VecT<1> { using T = float; };
-template <> struct VecT<2> { using T = float2; };
-template <> struct VecT<4> { using T = float4; };
+using vqd::vload;
+using vqd::vload_plain;
+using vqd::vstore;
+using vqd::wval;
 
-template <int V> __device__ __forceinline__ void vload(const float* p, float (&v)[V]) {
-    if constexpr (V == 4) { const float4 t = __ldg(reinterpret_cast<const float4*>(p)); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
-    else if constexpr (V == 2) { const float2 t = __ldg(reinterpret_cast<const float2*>(p)); v[0] = t.x; v[1] = t.y; }
-    else { v[0] = __ldg(p); }
-}
-template <int V> __device__ __forceinline__ void vload_plain(const float* p, float (&v)[V]) {
-    if constexpr (V == 4) { const float4 t = *reinterpret_cast<const float4*>(p); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
-    else if constexpr (V == 2) { const float2 t = *reinterpret_cast<const float2*>(p); v[0] = t.x; v[1] = t.y; }
-    else { v[0] = *p; }
-}
-template <int V> __device__ __forceinline__ void vstore(float* p, const float (&v)[V]) {
-    if constexpr (V == 4) *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-    else if constexpr (V == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
-    else *p = v[0];
-}
-
-__device__ __forceinline__ float wval(float w) { return w; }
-__device__ __forceinline__ float wval(int8_t w) { return (float)w; }
-
-// One thread per (variable i, vector v of V replicas).
-template <int V, typename WT, bool FIELD_ONLY>
+// One thread per (variable i, vector v of V replicas). Y_in and Y_out may be
+// the same buffer (in-place update).
+template <int V, typename WT, bool FIELD_ONLY, int UNROLL>
 __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const WT* __restrict__ w,
                                                      float wscale, const float* __restrict__ S_cur,
-                                                     float* __restrict__ S_nxt, float* __restrict__ Y,
+                                                     float* __restrict__ S_nxt, const float* Y_in, float* Y_out,
                                                      const float* __restrict__ bf, const float* __restrict__ a_table,
                                                      int k, float dt, float a0, float c0, float* __restrict__ F_out) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,33 +36,12 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
     float s[V], y[V], b = 0.0f, a_k = 0.0f;
     if constexpr (!FIELD_ONLY) {
         vload<V>(S_cur + me, s);
-        vload_plain<V>(Y + me, y);
+        vload_plain<V>(Y_in + me, y);
         b = __ldg(bf + i);
         a_k = __ldg(a_table + k);
     }
     float acc[V];
-#pragma unroll
-    for (int l = 0; l < V; ++l) acc[l] = 0.0f;
-    const int64_t p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
-    // four couplings per round: their gathers are issued together; a slot past
-    // the row end reads the variable itself with weight 0 (adds an exact 0)
-    for (int64_t p = p0; p < p1; p += 4) {
-        int64_t j[4];
-        float wv[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const bool on = p + u < p1;
-            j[u] = on ? (int64_t)__ldg(col + p + u) : i;
-            wv[u] = on ? wval(__ldg(w + p + u)) : 0.0f;
-        }
-        float sj[4][V];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) vload<V>(S_cur + j[u] * R + off, sj[u]);
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
-    }
+    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S_cur, R, off, i, acc);
     float F[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) F[l] = acc[l] * wscale;     // wscale is 1 or 1/2: exact
@@ -89,7 +50,7 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
 #pragma unroll
     for (int l = 0; l < V; ++l) vqd::bsb_update(F[l], b, a_k, dt, a0, c0, s[l], y[l]);
     vstore<V>(S_nxt + me, s);
-    vstore<V>(Y + me, y);
+    vstore<V>(Y_out + me, y);
 }
 
 __device__ __forceinline__ int64_t ewval(int8_t w) { return (int64_t)w; }
@@ -177,11 +138,9 @@ __global__ void __launch_bounds__(256) k_sparse_energy_x(int64_t n, int64_t B, c
     if (threadIdx.x == 0) parts[(int64_t)blockIdx.x * B + b] = sh[0];
 }
 
-int vec_width(int32_t R) { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
-
 template <bool FIELD_ONLY>
-int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
-                float dt, float a0, float c0, float* F_out) {
+int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
+                const float* a_table, int k, float dt, float a0, float c0, float* F_out) {
     const int V = vec_width(R);
     const int32_t nvec = R / V;
     const int64_t total = ctx->n * (int64_t)nvec;
@@ -191,8 +150,15 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, fl
     const float* bf = ctx->bf.as<float>();
     cudaStream_t st = ctx->stream;
 #define VQ_STEP(VV, WT, WPTR, SC)                                                                                   \
-    k_stream_step<VV, WT, FIELD_ONLY><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, Y, bf,   \
-                                                         a_table, k, dt, a0, c0, F_out)
+    do {                                                                                                            \
+        if (unroll == 4)                                                                                            \
+            k_stream_step<VV, WT, FIELD_ONLY, 4><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
+                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out); \
+        else                                                                                                        \
+            k_stream_step<VV, WT, FIELD_ONLY, 1><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
+                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out); \
+    } while (0)
+    const int unroll = ctx->stream_unroll == 4 ? 4 : 1;
     if (ctx->w8.p) {
         const int8_t* w = ctx->w8.as<int8_t>();
         if (V == 4) VQ_STEP(4, int8_t, w, 0.5f); else if (V == 2) VQ_STEP(2, int8_t, w, 0.5f); else VQ_STEP(1, int8_t, w, 0.5f);
@@ -207,13 +173,52 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, fl
 
 }  // namespace
 
+int vec_width(int32_t R) { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
+
 int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
                 float dt, float a0, float c0, float* F_out) {
-    return launch_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out);
+    return launch_step<false>(ctx, R, S_cur, S_nxt, Y, Y, a_table, k, dt, a0, c0, F_out);
+}
+
+int stream_step_y(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
+                  const float* a_table, int k, float dt, float a0, float c0, float* F_out) {
+    return launch_step<false>(ctx, R, S_cur, S_nxt, Y_in, Y_out, a_table, k, dt, a0, c0, F_out);
 }
 
 int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
-    return launch_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+    return launch_step<true>(ctx, R, S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+}
+
+// Pick the gather variant of the streaming kernels for R replicas by timing
+// three steps of each on the caller's buffers (contents are overwritten).
+// Runs eagerly on ctx->stream; must not be called during stream capture.
+int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y) {
+    if (ctx->stream_unroll != 0 && ctx->stream_tuned_R == R) return VELOXQ_OK;
+    cudaEvent_t e0, e1;
+    VQ_CUDA(cudaEventCreate(&e0));
+    VQ_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int pick = 1;
+    VQ_TRY(launch_init_state(ctx, R, 1, 0.1f, LAYOUT_NR, S_a, Y));
+    const float* at = ctx->a_table.as<float>();
+    for (int u : {1, 4}) {
+        ctx->stream_unroll = u;
+        VQ_TRY(launch_step<false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr));   // warm
+        VQ_CUDA(cudaEventRecord(e0, ctx->stream));
+        for (int k = 0; k < 3; ++k)
+            VQ_TRY(launch_step<false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f,
+                                      nullptr));
+        VQ_CUDA(cudaEventRecord(e1, ctx->stream));
+        VQ_CUDA(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        VQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) { best = ms; pick = u; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->stream_unroll = pick;
+    ctx->stream_tuned_R = R;
+    return VELOXQ_OK;
 }
 
 // number of row groups (partial sums) used by stream_energy

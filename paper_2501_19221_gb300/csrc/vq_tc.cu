@@ -11,8 +11,8 @@
 //         Sop = e4m3(448 s)  (|s| <= 1 by the walls)       (kind::f8f6f4)
 //         F_i = acc q_i / 448
 // Warp roles: warp 0 issues TMA, warp 1 allocates tensor memory and issues
-// the MMAs, warps 2-5 read the accumulator tile (one 32-lane quarter each)
-// and run the update for their rows. Every wait is bounded: on timeout the
+// the MMAs, warps 2-9 read the accumulator tile (a 32-lane quarter and half
+// of the columns each) and run the update for their rows. Every wait is bounded: on timeout the
 // kernel records a code in the error word and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -143,6 +143,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
 struct TcArgs {
     int32_t n, R, n_pad, k;
     float dt, a0, c0;
@@ -167,7 +177,7 @@ template <int PREC> __device__ __forceinline__ void store_op(void* base, int64_t
 }
 
 template <int PREC, bool FIELD_ONLY>
-__global__ void __launch_bounds__(192, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
+__global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -227,36 +237,51 @@ __global__ void __launch_bounds__(192, 1) k_tc_step(const __grid_constant__ CUte
             if (ok) umma_commit(accf);
         }
     } else {
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31; the
+        // first four epilogue warps take columns [0, BN/2), the next four the rest
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row = m0 + q * 32 + lane;
+        const bool row_ok = row < a.n;
+        float fscale = 1.0f, b = 0.0f;
+        if (row_ok) {
+            if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
+            if constexpr (!FIELD_ONLY) b = __ldg(a.bf + row);
+        }
+        const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
         if (mbar_wait(accf, 0, a.err, TC_ERR_EPILOGUE)) {
             tc_fence_after();
-            const bool row_ok = row < a.n;
-            float fscale = 1.0f, b = 0.0f;
-            if (row_ok) {
-                if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
-                if constexpr (!FIELD_ONLY) b = __ldg(a.bf + row);
-            }
-            const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
+            constexpr int CW = 16;   // columns per tensor-memory load
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
-                uint32_t v[32];
-                tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * 32), v);
-                if (!row_ok) continue;
+            for (int c = half * (BN / (2 * CW)); c < (half + 1) * (BN / (2 * CW)); ++c) {
+                uint32_t v[CW];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * CW), v);
+                const int r0 = n0 + c * CW;
+                // every load of the chunk is issued before any use (no early exit)
+                float sv[CW], yv[CW];
+                if constexpr (!FIELD_ONLY) {
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int r = n0 + c * 32 + j;
-                    if (r >= a.R) break;
-                    const int64_t p = (int64_t)r * a.n + row;
+                    for (int j = 0; j < CW; ++j) {
+                        const bool ok = row_ok && r0 + j < a.R;
+                        const int64_t p = (int64_t)(r0 + j) * a.n + row;
+                        sv[j] = ok ? a.S_cur[p] : 0.0f;
+                        yv[j] = ok ? a.Y[p] : 0.0f;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < CW; ++j) {
+                    const bool ok = row_ok && r0 + j < a.R;
+                    const int64_t p = (int64_t)(r0 + j) * a.n + row;
                     const float F = __uint_as_float(v[j]) * fscale;
-                    if (a.F_out) a.F_out[p] = F;
+                    if (ok && a.F_out) a.F_out[p] = F;
                     if constexpr (!FIELD_ONLY) {
-                        float s = a.S_cur[p], y = a.Y[p];
+                        float s = sv[j], y = yv[j];
                         vqd::bsb_update(F, b, a_k, a.dt, a.a0, a.c0, s, y);
-                        a.S_nxt[p] = s;
-                        a.Y[p] = y;
-                        store_op<PREC>(a.sop_nxt, (int64_t)r * a.n_pad + row, s);
+                        if (ok) {
+                            a.S_nxt[p] = s;
+                            a.Y[p] = y;
+                            store_op<PREC>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row, s);
+                        }
                     }
                 }
             }
@@ -422,7 +447,7 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     if (prec == VELOXQ_PREC_BF16) fn = field_only ? k_tc_step<1, true> : k_tc_step<1, false>;
     else fn = field_only ? k_tc_step<2, true> : k_tc_step<2, false>;
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    fn<<<grid, 192, TC_SMEM, ctx->stream>>>(mq, ms_cur, a);
+    fn<<<grid, 320, TC_SMEM, ctx->stream>>>(mq, ms_cur, a);
     VQ_LAUNCH_CHECK("tc step");
     return VELOXQ_OK;
 }

@@ -1,0 +1,157 @@
+"""Adjoint of the unrolled integrator (veloxq_grad): against the FP64 oracle's
+reverse mode on small instances, invariance under the checkpoint interval,
+central finite differences of the GPU loss, and the autograd.Function used
+to tune the schedule."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_19221_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2501_19221_gb300 import binding
+    return binding
+
+
+def _report(key, value):
+    d = os.environ.get("VELOXQ_REPORT_DIR")
+    if not d:
+        return
+    os.makedirs(d, exist_ok=True)
+    path = os.path.join(d, "grad_report.json")
+    data = json.load(open(path)) if os.path.exists(path) else {}
+    data[key] = value
+    json.dump(data, open(path, "w"), indent=1, sort_keys=True)
+
+
+def _lattice(B, L, seed=2):
+    sp = I.cubic_lattice_ising(L, seed=seed)
+    ctx = B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+    p, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+    return ctx, p
+
+
+def _sparse_real(B):
+    sp = I.random_sparse_qubo(60, 5, seed=7, vtype=np.float64, empty_rows=2)
+    vals = sp.val * np.random.default_rng(3).uniform(0.4, 1.2, size=sp.val.shape)
+    c = np.random.default_rng(4).normal(size=sp.n) * 0.3
+    return (B.veloxq_create_csr(sp.n, sp.rowptr, sp.col, vals, c),
+            O.problem_from_csr(sp.n, sp.rowptr, sp.col, vals, c))
+
+
+def _rel(a, b):
+    return abs(a - b) / max(abs(b), 1e-12)
+
+
+@pytest.mark.parametrize("inst", ["lattice", "sparse_real"])
+@pytest.mark.parametrize("ckpt", [1, 7, 40])
+def test_grad_matches_oracle_reverse_mode(B, inst, ckpt):
+    ctx, p = _lattice(B, 4) if inst == "lattice" else _sparse_real(B)
+    R, K, seed = 8, 40, 5
+    dt, c0 = np.float32(0.35), np.float32(0.2)
+    knots = [0.0, 0.3, 0.7, 1.0]
+    kn32 = [float(np.float32(v)) for v in knots]
+    sched = B.make_schedule(dt=float(dt), c0=float(c0), knots=knots, sigma0=0.2, readout_every=0)
+    g = B.veloxq_grad(ctx, R, K, sched, seed, ckpt)
+    S0, Y0 = O.init_state(p.n, R, seed, 0.2)
+    ref = O.bsb_grad(p, R, K, float(dt), 1.0, float(c0), kn32, S0, Y0)
+    _report(f"oracle_{inst}_ckpt{ckpt}", {"loss": [g["loss"], ref["loss"]], "d_dt": [g["d_dt"], ref["d_dt"]],
+                                          "d_c0": [g["d_kappa"], ref["d_c0"]],
+                                          "d_knots": [list(g["d_knots"]), list(ref["d_knots"])]})
+    assert _rel(g["loss"], ref["loss"]) <= 1e-5
+    scale = max(abs(ref["d_dt"]), abs(ref["d_c0"]), np.max(np.abs(ref["d_knots"])))
+    assert abs(g["d_dt"] - ref["d_dt"]) <= 1e-3 * scale
+    assert abs(g["d_kappa"] - ref["d_c0"]) <= 1e-3 * scale        # c0 given: d_kappa is dL/dc0
+    assert np.all(np.abs(g["d_knots"] - ref["d_knots"]) <= 1e-3 * scale)
+
+
+def test_grad_independent_of_checkpoint_interval(B):
+    """Segments are recomputed with the same kernels: every interval gives the
+    same loss and gradient bit for bit."""
+    ctx, _ = _lattice(B, 10, seed=3)
+    sched = B.make_schedule(dt=0.4, knots=[0.0, 0.5, 1.0], readout_every=0)
+    outs = [B.veloxq_grad(ctx, 16, 90, sched, 1, c) for c in (1, 13, 20, 90, 200)]
+    for o in outs[1:]:
+        assert o["loss"] == outs[0]["loss"]
+        assert o["d_dt"] == outs[0]["d_dt"] and o["d_kappa"] == outs[0]["d_kappa"]
+        assert np.array_equal(o["d_knots"], outs[0]["d_knots"])
+
+
+def test_grad_default_kappa_chain_rule(B):
+    """With c0 derived from kappa, d_kappa = dL/dc0 * 2 / rho(Qoff)."""
+    ctx, _ = _lattice(B, 5)
+    rho = ctx.info.rho
+    kappa = 0.8
+    c0 = float(np.float32(2.0 * kappa / rho))
+    ga = B.veloxq_grad(ctx, 8, 30, B.make_schedule(kappa=kappa, readout_every=0), 2, 10)
+    gb = B.veloxq_grad(ctx, 8, 30, B.make_schedule(c0=c0, readout_every=0), 2, 10)
+    assert ga["loss"] == gb["loss"]
+    assert ga["d_kappa"] == pytest.approx(gb["d_kappa"] * 2.0 / rho, rel=1e-12)
+
+
+def test_grad_central_differences_on_gpu(B):
+    """A 20^3 lattice, 64 replicas, 120 steps: adjoint vs central differences
+    of the GPU loss. Wall events move under a finite perturbation, so the two
+    agree to a few percent, not to rounding; the agreement is recorded."""
+    ctx, _ = _lattice(B, 20, seed=1)
+    R, K, seed = 64, 120, 3
+    base = dict(dt=0.3, kappa=1.0, knots=[0.0, 0.6, 1.0], readout_every=0)
+    g = B.veloxq_grad(ctx, R, K, B.make_schedule(**base), seed, 20)
+
+    def loss(**over):
+        kw = dict(base)
+        kw.update(over)
+        return B.veloxq_grad(ctx, R, K, B.make_schedule(**kw), seed, 20)["loss"]
+
+    h = 1e-3
+    fd_dt = (loss(dt=base["dt"] + h) - loss(dt=base["dt"] - h)) / (2 * h)
+    fd_k = (loss(kappa=1.0 + h) - loss(kappa=1.0 - h)) / (2 * h)
+    kp = list(base["knots"])
+    km = list(base["knots"])
+    kp[1] += h
+    km[1] -= h
+    fd_kn1 = (loss(knots=kp) - loss(knots=km)) / (2 * h)
+    agree = {"d_dt": [g["d_dt"], fd_dt], "d_kappa": [g["d_kappa"], fd_k], "d_knot1": [g["d_knots"][1], fd_kn1]}
+    _report("central_differences_L20", agree)
+    for a, f in agree.values():
+        assert abs(a - f) <= 0.1 * max(abs(f), abs(a)) + 1e-6, agree
+
+
+def test_autograd_function_and_schedule_tuning(B):
+    """BSBRelaxedEnergy exposes the adjoint to torch; a few gradient steps on
+    dt and the knots lower the relaxed energy (schedule tuning)."""
+    from paper_2501_19221_gb300.autograd import BSBRelaxedEnergy
+    ctx, _ = _lattice(B, 8, seed=4)
+    dt = torch.tensor(0.25, dtype=torch.float64, requires_grad=True)
+    kappa = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    knots = torch.tensor([0.0, 0.5, 1.0], dtype=torch.float64, requires_grad=True)
+    L0 = BSBRelaxedEnergy.apply(dt, kappa, knots, ctx, 32, 60, 7, 10)
+    L0.backward()
+    g = B.veloxq_grad(ctx, 32, 60, B.make_schedule(dt=0.25, kappa=1.0, knots=[0.0, 0.5, 1.0], readout_every=0), 7, 10)
+    assert float(L0) == g["loss"]
+    assert float(dt.grad) == g["d_dt"] and float(kappa.grad) == g["d_kappa"]
+    assert np.allclose(knots.grad.numpy(), g["d_knots"])
+    opt = torch.optim.Adam([dt, knots], lr=0.01)
+    losses = [float(L0)]
+    for _ in range(8):
+        opt.zero_grad()
+        L = BSBRelaxedEnergy.apply(dt, kappa, knots, ctx, 32, 60, 7, 10)
+        L.backward()
+        opt.step()
+        with torch.no_grad():
+            dt.clamp_(0.05, 1.0)
+        losses.append(float(L))
+    _report("tuning_losses", losses)
+    assert min(losses[1:]) < losses[0]
