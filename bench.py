@@ -24,6 +24,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -62,6 +63,17 @@ def workload(name: str) -> dict:
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
                 "readout_every": 50, "desc": "periodic 3-D +-J lattice L=464 (n ~ 1e8), int8 CSR"}
+    if name == "wishart_b512":
+        sizes = I.wishart_sizes(512, 100, 2000, seed=0)
+        return {"name": name, "kind": "batch", "sizes": sizes, "n": int(sizes.sum()), "R": 64, "K": 1000,
+                "readout_every": 0, "prec": 1,
+                "desc": "512 Wishart planted instances, n_i uniform in [100, 2000], alpha 0.75, BF16 field"}
+    if name in ("sk_n8192_fp32", "sk_n8192_bf16", "sk_n8192_fp8"):
+        Q, c = I.sk_qubo(8192, seed=0)
+        prec = {"fp32": 0, "bf16": 1, "fp8": 2}[name.split("_")[-1]]
+        return {"name": name, "kind": "dense", "Q": Q, "c": c, "n": 8192, "R": 1024, "K": 200,
+                "readout_every": 0, "prec": prec,
+                "desc": f"SK n=8192, Q_ij ~ N(0,1)/sqrt(n), field in {name.split('_')[-1].upper()}"}
     if name == "dense_n20":
         Q, c = I.dense_int_qubo(20, seed=0)
         return {"name": name, "kind": "dense", "Q": Q, "c": c, "n": 20, "R": 128, "K": 2000,
@@ -69,10 +81,20 @@ def workload(name: str) -> dict:
     raise SystemExit(f"unknown workload {name}")
 
 
+def batch_instances(w):
+    """Wishart Ising couplings of the batch, as the Ising form -J (seeded per instance)."""
+    if "inst" not in w:
+        w["inst"] = [(-I.wishart_ising(int(n), 0.75, seed=1000 + m, dtype=np.float32)["J"]).astype(np.float32)
+                     for m, n in enumerate(w["sizes"])]
+    return w["inst"]
+
+
 def create(B, w, stream=None):
     if w["kind"] == "ising_csr":
         sp = w["sp"]
         return B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
+    if w["kind"] == "batch":
+        return [B.veloxq_create_ising_dense(J, None, stream) for J in batch_instances(w)]
     return B.veloxq_create_dense(w["Q"], w["c"], stream)
 
 
@@ -80,6 +102,8 @@ def input_arrays(w) -> list:
     if w["kind"] == "ising_csr":
         sp = w["sp"]
         return [sp.rowptr, sp.col, sp.val, sp.lin]
+    if w["kind"] == "batch":
+        return list(batch_instances(w))
     return [w["Q"], w["c"]]
 
 
@@ -116,11 +140,11 @@ class ClockSampler:
 
     def __init__(self):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        fd, self.path = tempfile.mkstemp(prefix="veloxq_clocks_", suffix=".csv")
+        os.close(fd)
 
     def start(self):
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.fh = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                                           "-lms", "200"], stdout=self.fh, stderr=subprocess.DEVNULL)
@@ -158,6 +182,79 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- our arm
+class Runner:
+    """One workload on the library: a context (or a batch of them) and a solve."""
+
+    def __init__(self, B, w, stream):
+        self.B, self.w = B, w
+        self.batch = w["kind"] == "batch"
+        made = create(B, w)
+        self.ctxs = made if self.batch else [made]
+        for c in self.ctxs:
+            B.veloxq_set_stream(c, stream.cuda_stream)
+        self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0))
+        self.n_total = sum(c.info.n for c in self.ctxs)
+        self.nnz_field = sum(c.info.nnz_field for c in self.ctxs)
+
+    def solve(self, seed, want_x=False):
+        if self.batch:
+            out = self.B.veloxq_solve_batch(self.ctxs, self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)
+            return float(np.min(out["E"]))
+        return self.B.veloxq_solve(self.ctxs[0], self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)["E"]
+
+    def timing(self):
+        return self.B.veloxq_last_timing(self.ctxs[0])
+
+    def destroy(self):
+        for c in self.ctxs:
+            c.destroy()
+
+
+def roofline(B, w, runner, path, main_ms, main_launches):
+    peaks, src = _peaks()
+    n, R, K = runner.n_total, w["R"], w["K"]
+    if runner.batch:
+        qbytes = sum(2 * int(m) * int(m) for m in w["sizes"])
+        hbm = K * (qbytes + 18 * n * R)              # BF16 Q streamed per step + state r/w + operand write
+        ach = hbm / (main_ms / 1e3) / 1e9
+        return {"kernel": "k_batch", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
+                "algorithmic_bytes_per_launch": hbm, "ms_per_launch": main_ms}
+    if path == B.VELOXQ_PATH_RESIDENT:
+        smem_bytes = (runner.nnz_field + 2 * n) * 4 * R * K
+        peak = SMEM_BYTES_PER_CLK_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+        ach = smem_bytes / (main_ms / 1e3) / 1e9
+        return {"kernel": "k_resident", "bound": "smem", "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"derived: {SMEM_BYTES_PER_CLK_PER_SM} B/clk/SM x {NUM_SMS} SMs x "
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
+                "algorithmic_bytes_per_launch": smem_bytes, "ms_per_launch": main_ms}
+    if path == B.VELOXQ_PATH_DENSE and w.get("prec", 0) in (1, 2):
+        flops = 2.0 * n * n * R
+        peak = peaks["bf16_tflops"] * (2.0 if w["prec"] == 2 else 1.0)
+        per = main_ms / K
+        ach = flops / (per / 1e3) / 1e12
+        return {"kernel": "k_tc_step", "bound": "tensor", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "peak_source": f"{src} bf16_tflops" + (" x 2 (FP8/BF16 nominal ratio)" if w["prec"] == 2 else ""),
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": per}
+    if path == B.VELOXQ_PATH_DENSE:
+        flops = 2.0 * n * n * R
+        per = main_ms / K
+        fp32_peak = NUM_SMS * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        ach = flops / (per / 1e3) / 1e12
+        return {"kernel": "k_dense_step", "bound": "alu", "achieved": ach, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": ach / fp32_peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x max clock",
+                "algorithmic_flops_per_launch": flops, "ms_per_launch": per}
+    hbm_bytes = 16 * n * R + 5 * runner.nnz_field + 8 * (n + 1)      # state r/w + int8 CSR + rowptr, per step
+    per = main_ms / max(1, main_launches)
+    ach = hbm_bytes / (per / 1e3) / 1e9
+    return {"kernel": "k_stream_step", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
+            "algorithmic_bytes_per_launch": hbm_bytes, "ms_per_launch": per}
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -170,17 +267,15 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = workload(args.workload)
-    n, R, K = w["n"], w["R"], w["K"]
+    R, K = w["R"], w["K"]
     stream = torch.cuda.Stream()
-    ctx = create(B, w)
-    B.veloxq_set_stream(ctx, stream.cuda_stream)
-    sched = B.make_schedule(readout_every=w["readout_every"])
-    info = ctx.info
+    run = Runner(B, w, stream)
+    n = run.n_total
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     seed0 = 1000 * rank
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
-            B.veloxq_solve(ctx, R, K, sched, seed=seed0 + i)
+            run.solve(seed0 + i)
         torch.cuda.synchronize()
         clocks = ClockSampler()
         if rank == 0:
@@ -194,12 +289,11 @@ def run_ours(args, rank, world, local_rank):
         for i in range(args.steps):
             flush.add_(1.0)                                # write > L2 between timed steps (not timed)
             ev[i][0].record(stream)
-            out = B.veloxq_solve(ctx, R, K, sched, seed=seed0 + args.warmup + i, want_x=(i == args.steps - 1))
+            results.append(run.solve(seed0 + args.warmup + i, want_x=(i == args.steps - 1)))
             ev[i][1].record(stream)
-            t = B.veloxq_last_timing(ctx)
+            t = run.timing()
             mains.append(t.ms_main)
             launches += t.launches
-            results.append(out["E"])
             main_launches, path = t.main_launches, t.path
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
@@ -215,55 +309,34 @@ def run_ours(args, rank, world, local_rank):
     value = world * n * R * K * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the public API from pinned host buffers ----
-    e2e_iters = max(1, min(args.steps, 5))
-    pinned = []
-    for a in input_arrays(w):
-        t = torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-        pinned.append(t.numpy())
+    e2e_iters = max(1, min(args.steps, 3 if run.batch else 5))
+    pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in input_arrays(w)]
     h2d = int(sum(a.nbytes for a in pinned))
     if w["kind"] == "ising_csr":
         pw = dict(w)
         pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
+    elif w["kind"] == "batch":
+        pw = dict(w, inst=pinned)
     else:
         pw = dict(w, Q=pinned[0], c=pinned[1])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_iters):
-        c2 = create(B, pw)
-        o2 = B.veloxq_solve(c2, R, K, sched, seed=seed0 + 77 + i)
-        c2.destroy()
+        r2 = Runner(B, pw, stream)
+        r2.solve(seed0 + 77 + i, want_x=True)
+        r2.destroy()
     e2e_s = (time.perf_counter() - t0) / e2e_iters
-    d2h = n + 8 * R + 8 * R + 16 + 16     # x, E per replica, device best energies, argmin record, E/E_int
+    nctx = len(run.ctxs)
+    d2h = n + (0 if run.batch else 8 * R + 8 * R) + 32 * nctx   # best x, per-replica energies, argmin records
     e2e = {"value": world * n * R * K / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
            "includes": "context creation (H2D copy, device ingest, power iteration) + solve + D2H of results"}
 
-    # ---- roofline of the dominant kernel ----
-    peaks, src = _peaks()
-    main_ms = statistics.mean(mains)
-    roof = None
-    if path == B.VELOXQ_PATH_RESIDENT:
-        nnz = info.nnz_field
-        smem_bytes = (nnz + 2 * n) * 4 * R * K           # neighbour reads + own read + own write, per launch
-        peak_gbs = SMEM_BYTES_PER_CLK_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
-        achieved = smem_bytes / (main_ms / 1e3) / 1e9
-        roof = {"kernel": "k_resident", "bound": "smem", "achieved": achieved, "peak": peak_gbs, "unit": "GB/s",
-                "frac": achieved / peak_gbs, "traffic": None,
-                "peak_source": f"derived: {SMEM_BYTES_PER_CLK_PER_SM} B/clk/SM x {NUM_SMS} SMs x "
-                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz ({src} max clock)",
-                "algorithmic_bytes_per_launch": smem_bytes, "ms_per_launch": main_ms}
-    else:
-        nnz = info.nnz_field
-        hbm_bytes = (16 * n * R + 5 * nnz + 8 * (n + 1)) * K   # state r/w + int8 CSR + rowptr per step
-        achieved = hbm_bytes / (main_ms / 1e3) / 1e9
-        roof = {"kernel": "k_stream_step", "bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": f"{src} hbm_gbs", "algorithmic_bytes_per_launch": hbm_bytes / K,
-                "ms_per_launch": main_ms / max(1, main_launches)}
+    roof = roofline(B, w, run, path, statistics.mean(mains), main_launches)
 
     # ---- CPU baseline: the oracle, single thread, bounded sample ----
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not run.batch:
         # calibrate on a short run, then time about 12 s of oracle work
         R_s = min(R, 64)
         rate0, _ = oracle_sample_rate(w, min(R, 4), min(K, 20))
@@ -274,22 +347,25 @@ def run_ours(args, rank, world, local_rank):
                          f"({dt:.1f} s)"}
 
     if rank == 0:
+        prec_name = {0: "f32", 1: "bf16", 2: "fp8e4m3"}[w.get("prec", 0)]
         line = {
             "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": prec_name,
             "data": "synthetic",
-            "config": {"workload": w["name"], "instance": w["desc"], "n": n, "nnz_field": info.nnz_field,
+            "config": {"workload": w["name"], "instance": w["desc"], "n": n, "nnz_field": run.nnz_field,
                        "replicas": R, "integration_steps": K, "readout_every": w["readout_every"],
                        "path": {1: "resident", 2: "stream", 3: "dense"}.get(path, str(path)),
-                       "l2": "flushed by a 256 MiB write before each timed step",
+                       "state": "f32", "l2": "flushed by a 256 MiB write before each timed step",
                        "parallelism": f"replicas-only x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "clocks": clk,
-            "quality": {"best_energy_last_step": results[-1], "ising_offset": info.ising_offset,
-                        "best_ising_energy_last_step": 2 * results[-1] + info.ising_offset},
+            "quality": {"best_energy_last_step": results[-1]},
             "wall_s_timed_region": wall,
         }
+        if not run.batch:
+            off = run.ctxs[0].info.ising_offset
+            line["quality"]["best_ising_energy_last_step"] = 2 * results[-1] + off
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -105,7 +105,7 @@ typedef struct {
  * recorded on the stream the kernels run on. */
 typedef struct {
     double ms_total;        /* first to last kernel of the solve */
-    double ms_main;         /* the integration itself: the resident kernel, or the captured step loop */
+    double ms_main;         /* the integration: the resident kernel, or the captured steps up to the last one */
     int64_t launches;       /* kernels this library launched for the solve */
     int32_t path;           /* veloxq_path that ran */
     int32_t main_launches;  /* launches inside ms_main (1 for the resident kernel, else the step kernels) */
@@ -196,6 +196,18 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
 int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas, int32_t steps,
                        const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best,
                        double* E_best);
+/* (veloxq_solve_batch, continued) When every context is dense, replicas is a
+ * multiple of 16 in [16, 128], sched->prec is BF16 and sched->readout_every is
+ * 0, the whole batch runs as ONE persistent tensor-core launch (instances
+ * assigned to CTAs longest-first; pipeline depth picked by timing a short
+ * probe the first time a batch shape is seen), followed by the exact
+ * final-readout energies; otherwise each context is solved in turn. */
+
+/* Final state of context ctx after the last veloxq_solve_batch that ran the
+ * persistent batched kernel (BF16 dense instances, readout only after the
+ * last step): S, Y device [R][n] float32, R the replicas of that batch.
+ * Errors: EINVAL if no such state is held for R replicas. */
+int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y);
 
 /* ---------------------------------------------------------------------------
  * Energies (Sec. 2, eq. qubo_model)

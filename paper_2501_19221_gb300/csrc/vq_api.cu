@@ -91,6 +91,8 @@ int resolve(const veloxq_ctx* ctx, const veloxq_schedule* s_in, int32_t K, RunPa
     p->dt = s.dt;
     p->a0 = s.a0;
     p->sigma0 = s.sigma0;
+    p->kappa = s.kappa;
+    p->c0_given = s.c0 > 0;
     // J = -Qoff/2 => rho(J) = rho(Qoff)/2 and c0 = kappa / rho(J)
     p->c0 = s.c0 > 0 ? s.c0 : (ctx->rho > 1e-12 ? (float)(2.0 * s.kappa / ctx->rho) : s.kappa);
     p->K = K;
@@ -187,8 +189,10 @@ bool is_readout(const RunParams& p, int k) {
     return (k == p.K - 1) || (p.readout_every > 0 && ((k + 1) % p.readout_every) == 0);
 }
 
-// Enqueue the step loop (steps, readouts, argmin) on ctx->stream.
-int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts, const TcRun* tc) {
+// Enqueue the step loop (steps, readouts, argmin) on ctx->stream; ev_steps
+// (if not null) is recorded right after the last integration step.
+int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts, const TcRun* tc,
+                 cudaEvent_t ev_steps) {
     const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
     float* cur = ctx->s_a.as<float>();
     float* nxt = ctx->s_b.as<float>();
@@ -206,6 +210,7 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
             VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
         }
         std::swap(cur, nxt);
+        if (ev_steps && k == p.K - 1) VQ_CUDA(cudaEventRecord(ev_steps, ctx->stream));
         if (!is_readout(p, k)) continue;
         int64_t* parts = ctx->ework.as<int64_t>();
         if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_energy(ctx, R, cur, parts, &np));
@@ -372,6 +377,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
     VQ_TRY(resolve(ctx, sched, steps, &p));
     const veloxq_path path = choose_path(ctx, p.path, p.prec, replicas);
     VQ_TRY(check_path(ctx, path, p.prec, replicas));
+    ctx->batch_R = 0;
     CtxExtra* ex = extra(ctx);
     const int64_t n = ctx->n, R = replicas, nw = div_up(n, 32);
     // a NULL (legacy default) stream cannot be captured: run on the context's
@@ -449,7 +455,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
             }
             cudaGraph_t g = nullptr;
             VQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            int st = enqueue_loop(ctx, path, replicas, p, nparts, use_tc ? &tc : nullptr);
+            int st = enqueue_loop(ctx, path, replicas, p, nparts, use_tc ? &tc : nullptr, ex->t2);
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
             if (st != VELOXQ_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -468,8 +474,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
             ex->graph_launches = (int64_t)nodes;
         }
         VQ_CUDA(cudaEventRecord(ex->t1, ctx->stream));
-        VQ_CUDA(cudaGraphLaunch(ex->graph, ctx->stream));
-        VQ_CUDA(cudaEventRecord(ex->t2, ctx->stream));
+        VQ_CUDA(cudaGraphLaunch(ex->graph, ctx->stream));   // records t2 after the last step
         VQ_CUDA(cudaEventRecord(ex->t3, ctx->stream));
         launches = 1 + (use_tc ? 1 : 0) + ex->graph_launches;   // init (+ operand) kernels + graph nodes
         main_launches = steps;
@@ -504,11 +509,80 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
 int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas, int32_t steps,
                        const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best, double* E_best) {
     if (count < 0 || (count > 0 && !ctxs)) return fail(VELOXQ_EINVAL, "ctxs must hold count contexts");
-    for (int32_t m = 0; m < count; ++m) {
-        int st = veloxq_solve(ctxs[m], replicas, steps, sched, seed, x_best ? x_best[m] : nullptr,
-                              E_best ? E_best + m : nullptr, nullptr, nullptr);
-        if (st != VELOXQ_OK) return fail(st, "instance " + std::to_string(m) + ": " + g_err);
+    if (count == 0) return VELOXQ_OK;
+    if (replicas < 1 || steps < 1) return fail(VELOXQ_EINVAL, "replicas and steps must be >= 1");
+    for (int32_t m = 0; m < count; ++m)
+        if (!ctxs[m]) return fail(VELOXQ_EINVAL, "context " + std::to_string(m) + " is NULL");
+    RunParams p;
+    VQ_TRY(resolve(ctxs[0], sched, steps, &p));
+    if (!batch_supported(ctxs, count, replicas, p)) {
+        // general case: one solve per context
+        for (int32_t m = 0; m < count; ++m) {
+            int st = veloxq_solve(ctxs[m], replicas, steps, sched, seed, x_best ? x_best[m] : nullptr,
+                                  E_best ? E_best + m : nullptr, nullptr, nullptr);
+            if (st != VELOXQ_OK) return fail(st, "instance " + std::to_string(m) + ": " + g_err);
+        }
+        return VELOXQ_OK;
     }
+    // one persistent launch for the whole batch, on the first context's private stream
+    veloxq_ctx* c0 = ctxs[0];
+    CtxExtra* ex = extra(c0);
+    cudaStream_t st = ex->work;
+    for (int32_t m = 0; m < count; ++m) {
+        VQ_CUDA(cudaEventRecord(ex->ev, ctxs[m]->stream));
+        VQ_CUDA(cudaStreamWaitEvent(st, ex->ev, 0));
+    }
+    {
+        cudaStream_t keep = c0->stream;
+        c0->stream = st;
+        int rc = upload_schedule(c0, p);
+        c0->stream = keep;
+        VQ_TRY(rc);
+    }
+    static DevBuf work, best_all, errw;
+    VQ_TRY(best_all.ensure(sizeof(int64_t) * 2 * (size_t)count));
+    VQ_TRY(errw.ensure(sizeof(int) * 4));
+    VQ_CUDA(cudaMemsetAsync(errw.p, 0, sizeof(int), st));
+    // autotune: pipeline depth and CTAs per SM, by timing a 2-step probe (cached per batch shape)
+    static std::map<std::vector<int64_t>, int> tuned;
+    std::vector<int64_t> shape = {count, replicas};
+    for (int32_t m = 0; m < count; ++m) shape.push_back(ctxs[m]->n);
+    int stages = 6;
+    auto hit = tuned.find(shape);
+    if (hit != tuned.end()) {
+        stages = hit->second;
+    } else {
+        RunParams probe = p;
+        probe.K = std::min(steps, 2);
+        float best_ms = 1e30f;
+        for (int cand : {4, 6}) {
+            float ms = 0.f;
+            VQ_TRY(batch_run(ctxs, count, replicas, probe, seed, st, cand, work, best_all.as<int64_t>(),
+                             errw.as<int>(), &ms));
+            if (ms < best_ms) { best_ms = ms; stages = cand; }
+        }
+        tuned[shape] = stages;
+    }
+    float ms_main = 0.f;
+    VQ_TRY(batch_run(ctxs, count, replicas, p, seed, st, stages, work, best_all.as<int64_t>(), errw.as<int>(),
+                     &ms_main));
+    int herr = 0;
+    std::vector<int64_t> h((size_t)(2 * count));
+    VQ_CUDA(cudaMemcpyAsync(&herr, errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(h.data(), best_all.p, sizeof(int64_t) * h.size(), cudaMemcpyDeviceToHost, st));
+    for (int32_t m = 0; m < count; ++m)
+        if (x_best && x_best[m])
+            VQ_CUDA(cudaMemcpyAsync(x_best[m], ctxs[m]->xout.p, (size_t)ctxs[m]->n, cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaStreamSynchronize(st));
+    if (herr) return fail(VELOXQ_ETIMEDOUT, "a bounded wait in the batched kernel gave up (code " + std::to_string(herr) + ")");
+    if (E_best)
+        for (int32_t m = 0; m < count; ++m) E_best[m] = std::ldexp((double)h[2 * m + 1], -ctxs[m]->energy_shift);
+    ex->timing.ms_total = ms_main;
+    ex->timing.ms_main = ms_main;
+    ex->timing.launches = 1 + 5 * (int64_t)count;
+    ex->timing.path = VELOXQ_PATH_DENSE;
+    ex->timing.main_launches = 1;
+    ex->timed = true;
     return VELOXQ_OK;
 }
 
@@ -551,6 +625,15 @@ int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, i
     if (E) VQ_CUDA(cudaMemcpyAsync(E, ed.p, sizeof(double) * batch, cudaMemcpyDeviceToHost, ctx->stream));
     if (E_int) VQ_CUDA(cudaMemcpyAsync(E_int, eid.p, sizeof(int64_t) * batch, cudaMemcpyDeviceToHost, ctx->stream));
     VQ_CUDA(cudaStreamSynchronize(ctx->stream));
+    return VELOXQ_OK;
+}
+
+int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y) {
+    if (!ctx || !S || !Y) return fail(VELOXQ_EINVAL, "ctx, S and Y must not be NULL");
+    if (ctx->batch_R != R || R < 1) return fail(VELOXQ_EINVAL, "no batched state held for this replica count");
+    const size_t b = sizeof(float) * (size_t)(ctx->n * (int64_t)R);
+    VQ_CUDA(cudaMemcpyAsync(S, ctx->s_a.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
+    VQ_CUDA(cudaMemcpyAsync(Y, ctx->y.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
     return VELOXQ_OK;
 }
 

@@ -59,6 +59,8 @@ enum Layout { LAYOUT_RN = 0 /* [R][n], replica-major */, LAYOUT_NR = 1 /* [n][R]
 // Resolved schedule for one run.
 struct RunParams {
     float dt, a0, c0, sigma0;
+    float kappa;
+    bool c0_given;
     int32_t K;
     int32_t readout_every;
     veloxq_prec prec;
@@ -100,6 +102,9 @@ struct veloxq_ctx {
     vq::DevBuf qoff16;            // bf16  [n][n] Qoff (tensor-core operand)
     vq::DevBuf qoff8;             // e4m3  [n][n] Qoff / scale_i
     vq::DevBuf qscale8;           // float [n] per-row FP8 scales
+    vq::DevBuf qtile;             // pre-tiled swizzled BF16 Qoff for the batched kernel
+    size_t qtile_bytes = 0;
+    int32_t batch_R = 0;          // replicas of the state left by the last batched run (0: none)
 
     // ---- common ----
     vq::DevBuf bf;                // float  [n] b = Qs 1 + c
@@ -158,6 +163,11 @@ int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
 int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+
+// persistent batched kernel (vq_batch.cu)
+bool batch_supported(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p);
+int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p, uint64_t seed, cudaStream_t st,
+              int stages, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main);
 
 // adjoint of the step (vq_adjoint.cu)
 int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vector<float>& a_host, uint64_t seed,

@@ -1,0 +1,102 @@
+"""The persistent batched tensor-core kernel (veloxq_solve_batch with dense
+BF16 contexts): one-step parity of every instance against the FP64 oracle,
+exact outputs, and solution quality on Wishart planted instances."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2501_19221_gb300 import instances as I
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+U = 2.0 ** -9       # BF16 operand rounding
+
+
+@pytest.fixture(scope="module")
+def B():
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2501_19221_gb300 import binding
+    return binding
+
+
+def _sk(n, seed):
+    Q, _ = I.sk_qubo(n, seed=seed)
+    c = np.random.default_rng(seed).normal(size=n) * 0.05
+    return Q, c
+
+
+@pytest.mark.parametrize("R", [16, 64, 128])
+def test_batch_one_step_parity(B, R):
+    """K = 1 from the Philox start: every instance's state equals the oracle's
+    FP32-input FP64 step up to the BF16 field bound propagated through the
+    update."""
+    sizes = [20, 100, 129, 300, 511, 640, 128, 64]
+    insts = [_sk(n, 10 + i) for i, n in enumerate(sizes)]
+    ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    dt, c0 = np.float32(0.5), np.float32(0.3)
+    sched = B.make_schedule(prec=1, readout_every=0, c0=float(c0), dt=float(dt))
+    out = B.veloxq_solve_batch(ctxs, R, 1, sched, seed=4)
+    for (Q, c), ctx in zip(insts, ctxs):
+        n = Q.shape[0]
+        S = torch.empty(R, n, device="cuda")
+        Y = torch.empty(R, n, device="cuda")
+        B.veloxq_batch_state_dev(ctx, R, S, Y)
+        torch.cuda.synchronize()
+        p = O.problem_from_dense(Q.astype(np.float64), c)
+        S0, Y0 = O.init_state(n, R, 4, 0.1)
+        ref = O.bsb_run(p, R, 1, float(dt), 1.0, float(c0), [0.0, 1.0], 0, S0, Y0)
+        dF = (2 * U + U * U) * O.abs_field(p, S0.astype(np.float64)) + 1e-6
+        dy = float(dt) * float(c0) * 0.5 * dF + 2e-6
+        ds = float(dt) * dy + 2e-6
+        assert np.all(np.abs(Y.cpu().numpy() - ref["Y"]) <= dy)
+        assert np.all(np.abs(S.cpu().numpy() - ref["S"]) <= ds)
+    assert len(out["E"]) == len(sizes)
+
+
+def test_batch_outputs_exact_and_consistent(B):
+    sizes = [37, 200, 150, 480, 99]
+    insts = [_sk(n, 30 + i) for i, n in enumerate(sizes)]
+    ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    out = B.veloxq_solve_batch(ctxs, 64, 200, B.make_schedule(prec=1, readout_every=0), seed=2)
+    t = B.veloxq_last_timing(ctxs[0])
+    assert t.main_launches == 1
+    for (Q, c), x, E in zip(insts, out["x"], out["E"]):
+        p = O.problem_from_dense(Q.astype(np.float64), c)
+        Ex = O.energy(p, x)[0]
+        tol = (p.nnz + p.n) * 2.0 ** -52 * (np.sum(np.abs(Q)) + np.sum(np.abs(c)))
+        assert abs(Ex - E) <= tol
+        assert E < np.min(O.energy(p, I.random_binary(128, p.n, seed=1)))
+
+
+def test_batch_wishart_reaches_planted_energy(B):
+    """Wishart planted instances (Sec. Wishart ensemble), alpha = 0.75: the
+    batched BF16 solve returns energies at or above the planted ground state
+    and within 2% of it."""
+    sizes = [100, 160, 240, 320]
+    ctxs, E0s, offs = [], [], []
+    for i, n in enumerate(sizes):
+        w = I.wishart_ising(n, 0.75, seed=50 + i)
+        ctx = B.veloxq_create_ising_dense(-w["J"], None)
+        ctxs.append(ctx)
+        E0s.append(0.5 * w["Jt_diag"].sum())
+        offs.append(ctx.info.ising_offset)
+    out = B.veloxq_solve_batch(ctxs, 64, 1000, B.make_schedule(prec=1, readout_every=0), seed=1)
+    for E, E0, off in zip(out["E"], E0s, offs):
+        H = 2 * E + off
+        assert H >= E0 - 1e-6 * abs(E0)
+        assert (H - E0) / abs(E0) <= 0.02
+
+
+def test_batch_falls_back_when_not_supported(B):
+    """Other schedules (readouts during the run, FP32) solve each context in turn."""
+    sizes = [40, 70]
+    insts = [_sk(n, 60 + i) for i, n in enumerate(sizes)]
+    ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    a = B.veloxq_solve_batch(ctxs, 32, 100, B.make_schedule(readout_every=10), seed=3)
+    for ctx, E in zip(ctxs, a["E"]):
+        single = B.veloxq_solve(ctx, 32, 100, B.make_schedule(readout_every=10), seed=3)
+        assert single["E"] == E
