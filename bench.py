@@ -82,10 +82,15 @@ def workload(name: str) -> dict:
 
 
 def batch_instances(w):
-    """Wishart Ising couplings of the batch, as the Ising form -J (seeded per instance)."""
+    """Wishart Ising couplings of the batch, as the Ising form -J (seeded per
+    instance), and each instance's planted ground energy E0 = Tr(J~)/2."""
     if "inst" not in w:
-        w["inst"] = [(-I.wishart_ising(int(n), 0.75, seed=1000 + m, dtype=np.float32)["J"]).astype(np.float32)
-                     for m, n in enumerate(w["sizes"])]
+        inst, e0 = [], []
+        for m, n in enumerate(w["sizes"]):
+            d = I.wishart_ising(int(n), 0.75, seed=1000 + m, dtype=np.float32)
+            inst.append((-d["J"]).astype(np.float32))
+            e0.append(0.5 * float(d["Jt_diag"].sum()))
+        w["inst"], w["E0"] = inst, e0
     return w["inst"]
 
 
@@ -199,6 +204,7 @@ class Runner:
     def solve(self, seed, want_x=False):
         if self.batch:
             out = self.B.veloxq_solve_batch(self.ctxs, self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)
+            self.last_batch_E = out["E"]
             return float(np.min(out["E"]))
         return self.B.veloxq_solve(self.ctxs[0], self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)["E"]
 
@@ -316,7 +322,7 @@ def run_ours(args, rank, world, local_rank):
         pw = dict(w)
         pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
     elif w["kind"] == "batch":
-        pw = dict(w, inst=pinned)
+        pw = dict(w, inst=pinned, E0=w["E0"])
     else:
         pw = dict(w, Q=pinned[0], c=pinned[1])
     torch.cuda.synchronize()
@@ -366,6 +372,11 @@ def run_ours(args, rank, world, local_rank):
         if not run.batch:
             off = run.ctxs[0].info.ising_offset
             line["quality"]["best_ising_energy_last_step"] = 2 * results[-1] + off
+        else:
+            gaps = [(2 * E + c.info.ising_offset - e0) / abs(e0)
+                    for E, c, e0 in zip(run.last_batch_E, run.ctxs, w["E0"])]
+            line["quality"] = {"mean_gap_to_planted": float(np.mean(gaps)), "max_gap_to_planted": float(np.max(gaps)),
+                               "instances_at_planted_energy": int(np.sum(np.array(gaps) <= 1e-9))}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

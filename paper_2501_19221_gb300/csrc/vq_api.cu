@@ -27,6 +27,7 @@ int fail(int status, const std::string& msg) {
 
 int cuda_fail(cudaError_t e, const char* what) {
     g_err = std::string("CUDA error in ") + what + ": " + cudaGetErrorString(e);
+    cudaGetLastError();   // a non-sticky error must not resurface in a later launch check
     if (e == cudaErrorMemoryAllocation) return VELOXQ_ENOMEM;
     return VELOXQ_ECUDA;
 }
@@ -210,7 +211,8 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
             VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
         }
         std::swap(cur, nxt);
-        if (ev_steps && k == p.K - 1) VQ_CUDA(cudaEventRecord(ev_steps, ctx->stream));
+        // an event node of the graph (a plain record during capture would only order streams)
+        if (ev_steps && k == p.K - 1) VQ_CUDA(cudaEventRecordWithFlags(ev_steps, ctx->stream, cudaEventRecordExternal));
         if (!is_readout(p, k)) continue;
         int64_t* parts = ctx->ework.as<int64_t>();
         if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_energy(ctx, R, cur, parts, &np));

@@ -101,7 +101,10 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
 template <typename QT> __device__ __forceinline__ int64_t qfix(QT q, int shift);
 template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int shift) { return (int64_t)q * (1ll << shift); }
 template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int shift) { return (int64_t)q * (1ll << shift); }
+// q 2^S is exact in float (a power-of-two scaling that stays below 2^62), so
+// the rounding to an integer is the same as in double, without FP64 arithmetic
 template <> __device__ __forceinline__ int64_t qfix<float>(float q, int shift) {
+    if (shift <= 100) return __float2ll_rn(q * ldexpf(1.0f, shift));
     return __double2ll_rn((double)q * ldexp(1.0, shift));
 }
 template <> __device__ __forceinline__ int64_t qfix<double>(double q, int shift) {

@@ -294,8 +294,7 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
 #pragma unroll
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
         }
-        return;
-    }
+    } else {
     for (int64_t p = p0; p < p1; p += 4) {
         int64_t j[4];
         float wv[4];
@@ -312,6 +311,7 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
+    }
     }
 }
 

@@ -119,20 +119,34 @@ def _fd_check(B, ctx, R, K, base, seed, h):
     return {"d_dt": [g["d_dt"], fd_dt], "d_kappa": [g["d_kappa"], fd_k], "d_knot1": [float(g["d_knots"][1]), fd_kn1]}
 
 
-def test_grad_central_differences_on_gpu(B):
-    """A 20^3 lattice, 64 replicas. Over a short horizon (few wall events move
-    under the perturbation) the adjoint equals central differences of the GPU
-    loss to 2%. Over a long post-bifurcation horizon, wall-hit events move
-    under any finite perturbation and the two part (the adjoint is the
-    derivative of the piecewise-smooth loss, FD averages over its jumps): that
-    comparison is recorded, not asserted."""
-    ctx, _ = _lattice(B, 20, seed=1)
-    short = _fd_check(B, ctx, 64, 40, dict(dt=0.3, kappa=1.0, knots=[0.0, 0.3, 0.5], readout_every=0), 3, 1e-3)
-    _report("central_differences_L20_K40", short)
-    long = _fd_check(B, ctx, 64, 120, dict(dt=0.3, kappa=1.0, knots=[0.0, 0.6, 1.0], readout_every=0), 3, 1e-3)
-    _report("central_differences_L20_K120_walls", long)
-    for a, f in short.values():
-        assert abs(a - f) <= 0.02 * max(abs(f), abs(a)) + 1e-6, short
+def test_grad_mid_size_against_oracle_and_differences(B):
+    """A 20^3 lattice (8000 variables), 64 replicas, 40 steps: the GPU adjoint
+    against the oracle's FP64 reverse mode (1e-2: over 40 steps an FP32
+    trajectory may cross a wall the FP64 one just misses). Central differences
+    of the GPU loss are recorded beside it, short and long horizon: a finite
+    perturbation moves wall-hit events, which the derivative of the
+    piecewise-smooth loss does not see, so they are reported, not asserted."""
+    ctx, p = _lattice(B, 20, seed=1)
+    R, K, seed = 64, 40, 3
+    base = dict(dt=0.3, kappa=1.0, knots=[0.0, 0.3, 0.5], readout_every=0)
+    g = B.veloxq_grad(ctx, R, K, B.make_schedule(**base), seed, 20)
+    c0 = float(np.float32(2.0 * 1.0 / ctx.info.rho))
+    gc = B.veloxq_grad(ctx, R, K, B.make_schedule(dt=0.3, c0=c0, knots=[0.0, 0.3, 0.5], readout_every=0), seed, 20)
+    S0, Y0 = O.init_state(p.n, R, seed, 0.1)
+    kn32 = [float(np.float32(v)) for v in base["knots"]]
+    ref = O.bsb_grad(p, R, K, float(np.float32(0.3)), 1.0, c0, kn32, S0, Y0)
+    _report("oracle_L20_K40", {"loss": [gc["loss"], ref["loss"]], "d_dt": [gc["d_dt"], ref["d_dt"]],
+                               "d_c0": [gc["d_kappa"], ref["d_c0"]],
+                               "d_knots": [list(gc["d_knots"]), list(ref["d_knots"])]})
+    assert _rel(gc["loss"], ref["loss"]) <= 1e-5
+    scale = max(abs(ref["d_dt"]), abs(ref["d_c0"]), np.max(np.abs(ref["d_knots"])))
+    assert abs(gc["d_dt"] - ref["d_dt"]) <= 1e-2 * scale
+    assert abs(gc["d_kappa"] - ref["d_c0"]) <= 1e-2 * scale
+    assert np.all(np.abs(gc["d_knots"] - ref["d_knots"]) <= 1e-2 * scale)
+    _report("central_differences_L20_K40", _fd_check(B, ctx, R, K, base, seed, 1e-3))
+    _report("central_differences_L20_K120_walls",
+            _fd_check(B, ctx, R, 120, dict(dt=0.3, kappa=1.0, knots=[0.0, 0.6, 1.0], readout_every=0), seed, 1e-3))
+    assert np.isfinite(g["d_dt"])
 
 
 def test_autograd_function_and_schedule_tuning(B):
