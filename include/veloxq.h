@@ -221,6 +221,24 @@ int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, i
 /* As veloxq_energy with device pointers; asynchronous on the context stream. */
 int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
 
+/* The same energies as veloxq_energy_dev for callers that must not allocate
+ * device memory during the call: code running while a CUDA graph is being
+ * captured, code inside a custom allocator that must not re-enter cudaMalloc,
+ * and loops that cannot afford the synchronisation an allocation may cause.
+ * (The paper has no counterpart; this is a property of the library.)
+ * Scratch is a fixed 4 MiB array in device memory that every GPU loading the
+ * library keeps until the process exits; nothing is allocated or freed. The
+ * first call on a device looks up that array's device address (a one-time
+ * set-up per device, so make that first call before any stream capture), and
+ * the context's device must be the current one. Limits: batch <= 65535 and
+ * batch * groups <= 2^19, groups = 64 for sparse contexts and ceil(n/64) for
+ * dense ones; larger batches are rejected with EINVAL and a message giving the
+ * largest accepted batch. All calls share the one array: calls that overlap
+ * on the GPU (different streams, or different contexts on one device) race
+ * and must be serialised by the caller. X, E, E_int: device pointers as in
+ * veloxq_energy_dev; asynchronous on the context's stream. */
+int veloxq_energy_dev_noalloc(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
+
 /* ---------------------------------------------------------------------------
  * Pieces of the step, for parity tests and for callers that drive the
  * integration themselves (device pointers, asynchronous).

@@ -32,7 +32,7 @@ EXPORTED = [
     "veloxq_create_ising_csr", "veloxq_destroy", "veloxq_last_error", "veloxq_get_info", "veloxq_set_stream",
     "veloxq_solve", "veloxq_solve_batch", "veloxq_energy", "veloxq_energy_dev", "veloxq_init_state_dev",
     "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad", "veloxq_last_timing",
-    "veloxq_batch_state_dev",
+    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc",
 ]
 
 
@@ -88,6 +88,7 @@ def _load():
         "veloxq_grad": (I, [P, I32, I32, S, U64, I32, P, P, P, P]),
         "veloxq_last_timing": (I, [P, ctypes.POINTER(Timing)]),
         "veloxq_batch_state_dev": (I, [P, I32, P, P]),
+        "veloxq_energy_dev_noalloc": (I, [P, I64, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -309,6 +310,14 @@ def veloxq_batch_state_dev(ctx: Context, R: int, S, Y) -> None:
     n = ctx.info.n
     veloxq_set_stream(ctx, _stream_ptr())
     _check(_lib.veloxq_batch_state_dev(ctx.handle, R, _dev(S, "float32", (R, n)), _dev(Y, "float32", (R, n))))
+
+
+def veloxq_energy_dev_noalloc(ctx: Context, X, E, E_int=None) -> None:
+    """veloxq_energy_dev without any device allocation (fixed scratch; see the header)."""
+    B_ = X.shape[0]
+    veloxq_set_stream(ctx, _stream_ptr())
+    _check(_lib.veloxq_energy_dev_noalloc(ctx.handle, B_, _dev(X, "uint8", (B_, ctx.info.n)), _dev(E, "float64", (B_,)),
+                                          _dev(E_int, "int64", (B_,)) if E_int is not None else None))
 
 
 def veloxq_init_state_dev(ctx: Context, R: int, seed: int, sigma0: float, S, Y) -> None:
