@@ -36,6 +36,15 @@ import numpy as np
 from paper_2501_19221_gb300 import instances as I
 
 L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of
+# the current kernel build (summaries and commands in profiles/); a kernel that
+# changes after its capture must be removed from this table.
+NCU_TRAFFIC = {
+    ("k_resident", "chimera_c16"): 294_400,
+    ("k_tc_step", "sk_n8192_bf16"): 409_447_936,
+    ("k_stream_step", "lattice_l100"): 4_133_930_000,
+}
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152
 
@@ -261,6 +270,49 @@ def roofline(B, w, runner, path, main_ms, main_launches):
             "algorithmic_bytes_per_launch": hbm_bytes, "ms_per_launch": per}
 
 
+def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200):
+    """Time-to-target of the mixed-precision forms against the plain FP32
+    form on the dense SK instance (n = 8192, 1024 replicas). The target E* is
+    the median over `seeds` of the FP32 form's best energy after K steps; a
+    form reaches it at the smallest K' of a grid where at least half of the
+    seeds end at or below E*. Times are CUDA-event times of whole solves."""
+    import torch
+    Q, c = I.sk_qubo(n, seed=0)
+    ctx = B.veloxq_create_dense(Q, c)
+    B.veloxq_set_stream(ctx, stream.cuda_stream)
+
+    def solve(prec, steps, seed):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        E = B.veloxq_solve(ctx, R, steps, B.make_schedule(prec=prec, readout_every=0), seed=seed, want_x=False,
+                           want_per_replica=False)["E"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return E, e0.elapsed_time(e1)
+
+    out = {"workload": f"sk n={n}, {R} replicas, final readout only", "seeds": seeds}
+    with torch.cuda.stream(stream):
+        solve(0, 4, 0)
+        fp32 = [solve(0, K, 100 + s) for s in range(seeds)]
+        E_star = float(np.median([e for e, _ in fp32]))
+        t32 = float(np.median([t for _, t in fp32]))
+        out["E_star"] = E_star
+        out["fp32"] = {"steps": K, "ms": t32, "success": float(np.mean([e <= E_star for e, _ in fp32]))}
+        for name, prec in (("bf16", 1), ("fp8", 2)):
+            solve(prec, 4, 0)
+            best = None
+            for k2 in (25, 50, 100, 150, K, 2 * K):
+                runs = [solve(prec, k2, 100 + s) for s in range(seeds)]
+                p = float(np.mean([e <= E_star for e, _ in runs]))
+                if p >= 0.5:
+                    best = {"steps": k2, "ms": float(np.median([t for _, t in runs])), "success": p}
+                    break
+            out[name] = best
+            out[f"speedup_{name}"] = (t32 / best["ms"]) if best else None
+    ctx.destroy()
+    return out
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import __graft_entry__ as g
@@ -339,6 +391,10 @@ def run_ours(args, rank, world, local_rank):
            "includes": "context creation (H2D copy, device ingest, power iteration) + solve + D2H of results"}
 
     roof = roofline(B, w, run, path, statistics.mean(mains), main_launches)
+    roof["traffic"] = NCU_TRAFFIC.get((roof["kernel"], w["name"]))
+    ttt = None
+    if args.ttt and rank == 0:
+        ttt = time_to_target(B, stream, seeds=args.ttt_seeds)
 
     # ---- CPU baseline: the oracle, single thread, bounded sample ----
     cpu = None
@@ -365,6 +421,7 @@ def run_ours(args, rank, world, local_rank):
                        "state": "f32", "l2": "flushed by a 256 MiB write before each timed step",
                        "parallelism": f"replicas-only x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "time_to_target": ttt,
             "clocks": clk,
             "quality": {"best_energy_last_step": results[-1]},
             "wall_s_timed_region": wall,
@@ -416,6 +473,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chimera_c16")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ttt", dest="ttt", action="store_true", default=True,
+                    help="measure time-to-target of BF16/FP8 against FP32 on the dense SK instance (default on)")
+    ap.add_argument("--no-ttt", dest="ttt", action="store_false")
+    ap.add_argument("--ttt-seeds", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
