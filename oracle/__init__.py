@@ -250,6 +250,25 @@ def ising_csr_to_qubo(n, rowptr, col, J, h=None):
     return p, C.value
 
 
+def ising_pairs_to_qubo(n, pi, pj, pv, h=None):
+    """App. A Ising -> QUBO from a list of coupled pairs (i < j, J_ij): returns
+    (Problem, C) with H(s) = 2 E(x) + C. A subset of pairs gives the exact
+    off-diagonal entries of those pairs (for sampled rows of huge instances);
+    the diagonal is then that of the subset."""
+    lib = _load()
+    pi = np.ascontiguousarray(pi, dtype=np.int64)
+    pj = np.ascontiguousarray(pj, dtype=np.int64)
+    pv = np.ascontiguousarray(pv, dtype=np.float64)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    m = pi.shape[0]
+    er = np.zeros(2 * m + n, dtype=np.int64)
+    ec = np.zeros(2 * m + n, dtype=np.int64)
+    ev = np.zeros(2 * m + n, dtype=np.float64)
+    C = ctypes.c_double(0.0)
+    lib.oracle_ising_pairs_to_qubo(n, m, _p(pi), _p(pj), _p(pv), _p(hh), _p(er), _p(ec), _p(ev), ctypes.byref(C))
+    return Problem(n, er, ec, ev, np.zeros(n)), C.value
+
+
 def qubo_to_ising(Q: np.ndarray):
     """App. A QUBO -> Ising for symmetric Q: (J, h, C) with Q(x) = H(s)/2 + C/2."""
     lib = _load()

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_loss(int64_t n, int32_t R, 
                                                           const int32_t* __restrict__ col, const WT* __restrict__ w,
                                                           float wscale, const float* __restrict__ S,
                                                           const float* __restrict__ bf, float* lam_s, float* lam_y,
-                                                          double* parts) {
+                                                          double* parts, int udeg) {
     __shared__ double sh[kAdjThreads];
     double e = 0.0;
     const int64_t total = n * (int64_t)nvec;
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_loss(int64_t n, int32_t R, 
         const int64_t off = (int64_t)(t - i * nvec) * V;
         const int64_t me = i * R + off;
         float acc[V], s[V], ls[V], ly[V];
-        vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S, R, off, i, acc);
+        vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S, R, off, i, acc, udeg);
         vqd::vload<V>(S + me, s);
         const float b = __ldg(bf + i);
 #pragma unroll
@@ -87,7 +87,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
                                                        const float* __restrict__ Yk, const float* __restrict__ bf,
                                                        float a_k, float dt, float a0, float c0,
                                                        const float* __restrict__ lam_s, float* lam_y, float* gphi,
-                                                       float* gsl, double* parts3) {
+                                                       float* gsl, double* parts3, int udeg) {
     __shared__ double sh[3 * kAdjThreads];
     double acc3[3] = {0.0, 0.0, 0.0};
     const int64_t total = n * (int64_t)nvec;
@@ -96,7 +96,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
         const int64_t off = (int64_t)(t - i * nvec) * V;
         const int64_t me = i * R + off;
         float acc[V], s[V], y[V], ls[V], ly[V], gp[V], gs[V], gy[V];
-        vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, Sk, R, off, i, acc);
+        vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, Sk, R, off, i, acc, udeg);
         vqd::vload<V>(Sk + me, s);
         vqd::vload<V>(Yk + me, y);
         vqd::vload<V>(lam_s + me, ls);
@@ -140,14 +140,14 @@ template <int V, typename WT, int UNROLL>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_b(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col, const WT* __restrict__ w,
                                                        float wscale, const float* __restrict__ gphi,
-                                                       const float* __restrict__ gsl, float* lam_s) {
+                                                       const float* __restrict__ gsl, float* lam_s, int udeg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / nvec;
     if (i >= n) return;
     const int64_t off = (int64_t)(t - i * nvec) * V;
     const int64_t me = i * R + off;
     float acc[V], g[V];
-    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, gphi, R, off, i, acc);
+    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, gphi, R, off, i, acc, udeg);
     vqd::vload<V>(gsl + me, g);
 #pragma unroll
     for (int l = 0; l < V; ++l) g[l] = g[l] - 0.5f * (acc[l] * wscale);
@@ -206,19 +206,19 @@ struct AdjLaunch {
     static void loss(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* S, float* ls, float* ly, double* parts) {
         k_adj_loss<V, WT, U><<<kAdjBlocks, kAdjThreads, 0, c->stream>>>(c->n, R, R / V, c->rowptr.as<int64_t>(),
                                                                          c->col.as<int32_t>(), w, ws, S,
-                                                                         c->bf.as<float>(), ls, ly, parts);
+                                                                         c->bf.as<float>(), ls, ly, parts, c->uniform_deg);
     }
     static void a(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* Sk, const float* Yk, float a_k, float dt,
                   float a0, float c0, const float* ls, float* ly, float* gp, float* gs, double* parts3) {
         k_adj_a<V, WT, U><<<kAdjBlocks, kAdjThreads, 0, c->stream>>>(c->n, R, R / V, c->rowptr.as<int64_t>(),
                                                                       c->col.as<int32_t>(), w, ws, Sk, Yk,
                                                                       c->bf.as<float>(), a_k, dt, a0, c0, ls, ly, gp,
-                                                                      gs, parts3);
+                                                                      gs, parts3, c->uniform_deg);
     }
     static void b(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* gp, const float* gs, float* ls) {
         const int64_t total = c->n * (int64_t)(R / V);
         k_adj_b<V, WT, U><<<(unsigned)div_up(total, kAdjThreads), kAdjThreads, 0, c->stream>>>(
-            c->n, R, R / V, c->rowptr.as<int64_t>(), c->col.as<int32_t>(), w, ws, gp, gs, ls);
+            c->n, R, R / V, c->rowptr.as<int64_t>(), c->col.as<int32_t>(), w, ws, gp, gs, ls, c->uniform_deg);
     }
 };
 

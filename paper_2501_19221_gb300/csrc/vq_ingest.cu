@@ -577,10 +577,18 @@ int ingest_csr_t(veloxq_ctx* ctx, const int64_t* rph, const int32_t* colh, const
         DevBuf mtmp;
         VQ_TRY(mtmp.ensure(mb + 16));
         VQ_CUDA(cub::DeviceReduce::Max(mtmp.p, mb, cnt, dmax, n, st));
-        int64_t hm = 0;
+        int64_t hm = 0, hmin = 0;
         VQ_CUDA(cudaMemcpyAsync(&hm, dmax, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        int64_t* dmin = (int64_t*)(scal + 12);
+        size_t nb = 0;
+        cub::DeviceReduce::Min(nullptr, nb, cnt, dmin, n, st);
+        DevBuf ntmp;
+        VQ_TRY(ntmp.ensure(nb + 16));
+        VQ_CUDA(cub::DeviceReduce::Min(ntmp.p, nb, cnt, dmin, n, st));
+        VQ_CUDA(cudaMemcpyAsync(&hmin, dmin, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
         VQ_CUDA(cudaStreamSynchronize(st));
         ctx->max_row = (int)hm;
+        ctx->uniform_deg = (hm == hmin && hm < (1 << 20)) ? (int)hm : -1;
     }
     return VELOXQ_OK;
 }

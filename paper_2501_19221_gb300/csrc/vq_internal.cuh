@@ -93,6 +93,7 @@ struct veloxq_ctx {
     vq::DevBuf w8;                // int8  [nnz]   2 Qs_ij when integer and |2Qs| <= 127
     vq::DevBuf wfix;              // int64 [nnz]   round(Qs_ij 2^S) (energy), when w8 is absent
     int max_row = 0;              // longest row of the field structure
+    int uniform_deg = -1;         // every row holds this many couplings (-1: rows differ)
     bool wf_half_exact = false;   // every Qs_ij is an exact half (integer |2 Qs| <= 2047)
 
     // ---- dense ----
@@ -281,10 +282,12 @@ __device__ __forceinline__ float wval(int8_t w) { return (float)w; }
 template <int V, typename WT, int UNROLL>
 __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const WT* __restrict__ w, const float* X, int32_t R, int64_t off,
-                                            int64_t i, float (&acc)[V]) {
+                                            int64_t i, float (&acc)[V], int udeg = -1) {
 #pragma unroll
     for (int l = 0; l < V; ++l) acc[l] = 0.0f;
-    const int64_t p0 = __ldg(rp + i), p1 = __ldg(rp + i + 1);
+    // rows of a regular graph start at i * degree: no row pointer is read
+    const int64_t p0 = udeg >= 0 ? i * udeg : __ldg(rp + i);
+    const int64_t p1 = udeg >= 0 ? p0 + udeg : __ldg(rp + i + 1);
     if constexpr (UNROLL == 1) {
         for (int64_t p = p0; p < p1; ++p) {
             const int64_t j = __ldg(col + p);

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
                                                      float wscale, const float* __restrict__ S_cur,
                                                      float* __restrict__ S_nxt, const float* Y_in, float* Y_out,
                                                      const float* __restrict__ bf, const float* __restrict__ a_table,
-                                                     int k, float dt, float a0, float c0, float* __restrict__ F_out) {
+                                                     int k, float dt, float a0, float c0, float* __restrict__ F_out,
+                                                     int udeg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / nvec;
     if (i >= n) return;
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
         a_k = __ldg(a_table + k);
     }
     float acc[V];
-    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S_cur, R, off, i, acc);
+    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S_cur, R, off, i, acc, udeg);
     float F[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) F[l] = acc[l] * wscale;     // wscale is 1 or 1/2: exact
@@ -153,10 +154,12 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
     do {                                                                                                            \
         if (unroll == 4)                                                                                            \
             k_stream_step<VV, WT, FIELD_ONLY, 4><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
-                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out); \
+                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out,  \
+                                                                    ctx->uniform_deg);                               \
         else                                                                                                        \
             k_stream_step<VV, WT, FIELD_ONLY, 1><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
-                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out); \
+                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out,  \
+                                                                    ctx->uniform_deg);                               \
     } while (0)
     const int unroll = ctx->stream_unroll == 4 ? 4 : 1;
     if (ctx->w8.p) {

@@ -10,6 +10,9 @@
 //   FP8 : Qop = e4m3(Qoff_ij / q_i), q_i = amax_i / 448,
 //         Sop = e4m3(448 s)  (|s| <= 1 by the walls)       (kind::f8f6f4)
 //         F_i = acc q_i / 448
+// The kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x,
+// + gridDim.x, ...; two accumulator buffers in tensor memory let the
+// epilogue of one tile overlap the main loop of the next.
 // Warp roles: warp 0 issues TMA, warp 1 allocates tensor memory and issues
 // the MMAs, warps 2-9 read the accumulator tile (a 32-lane quarter and half
 // of the columns each) and run the update for their rows. Every wait is bounded: on timeout the
@@ -19,6 +22,8 @@
 #include <cuda_bf16.h>
 #include <cuda_fp8.h>
 
+#include <algorithm>
+
 #include "vq_internal.cuh"
 
 namespace vq {
@@ -27,7 +32,7 @@ namespace {
 
 constexpr int BM = 128, BN = 256, BKB = 128, STAGES = 4;
 constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BN * BKB, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers*/;
+constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4 };
@@ -183,26 +188,31 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
     uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accf + 1);
+    uint64_t* accf = empty + STAGES;      // [2] accumulator buffer ready for the epilogue
+    uint64_t* acce = accf + 2;            // [2] accumulator buffer drained by the epilogue
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     constexpr int EB = PREC == 1 ? 2 : 1;
     constexpr int BK = BKB / EB;                 // elements per K block
     constexpr int KSTEP_B = 32;                  // bytes of K per MMA (16 bf16 / 32 e4m3)
     const int num_kb = (a.n_pad + BK - 1) / BK;
+    const int MT = (a.n + BM - 1) / BM, NT = (a.R + BN - 1) / BN;
+    const int tiles = MT * NT;                   // tile t: row block t / NT, replica block t % NT
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accf, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 8);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp == 1) tmem_alloc(tmem_slot, BN);
+    if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -210,52 +220,70 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
 
     if (warp == 0) {
         if (lane == 0) {
-            for (int kb = 0; kb < num_kb; ++kb) {
-                const int s = kb % STAGES, u = kb / STAGES;
-                if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) break;
-                uint8_t* sa = smem + s * STAGE_BYTES;
-                mbar_expect_tx(&full[s], STAGE_BYTES);
-                tma_load_2d(sa, &tmA, kb * BK, m0, &full[s]);
-                tma_load_2d(sa + A_BYTES, &tmB, kb * BK, n0, &full[s]);
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    const uint32_t s = it % STAGES, u = it / STAGES;
+                    if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) { ok = false; break; }
+                    uint8_t* sa = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full[s], STAGE_BYTES);
+                    tma_load_2d(sa, &tmA, kb * BK, m0, &full[s]);
+                    tma_load_2d(sa + A_BYTES, &tmB, kb * BK, n0, &full[s]);
+                    ++it;
+                }
             }
         }
     } else if (warp == 1) {
         if (lane == 0) {
             constexpr uint32_t idesc = instr_desc<PREC>();
+            uint32_t it = 0, tt = 0;
             bool ok = true;
-            for (int kb = 0; kb < num_kb; ++kb) {
-                const int s = kb % STAGES, u = kb / STAGES;
-                if (!mbar_wait(&full[s], u & 1, a.err, TC_ERR_MMA)) { ok = false; break; }
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
+                const uint32_t b = tt & 1u;
+                if (tt >= 2 && !mbar_wait(&acce[b], ((tt >> 1) - 1) & 1u, a.err, TC_ERR_MMA)) { ok = false; break; }
                 tc_fence_after();
-                const uint8_t* sa = smem + s * STAGE_BYTES;
+                const uint32_t d = tmem + b * BN;
+                for (int kb = 0; kb < num_kb; ++kb) {
+                    const uint32_t s = it % STAGES, u = it / STAGES;
+                    if (!mbar_wait(&full[s], u & 1, a.err, TC_ERR_MMA)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint8_t* sa = smem + s * STAGE_BYTES;
 #pragma unroll
-                for (int kk = 0; kk < BKB / KSTEP_B; ++kk)
-                    umma<PREC>(tmem, smem_desc(sa + kk * KSTEP_B), smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc,
-                               (kb | kk) != 0 ? 1u : 0u);
-                umma_commit(&empty[s]);
+                    for (int kk = 0; kk < BKB / KSTEP_B; ++kk)
+                        umma<PREC>(d, smem_desc(sa + kk * KSTEP_B), smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc,
+                                   (kb | kk) != 0 ? 1u : 0u);
+                    umma_commit(&empty[s]);
+                    ++it;
+                }
+                if (ok) umma_commit(&accf[b]);
             }
-            if (ok) umma_commit(accf);
         }
     } else {
         // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31; the
         // first four epilogue warps take columns [0, BN/2), the next four the rest
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
-        const int row = m0 + q * 32 + lane;
-        const bool row_ok = row < a.n;
-        float fscale = 1.0f, b = 0.0f;
-        if (row_ok) {
-            if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
-            if constexpr (!FIELD_ONLY) b = __ldg(a.bf + row);
-        }
         const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
-        if (mbar_wait(accf, 0, a.err, TC_ERR_EPILOGUE)) {
+        uint32_t tt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tt) {
+            const uint32_t b = tt & 1u;
+            const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+            const int row = m0 + q * 32 + lane;
+            const bool row_ok = row < a.n;
+            float fscale = 1.0f, bi = 0.0f;
+            if (row_ok) {
+                if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
+                if constexpr (!FIELD_ONLY) bi = __ldg(a.bf + row);
+            }
+            if (!mbar_wait(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
             tc_fence_after();
             constexpr int CW = 16;   // columns per tensor-memory load
 #pragma unroll 1
             for (int c = half * (BN / (2 * CW)); c < (half + 1) * (BN / (2 * CW)); ++c) {
                 uint32_t v[CW];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(c * CW), v);
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)(c * CW), v);
                 const int r0 = n0 + c * CW;
                 // every load of the chunk is issued before any use (no early exit)
                 float sv[CW], yv[CW];
@@ -276,7 +304,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     if (ok && a.F_out) a.F_out[p] = F;
                     if constexpr (!FIELD_ONLY) {
                         float s = sv[j], y = yv[j];
-                        vqd::bsb_update(F, b, a_k, a.dt, a.a0, a.c0, s, y);
+                        vqd::bsb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
                         if (ok) {
                             a.S_nxt[p] = s;
                             a.Y[p] = y;
@@ -285,12 +313,16 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     }
                 }
             }
+            // hand the accumulator buffer back to the MMA warp
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
         }
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (warp == 1) tmem_dealloc(tmem, BN);
+    if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
 
 // ---- operand preparation --------------------------------------------------
@@ -441,7 +473,15 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     a.a_table = a_table;
     a.F_out = F_out;
     a.err = err;
-    dim3 grid((unsigned)div_up(ctx->n, BM), (unsigned)div_up(R, BN));
+    // persistent: one CTA per SM (at most one per tile), tiles strided over the CTAs
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        VQ_CUDA(cudaGetDevice(&dev));
+        VQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    const int64_t tiles = div_up(ctx->n, BM) * div_up(R, BN);
+    dim3 grid((unsigned)std::min<int64_t>(tiles, sms));
     const bool field_only = S_nxt == nullptr;
     void (*fn)(const CUtensorMap, const CUtensorMap, const TcArgs);
     if (prec == VELOXQ_PREC_BF16) fn = field_only ? k_tc_step<1, true> : k_tc_step<1, false>;
