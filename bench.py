@@ -41,9 +41,9 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # the current kernel build (summaries and commands in profiles/); a kernel that
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
-    ("k_resident", "chimera_c16"): 294_400,
-    ("k_tc_step", "sk_n8192_bf16"): 409_447_936,
-    ("k_stream_step", "lattice_l100"): 4_133_930_000,
+    ("k_resident", "chimera_c16"): 285_952,
+    ("k_tc_step", "sk_n8192_bf16"): 284_011_008,
+    ("k_tc_step", "sk_n8192_fp8"): 176_409_600,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152

@@ -183,7 +183,7 @@ int veloxq_last_timing(veloxq_ctx* ctx, veloxq_timing* timing);
  *   E_best        its energy as a double;
  *   E_best_int    its exact int64 energy (integer contexts only, else untouched);
  *   E_per_replica `replicas` doubles, each replica's best energy.
- * Errors: EINVAL (replicas < 1, steps < 1, bad schedule), EUNSUPPORTED (path
+ * Errors: EINVAL (replicas < 1 or > 2^20, steps < 1, bad schedule), EUNSUPPORTED (path
  * or precision not available for this context), ENOMEM, ECUDA. */
 int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched,
                  uint64_t seed, uint8_t* x_best, double* E_best, int64_t* E_best_int,

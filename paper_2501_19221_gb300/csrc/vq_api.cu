@@ -239,6 +239,10 @@ int stream_energy_parts_count(veloxq_ctx* ctx, veloxq_path path, int32_t R) {
 
 using namespace vq;
 
+// Replica counts above 2^20 would overflow the second grid axis of the dense
+// kernels (R / 32 blocks); no workload comes near it.
+static constexpr int32_t kMaxReplicas = 1 << 20;
+
 extern "C" {
 
 void veloxq_schedule_default(veloxq_schedule* s) {
@@ -372,7 +376,7 @@ int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho) {
 int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                  uint8_t* x_best, double* E_best, int64_t* E_best_int, double* E_per_replica) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    if (replicas < 1) return fail(VELOXQ_EINVAL, "replicas must be >= 1");
+    if (replicas < 1 || replicas > kMaxReplicas) return fail(VELOXQ_EINVAL, "replicas must be in [1, 2^20]");
     if (steps < 1) return fail(VELOXQ_EINVAL, "steps must be >= 1");
     if (E_best_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_best_int requires an integer-valued context");
     RunParams p;
@@ -512,7 +516,8 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
                        const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best, double* E_best) {
     if (count < 0 || (count > 0 && !ctxs)) return fail(VELOXQ_EINVAL, "ctxs must hold count contexts");
     if (count == 0) return VELOXQ_OK;
-    if (replicas < 1 || steps < 1) return fail(VELOXQ_EINVAL, "replicas and steps must be >= 1");
+    if (replicas < 1 || replicas > kMaxReplicas || steps < 1)
+        return fail(VELOXQ_EINVAL, "replicas must be in [1, 2^20] and steps >= 1");
     for (int32_t m = 0; m < count; ++m)
         if (!ctxs[m]) return fail(VELOXQ_EINVAL, "context " + std::to_string(m) + " is NULL");
     RunParams p;
@@ -641,14 +646,14 @@ int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y) {
 
 int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, float* S, float* Y) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    if (R < 1 || !S || !Y) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, Y required");
+    if (R < 1 || R > kMaxReplicas || !S || !Y) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, Y required");
     if (!(std::isfinite(sigma0) && sigma0 >= 0)) return fail(VELOXQ_EINVAL, "sigma0 must be finite and >= 0");
     return launch_init_state(ctx, R, seed, sigma0, LAYOUT_RN, S, Y);
 }
 
 int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    if (R < 1 || !S || !F) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, F required");
+    if (R < 1 || R > kMaxReplicas || !S || !F) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, F required");
     if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
     if (ctx->dense) {
         if (prec == VELOXQ_PREC_FP32) return dense_field(ctx, R, S, F);
@@ -672,7 +677,7 @@ int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* 
 int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_count, int32_t K,
                      const veloxq_schedule* sched, float* S, float* Y, float* F_last) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    if (R < 1 || !S || !Y) return fail(VELOXQ_EINVAL, "R >= 1 and non-NULL S, Y required");
+    if (R < 1 || R > kMaxReplicas || !S || !Y) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, Y required");
     if (K < 1 || k_begin < 0 || k_count < 0 || (int64_t)k_begin + k_count > K)
         return fail(VELOXQ_EINVAL, "need 0 <= k_begin, 0 <= k_count, k_begin + k_count <= K");
     if (k_count == 0) return VELOXQ_OK;
@@ -732,7 +737,8 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
 int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                 int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa, double* d_knots) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
-    if (replicas < 1 || steps < 1) return fail(VELOXQ_EINVAL, "replicas and steps must be >= 1");
+    if (replicas < 1 || replicas > kMaxReplicas || steps < 1)
+        return fail(VELOXQ_EINVAL, "replicas must be in [1, 2^20] and steps >= 1");
     if (ckpt_every < 1) return fail(VELOXQ_EINVAL, "ckpt_every must be >= 1");
     RunParams p;
     VQ_TRY(resolve(ctx, sched, steps, &p));

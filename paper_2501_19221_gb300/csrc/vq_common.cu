@@ -47,13 +47,15 @@ __global__ void k_best_bits_rn(int64_t n, int32_t R, const float* __restrict__ S
     if ((threadIdx.x & 31) == 0) bits[r * nw + (i >> 5)] = word;
 }
 
-// variable-major state: lanes over replicas, 32 variables per thread
+// variable-major state: a thread makes one word (32 variables) of one
+// replica; consecutive threads take consecutive replicas of the same word.
 __global__ void k_best_bits_nr(int64_t n, int32_t R, const float* __restrict__ S, const uint8_t* __restrict__ improved,
                                uint32_t* bits) {
     const int64_t nw = (n + 31) / 32;
-    const int32_t r = blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t w = blockIdx.y;
-    if (r >= R || w >= nw || !improved[r]) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;   // over nw * R
+    const int64_t w = t / R;
+    const int32_t r = (int32_t)(t - w * R);
+    if (w >= nw || !improved[r]) return;
     uint32_t word = 0;
     for (int b = 0; b < 32; ++b) {
         const int64_t i = w * 32 + b;
@@ -100,9 +102,13 @@ __global__ void k_unpack(int64_t n, const uint32_t* __restrict__ bits, const int
     x[i] = (uint8_t)((bits[r * nw + (i >> 5)] >> (i & 31)) & 1u);
 }
 
+// 32x32 tiles, numbered along one grid axis (either side may exceed the
+// 65535 limit of the second axis: n ~ 1e8 variables by a few replicas).
 __global__ void k_transpose(const float* __restrict__ in, float* __restrict__ out, int64_t rows, int64_t cols) {
     __shared__ float tile[32][33];
-    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    const int64_t tcols = (cols + 31) / 32;
+    const int64_t tr = (int64_t)blockIdx.x / tcols;
+    const int64_t r0 = tr * 32, c0 = ((int64_t)blockIdx.x - tr * tcols) * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int64_t r = r0 + k, c = c0 + threadIdx.x;
         tile[k][threadIdx.x] = (r < rows && c < cols) ? in[r * cols + c] : 0.0f;
@@ -135,8 +141,11 @@ int launch_init_state(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, L
 }
 
 int launch_transpose(cudaStream_t st, const float* in, float* out, int64_t rows, int64_t cols) {
-    dim3 b(32, 8), g((unsigned)div_up(cols, 32), (unsigned)div_up(rows, 32));
-    k_transpose<<<g, b, 0, st>>>(in, out, rows, cols);
+    const int64_t tiles = div_up(cols, 32) * div_up(rows, 32);
+    if (tiles == 0) return VELOXQ_OK;
+    if (tiles > INT32_MAX) return fail(VELOXQ_EINVAL, "transpose: state too large");
+    dim3 b(32, 8);
+    k_transpose<<<(unsigned)tiles, b, 0, st>>>(in, out, rows, cols);
     VQ_LAUNCH_CHECK("transpose");
     return VELOXQ_OK;
 }
@@ -153,8 +162,8 @@ int launch_best_bits(veloxq_ctx* ctx, int32_t R, Layout layout, const float* S, 
         const int64_t total = (int64_t)R * nw * 32;
         k_best_bits_rn<<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(n, R, S, improved, bits);
     } else {
-        dim3 g((unsigned)div_up(R, 128), (unsigned)nw);
-        k_best_bits_nr<<<g, 128, 0, ctx->stream>>>(n, R, S, improved, bits);
+        const int64_t total = (int64_t)R * nw;
+        k_best_bits_nr<<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(n, R, S, improved, bits);
     }
     VQ_LAUNCH_CHECK("best_bits");
     return VELOXQ_OK;

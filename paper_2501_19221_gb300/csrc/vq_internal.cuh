@@ -240,6 +240,32 @@ __device__ __forceinline__ BsbPre bsb_pre(float F, float b, float a_k, float dt,
     return o;
 }
 
+// Two-lane FP32 arithmetic (the packed .f32x2 forms of sm_100 and later):
+// each lane is rounded exactly as the scalar instruction rounds it, so the
+// results equal the scalar forms bit for bit, at half the issued instructions.
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a0, float a1, float b0, float b1, float c0,
+                                     float c1) {
+    asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\tmov.b64 rc, {%6, %7};\n\t"
+        "fma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1), "f"(c0), "f"(c1));
+}
+__device__ __forceinline__ void add2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "add.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+__device__ __forceinline__ void mul2(float& d0, float& d1, float a0, float a1, float b0, float b1) {
+    asm("{\n\t.reg .b64 ra, rb, rd;\n\t"
+        "mov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+        "mul.rn.f32x2 rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+        : "=f"(d0), "=f"(d1)
+        : "f"(a0), "f"(a1), "f"(b0), "f"(b1));
+}
+
 // One ballistic-SB update of a single (variable, replica) given its field F:
 // y <- y + dt(-(a0 - a_k) s + c0 phi), s <- s + dt a0 y, wall at |s| > 1.
 __device__ __forceinline__ void bsb_update(float F, float b, float a_k, float dt, float a0, float c0,
@@ -252,6 +278,24 @@ __device__ __forceinline__ void bsb_update(float F, float b, float a_k, float dt
         s = o.sh;
         y = o.yh;
     }
+}
+
+// The same update for two replicas of one variable (b shared), in the
+// two-lane forms: the same operations in the same order as bsb_pre, hence
+// the same bits as two calls of bsb_update.
+__device__ __forceinline__ void bsb_update2(float F0, float F1, float b, float a_k, float dt, float a0, float c0,
+                                            float& s0, float& s1, float& y0, float& y1) {
+    float t0, t1, m0, m1, d0, d1, yh0, yh1, sh0, sh1;
+    add2(t0, t1, F0, F1, b, b);
+    const float nak = -__fsub_rn(a0, a_k);
+    mul2(m0, m1, nak, nak, s0, s1);
+    const float hc = __fmul_rn(-0.5f, c0);
+    fma2(d0, d1, hc, hc, t0, t1, m0, m1);
+    fma2(yh0, yh1, dt, dt, d0, d1, y0, y1);
+    const float da = __fmul_rn(dt, a0);
+    fma2(sh0, sh1, da, da, yh0, yh1, s0, s1);
+    if (fabsf(sh0) > 1.0f) { s0 = copysignf(1.0f, sh0); y0 = 0.0f; } else { s0 = sh0; y0 = yh0; }
+    if (fabsf(sh1) > 1.0f) { s1 = copysignf(1.0f, sh1); y1 = 0.0f; } else { s1 = sh1; y1 = yh1; }
 }
 
 // Vector loads/stores of V consecutive replicas.

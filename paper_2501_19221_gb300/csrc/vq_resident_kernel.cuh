@@ -1,0 +1,446 @@
+// vq_resident_kernel.cuh -- the whole run of a sparse instance in ONE launch
+// (kernel template). Each vq_resident_rc*.cu instantiates the variants for
+// one replica count per CTA, so the variants compile in parallel.
+//
+// Replicas are independent (App. B: many replicas evolved in parallel, the
+// best kept), so a CTA owns RC replicas and every variable of them: their
+// positions s live in shared memory (two buffers, variable-major [n][RC]),
+// their momenta y in registers, the CSR rows of Qs in shared memory when
+// they fit. A step needs no communication beyond the CTA: field, update,
+// walls, readout, exact energy and best-so-far all stay on chip, with one
+// __syncthreads per step. Only the final best energies and bit vectors are
+// written to global memory.
+#pragma once
+#include <cuda_fp16.h>
+
+#include <algorithm>
+
+#include "vq_internal.cuh"
+
+namespace vq {
+
+namespace resident {
+
+constexpr int kSmemMax = 232448;   // 227 KB opt-in per CTA
+
+struct ResArgs {
+    int32_t n, R, K, k_begin, k_end, readout_every, nwords;
+    int32_t ell_d;         // ELL layout: slots per row (even), else 0
+    float dt, a0, c0, sigma0;
+    uint64_t seed;
+    const int64_t* rowptr;
+    const int32_t* col;
+    const float* wf;
+    const int64_t* wfix;   // real instances: round(Qs 2^S); integer: null (2Qs = 2 wf exactly)
+    const int64_t* dfix;
+    const float* bf;
+    const float* a_table;
+    const float* S_in;     // [R][n] or null (Philox)
+    const float* Y_in;
+    float* S_out;          // [R][n] or null
+    float* Y_out;
+    float* F_out;          // [R][n] field of the last step, or null
+    int64_t* best_e;       // [R]
+    uint32_t* best_bits;   // [R][nwords]
+};
+
+// Shared-memory layout of the positions: variable-major, RC replicas per
+// variable. For RC >= 4 the 16-byte chunks of a row are XOR-swizzled across
+// the 128-byte line by the line index, so rows 4 or 8 apart (the same
+// in-line position, as in Chimera cells) land on different banks.
+template <int RC> __device__ __forceinline__ int soff(int j, int h) {
+    if constexpr (RC >= 4) {
+        const int line = (j * RC) >> 5;
+        const int c = ((j * RC) >> 2) & 7;
+        return (line << 5) + ((((c + h) ^ line) & 7) << 2);
+    } else {
+        return j * RC;
+    }
+}
+template <int RC> __device__ __forceinline__ int selem(int j, int r) {
+    if constexpr (RC >= 4) return soff<RC>(j, r >> 2) + (r & 3);
+    else return j * RC + r;
+}
+template <int RC> __device__ __forceinline__ void ld_row(const float* s, int j, float (&v)[RC]) {
+    if constexpr (RC >= 4) {
+#pragma unroll
+        for (int h = 0; h < RC / 4; ++h) {
+            const float4 a = *reinterpret_cast<const float4*>(s + soff<RC>(j, h));
+            v[4 * h] = a.x; v[4 * h + 1] = a.y; v[4 * h + 2] = a.z; v[4 * h + 3] = a.w;
+        }
+    } else if constexpr (RC == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(s + 2 * j);
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = s[j];
+    }
+}
+// The same load given the float offset of the row's first chunk (the second
+// chunk of an 8-replica row is at offset ^ 4: the chunk pair is XOR-swizzled
+// together).
+template <int RC> __device__ __forceinline__ void ld_row_at(const float* s, int o, float (&v)[RC]) {
+    if constexpr (RC == 8) {
+        const float4 a = *reinterpret_cast<const float4*>(s + o);
+        const float4 b = *reinterpret_cast<const float4*>(s + (o ^ 4));
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+    } else if constexpr (RC == 4) {
+        const float4 a = *reinterpret_cast<const float4*>(s + o);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    } else if constexpr (RC == 2) {
+        const float2 a = *reinterpret_cast<const float2*>(s + o);
+        v[0] = a.x; v[1] = a.y;
+    } else {
+        v[0] = s[o];
+    }
+}
+template <int RC> __device__ __forceinline__ void st_row(float* s, int j, const float (&v)[RC]) {
+    if constexpr (RC >= 4) {
+#pragma unroll
+        for (int h = 0; h < RC / 4; ++h)
+            *reinterpret_cast<float4*>(s + soff<RC>(j, h)) = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    } else if constexpr (RC == 2) {
+        *reinterpret_cast<float2*>(s + 2 * j) = make_float2(v[0], v[1]);
+    } else {
+        s[j] = v[0];
+    }
+}
+
+// A coupling in shared memory: column (16 bits) and value. PACKED stores the
+// value as an exact half in the upper 16 bits of one word, with the float
+// offset of the neighbour's state row in the lower 16 bits.
+//
+// ELL (integer instances whose rows are nearly equally long, such as Chimera
+// graphs and lattices): slot p of row i is word [p * n + i], so the threads of
+// a warp read consecutive words (no bank conflicts, no row pointers); rows
+// shorter than the slot count are padded with a zero weight on the row's own
+// state, which adds an exact zero to the field and to the energy.
+template <bool PACKED> struct Ent;
+template <> struct Ent<true> { uint32_t w; };
+template <> struct Ent<false> { uint16_t c; };
+
+struct SmemPlan {
+    size_t s0, s1, b, rp, col, val, bits, red, best, flag, total;
+};
+
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+__host__ __device__ inline SmemPlan plan_smem(int n, int64_t nnz, int RC, int threads, int nwords, bool csr_smem,
+                                              bool packed, int ell_d) {
+    SmemPlan p;
+    size_t o = 0;
+    const size_t rows = (size_t)((n * RC + 31) / 32 * 32);   // whole 128-byte lines (swizzle)
+    p.s0 = o; o = align16(o + sizeof(float) * rows);
+    p.s1 = o; o = align16(o + sizeof(float) * rows);
+    p.b = o; o = align16(o + sizeof(float) * (size_t)n);
+    p.rp = o; o = align16(o + (csr_smem && ell_d == 0 ? sizeof(int32_t) * (size_t)(n + 1) : 0));
+    p.col = o; o = align16(o + (ell_d > 0 ? 4 * (size_t)ell_d * n : csr_smem ? (packed ? 4 : 2) * (size_t)nnz : 0));
+    p.val = o; o = align16(o + (csr_smem && !packed ? sizeof(float) * (size_t)nnz : 0));
+    p.bits = o; o = align16(o + sizeof(uint32_t) * (size_t)RC * nwords);
+    p.red = o; o = align16(o + sizeof(int64_t) * (size_t)(threads / 32) * RC);
+    p.best = o; o = align16(o + sizeof(int64_t) * RC);
+    p.flag = o; o = align16(o + sizeof(int32_t) * RC);
+    p.total = o;
+    return p;
+}
+
+// acc[r] += w * sj[r] (two lanes per instruction where RC >= 2; the same
+// bits as scalar fmaf).
+template <int RC> __device__ __forceinline__ void acc_fma(float (&acc)[RC], float w, const float (&sj)[RC]) {
+    if constexpr (RC >= 2) {
+#pragma unroll
+        for (int r = 0; r < RC; r += 2) vqd::fma2(acc[r], acc[r + 1], w, w, sj[r], sj[r + 1], acc[r], acc[r + 1]);
+    } else {
+        acc[0] = fmaf(w, sj[0], acc[0]);
+    }
+}
+
+__device__ __forceinline__ float ent_w(uint32_t e) { return __half2float(__ushort_as_half((unsigned short)(e >> 16))); }
+
+template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, bool ELL>
+__global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int n = a.n;
+    const int T = blockDim.x;
+    const int tid = threadIdx.x;
+    const int lane = tid & 31, warp = tid >> 5;
+    const int r0 = blockIdx.x * RC;
+    const SmemPlan pl = plan_smem(n, CSR_SMEM ? a.rowptr[n] : 0, RC, T, a.nwords, CSR_SMEM, PACKED, ELL ? a.ell_d : 0);
+    float* sA = reinterpret_cast<float*>(smem + pl.s0);
+    float* sB = reinterpret_cast<float*>(smem + pl.s1);
+    float* bsh = reinterpret_cast<float*>(smem + pl.b);
+    int32_t* rps = reinterpret_cast<int32_t*>(smem + pl.rp);
+    uint16_t* cols = reinterpret_cast<uint16_t*>(smem + pl.col);
+    uint32_t* packs = reinterpret_cast<uint32_t*>(smem + pl.col);
+    float* vals = reinterpret_cast<float*>(smem + pl.val);
+    uint32_t* bits = reinterpret_cast<uint32_t*>(smem + pl.bits);
+    int64_t* red = reinterpret_cast<int64_t*>(smem + pl.red);
+    int64_t* best = reinterpret_cast<int64_t*>(smem + pl.best);
+    int32_t* flag = reinterpret_cast<int32_t*>(smem + pl.flag);
+
+    // ---- stage constants ----
+    for (int i = tid; i < n; i += T) bsh[i] = a.bf[i];
+    if constexpr (ELL) {
+        const int64_t tot = (int64_t)a.ell_d * n;
+        for (int64_t idx = tid; idx < tot; idx += T) {
+            const int p = (int)(idx / n), i = (int)(idx - (int64_t)p * n);
+            const int64_t q0 = a.rowptr[i];
+            uint32_t e = (uint32_t)soff<RC>(i, 0);   // padding: weight +0 on the own row
+            if (q0 + p < a.rowptr[i + 1])
+                e = (uint32_t)soff<RC>(a.col[q0 + p], 0) |
+                    ((uint32_t)__half_as_ushort(__float2half_rn(a.wf[q0 + p])) << 16);
+            packs[idx] = e;
+        }
+    } else if constexpr (CSR_SMEM) {
+        const int64_t nnz = a.rowptr[n];
+        for (int i = tid; i <= n; i += T) rps[i] = (int32_t)a.rowptr[i];
+        for (int64_t p = tid; p < nnz; p += T) {
+            if constexpr (PACKED) {
+                // low half: the float offset of the neighbour's first chunk in the state layout
+                packs[p] = (uint32_t)soff<RC>(a.col[p], 0) | ((uint32_t)__half_as_ushort(__float2half_rn(a.wf[p])) << 16);
+            } else {
+                cols[p] = (uint16_t)a.col[p];
+                vals[p] = a.wf[p];
+            }
+        }
+    }
+    for (int w = tid; w < RC * a.nwords; w += T) bits[w] = 0u;
+    if (tid < RC) best[tid] = INT64_MAX;
+
+    // ---- initial state: s in shared memory, y in registers ----
+    float y[RPT][RC];
+#pragma unroll
+    for (int q = 0; q < RPT; ++q) {
+        const int i = tid + q * T;
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            float s = 0.0f, yv = 0.0f;
+            if (i < n && r0 + r < a.R) {
+                if (a.S_in) {
+                    s = a.S_in[(int64_t)(r0 + r) * n + i];
+                    yv = a.Y_in[(int64_t)(r0 + r) * n + i];
+                } else {
+                    vqd::init_pair(i, r0 + r, a.seed, a.sigma0, &s, &yv);
+                }
+            }
+            if (i < n) sA[selem<RC>(i, r)] = s;
+            y[q][r] = yv;
+        }
+    }
+    __syncthreads();
+
+    float* sc = sA;
+    float* sn = sB;
+    for (int k = a.k_begin; k < a.k_end; ++k) {
+        const float a_k = __ldg(a.a_table + k);
+        const bool last = (k == a.k_end - 1);
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * T;
+            if (i < n) {
+                float acc[RC];
+#pragma unroll
+                for (int r = 0; r < RC; ++r) acc[r] = 0.0f;
+                if constexpr (ELL) {
+                    // two slots per iteration: both neighbours' loads are in flight together
+                    const uint32_t* e = packs + i;
+                    for (int p = 0; p < a.ell_d; p += 2, e += 2 * n) {
+                        const uint32_t e0 = e[0], e1 = e[n];
+                        float s0[RC], s1[RC];
+                        ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
+                        ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
+                        acc_fma<RC>(acc, ent_w(e0), s0);
+                        acc_fma<RC>(acc, ent_w(e1), s1);
+                    }
+                } else {
+                    int p0, p1;
+                    if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
+                    else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
+                    for (int p = p0; p < p1; ++p) {
+                        float w;
+                        float sj[RC];
+                        if constexpr (CSR_SMEM && PACKED) {
+                            const uint32_t e = packs[p];
+                            w = ent_w(e);
+                            ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
+                        } else {
+                            int j;
+                            if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
+                            else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                            ld_row<RC>(sc, j, sj);
+                        }
+                        acc_fma<RC>(acc, w, sj);
+                    }
+                }
+                float s[RC];
+                ld_row<RC>(sc, i, s);
+                const float b = bsh[i];
+                if constexpr (RC >= 2) {
+#pragma unroll
+                    for (int r = 0; r < RC; r += 2)
+                        vqd::bsb_update2(acc[r], acc[r + 1], b, a_k, a.dt, a.a0, a.c0, s[r], s[r + 1], y[q][r],
+                                         y[q][r + 1]);
+                } else {
+                    vqd::bsb_update(acc[0], b, a_k, a.dt, a.a0, a.c0, s[0], y[q][0]);
+                }
+                st_row<RC>(sn, i, s);
+                if (last && a.F_out) {
+#pragma unroll
+                    for (int r = 0; r < RC; ++r)
+                        if (r0 + r < a.R) a.F_out[(int64_t)(r0 + r) * n + i] = acc[r];
+                }
+            }
+        }
+        __syncthreads();
+        float* tmp = sc; sc = sn; sn = tmp;
+
+        const bool readout = (a.readout_every >= 0) &&
+                             ((k == a.K - 1) || (a.readout_every > 0 && ((k + 1) % a.readout_every) == 0));
+        if (!readout) continue;
+        // ---- exact energy of x = [s > 0], fixed point (int64 multiples of 2^-S) ----
+        int64_t part[RC];
+#pragma unroll
+        for (int r = 0; r < RC; ++r) part[r] = 0;
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * T;
+            if (i < n) {
+                float si[RC];
+                ld_row<RC>(sc, i, si);
+                bool any = false;
+#pragma unroll
+                for (int r = 0; r < RC; ++r) any |= si[r] > 0.0f;
+                if (any) {
+                    int64_t row[RC];
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) row[r] = 0;
+                    if constexpr (ELL) {
+                        // integer instances only: 2 Qs is exact from the half value
+                        const uint32_t* e = packs + i;
+                        for (int p = 0; p < a.ell_d; ++p, e += n) {
+                            const uint32_t ev = e[0];
+                            float sj[RC];
+                            ld_row_at<RC>(sc, (int)(ev & 0xFFFFu), sj);
+                            const int64_t wq = (int64_t)__float2int_rn(2.0f * ent_w(ev));
+#pragma unroll
+                            for (int r = 0; r < RC; ++r) row[r] += sj[r] > 0.0f ? wq : 0;
+                        }
+                    } else {
+                    int p0, p1;
+                    if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
+                    else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
+                    for (int p = p0; p < p1; ++p) {
+                        float w;
+                        float sj[RC];
+                        if constexpr (CSR_SMEM && PACKED) {
+                            const uint32_t e = packs[p];
+                            w = ent_w(e);
+                            ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
+                        } else {
+                            int j;
+                            if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
+                            else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                            ld_row<RC>(sc, j, sj);
+                        }
+                        // 2 Qs for integer instances (exact), the fixed-point weight otherwise
+                        const int64_t wq = a.wfix ? __ldg(a.wfix + p) : (int64_t)__float2int_rn(2.0f * w);
+#pragma unroll
+                        for (int r = 0; r < RC; ++r) row[r] += sj[r] > 0.0f ? wq : 0;
+                    }
+                    }
+                    const int64_t d = __ldg(a.dfix + i);
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) part[r] += si[r] > 0.0f ? d + row[r] : 0;
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RC; ++r) {
+            int64_t v = part[r];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red[warp * RC + r] = v;
+        }
+        __syncthreads();
+        if (tid < RC) {
+            int64_t tot = 0;
+            for (int w = 0; w < (T >> 5); ++w) tot += red[w * RC + tid];
+            const bool better = tot < best[tid];
+            if (better) best[tid] = tot;
+            flag[tid] = better ? 1 : 0;
+        }
+        __syncthreads();
+        // save the bits of improved replicas: a warp covers 32 consecutive variables
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * T;
+            const int base = warp * 32 + q * T;
+            if (base < n) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) {
+                    if (!flag[r]) continue;
+                    const bool bit = (i < n) && sc[selem<RC>(i, r)] > 0.0f;
+                    const uint32_t word = __ballot_sync(0xffffffffu, bit);
+                    if (lane == 0) bits[r * a.nwords + (base >> 5)] = word;
+                }
+            }
+        }
+        // flags are next written after at least one more __syncthreads
+    }
+    __syncthreads();
+
+    // ---- write results ----
+    if (a.best_e && tid < RC && r0 + tid < a.R) a.best_e[r0 + tid] = best[tid];
+    if (a.best_bits)
+        for (int w = tid; w < RC * a.nwords; w += T) {
+            const int r = w / a.nwords;
+            if (r0 + r < a.R) a.best_bits[(int64_t)(r0 + r) * a.nwords + (w - r * a.nwords)] = bits[w];
+        }
+    if (a.S_out) {
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * T;
+            if (i >= n) continue;
+#pragma unroll
+            for (int r = 0; r < RC; ++r)
+                if (r0 + r < a.R) {
+                    a.S_out[(int64_t)(r0 + r) * n + i] = sc[selem<RC>(i, r)];
+                    a.Y_out[(int64_t)(r0 + r) * n + i] = y[q][r];
+                }
+        }
+    }
+}
+
+using KFn = void (*)(const ResArgs);
+
+// 1024-thread CTAs keep at most 8 momenta per thread in registers (64-register
+// cap); 512-thread CTAs up to 32.
+template <int RC, int RPT> KFn pick_csr(bool csr_smem, bool packed, bool ell) {
+    constexpr int MAXT = (RC * RPT <= 8) ? 1024 : 512;
+    if constexpr (RC * RPT > 32) {
+        return nullptr;   // never planned (the momenta do not fit in registers)
+    } else {
+        if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, false>;
+        if (ell) return k_resident<RC, RPT, true, true, MAXT, true>;
+        return packed ? k_resident<RC, RPT, true, true, MAXT, false> : k_resident<RC, RPT, true, false, MAXT, false>;
+    }
+}
+
+template <int RC> KFn pick_rpt(int rpt, bool csr_smem, bool packed, bool ell) {
+    switch (rpt) {
+        case 1: return pick_csr<RC, 1>(csr_smem, packed, ell);
+        case 2: return pick_csr<RC, 2>(csr_smem, packed, ell);
+        case 4: return pick_csr<RC, 4>(csr_smem, packed, ell);
+        case 8: return pick_csr<RC, 8>(csr_smem, packed, ell);
+        default: return pick_csr<RC, 16>(csr_smem, packed, ell);
+    }
+}
+
+}  // namespace resident
+
+// one per replica count per CTA (vq_resident_rc*.cu)
+resident::KFn resident_pick_rc1(int rpt, bool csr_smem, bool packed, bool ell);
+resident::KFn resident_pick_rc2(int rpt, bool csr_smem, bool packed, bool ell);
+resident::KFn resident_pick_rc4(int rpt, bool csr_smem, bool packed, bool ell);
+resident::KFn resident_pick_rc8(int rpt, bool csr_smem, bool packed, bool ell);
+
+}  // namespace vq
