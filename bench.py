@@ -42,8 +42,8 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 285_952,
-    ("k_tc_step", "sk_n8192_bf16"): 284_011_008,
-    ("k_tc_step", "sk_n8192_fp8"): 176_409_600,
+    ("k_tc_step", "sk_n8192_fp8"): 176_619_520,
+    ("k_stream_step", "lattice_l100"): 4_125_188_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152
@@ -68,6 +68,12 @@ def workload(name: str) -> dict:
         sp = I.cubic_lattice_ising(100, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 256, "K": 400,
                 "readout_every": 50, "desc": "periodic 3-D +-J lattice L=100, int8 CSR"}
+    if name == "grad_l100":
+        sp = I.cubic_lattice_ising(100, seed=0)
+        return {"name": name, "kind": "grad", "sp": sp, "n": sp.n, "R": 256, "K": 400, "ckpt": 20,
+                "readout_every": 0, "dt": 0.5, "knots": [0.0, 0.5, 1.0],
+                "desc": "gradient of the mean relaxed energy w.r.t. dt, kappa and 3 schedule knots, periodic "
+                        "3-D +-J lattice L=100, int8 CSR, 400 unrolled steps, checkpoint every 20"}
     if name == "lattice_l464":
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
@@ -104,7 +110,7 @@ def batch_instances(w):
 
 
 def create(B, w, stream=None):
-    if w["kind"] == "ising_csr":
+    if w["kind"] in ("ising_csr", "grad"):
         sp = w["sp"]
         return B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
     if w["kind"] == "batch":
@@ -113,7 +119,7 @@ def create(B, w, stream=None):
 
 
 def input_arrays(w) -> list:
-    if w["kind"] == "ising_csr":
+    if w["kind"] in ("ising_csr", "grad"):
         sp = w["sp"]
         return [sp.rowptr, sp.col, sp.val, sp.lin]
     if w["kind"] == "batch":
@@ -123,7 +129,7 @@ def input_arrays(w) -> list:
 
 def oracle_problem(w):
     import oracle as O
-    if w["kind"] == "ising_csr":
+    if w["kind"] in ("ising_csr", "grad"):
         sp = w["sp"]
         p, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
         return p
@@ -141,7 +147,10 @@ def oracle_sample_rate(w, R_s: int, K_s: int) -> tuple:
     K = w["K"]
     knots = [0.0, (K_s - 1) / (K - 1) if K > 1 else 0.0]
     t0 = time.perf_counter()
-    O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0)
+    if w["kind"] == "grad":
+        O.bsb_grad(p, R_s, K_s, w["dt"], 1.0, c0, knots, S0, Y0)
+    else:
+        O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0)
     dt = time.perf_counter() - t0
     return p.n * R_s * K_s / dt, dt
 
@@ -206,11 +215,19 @@ class Runner:
         self.ctxs = made if self.batch else [made]
         for c in self.ctxs:
             B.veloxq_set_stream(c, stream.cuda_stream)
-        self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0))
+        self.grad = w["kind"] == "grad"
+        if self.grad:
+            self.sched = B.make_schedule(readout_every=0, dt=w["dt"], knots=w["knots"])
+        else:
+            self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0))
         self.n_total = sum(c.info.n for c in self.ctxs)
         self.nnz_field = sum(c.info.nnz_field for c in self.ctxs)
 
     def solve(self, seed, want_x=False):
+        if self.grad:
+            self.last_grad = self.B.veloxq_grad(self.ctxs[0], self.w["R"], self.w["K"], self.sched, seed,
+                                                self.w["ckpt"])
+            return self.last_grad["loss"]
         if self.batch:
             out = self.B.veloxq_solve_batch(self.ctxs, self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)
             self.last_batch_E = out["E"]
@@ -235,6 +252,17 @@ def roofline(B, w, runner, path, main_ms, main_launches):
         return {"kernel": "k_batch", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
                 "algorithmic_bytes_per_launch": hbm, "ms_per_launch": main_ms}
+    if runner.grad:
+        # one reverse step: k_adj_a reads s_k, y_k, lam_s, lam_y and writes g_phi, the local g_s and lam_y
+        # (28 B per variable-replica); k_adj_b reads the local g_s and g_phi (gathered, from L2 after one
+        # DRAM read) and writes lam_s (12 B); each gathers through the int8 couplings and columns once
+        hbm_bytes = 40 * n * R + 2 * 5 * runner.nnz_field
+        per = main_ms / K
+        ach = hbm_bytes / (per / 1e3) / 1e9
+        return {"kernel": "k_adj_a+k_adj_b", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
+                "algorithmic_bytes_per_launch": hbm_bytes, "ms_per_launch": per,
+                "launch": "one reverse step (k_adj_a, k_adj_b and the 1-block k_adj_reduce)"}
     if path == B.VELOXQ_PATH_RESIDENT:
         smem_bytes = (runner.nnz_field + 2 * n) * 4 * R * K
         peak = SMEM_BYTES_PER_CLK_PER_SM * NUM_SMS * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
@@ -370,7 +398,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_iters = max(1, min(args.steps, 3 if run.batch else 5))
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in input_arrays(w)]
     h2d = int(sum(a.nbytes for a in pinned))
-    if w["kind"] == "ising_csr":
+    if w["kind"] in ("ising_csr", "grad"):
         pw = dict(w)
         pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
     elif w["kind"] == "batch":
@@ -385,10 +413,14 @@ def run_ours(args, rank, world, local_rank):
         r2.destroy()
     e2e_s = (time.perf_counter() - t0) / e2e_iters
     nctx = len(run.ctxs)
-    d2h = n + (0 if run.batch else 8 * R + 8 * R) + 32 * nctx   # best x, per-replica energies, argmin records
+    if run.grad:
+        d2h = 8 * (2 + w["K"] + 8 + len(w["knots"]))             # loss, d_dt, d_c0, per-step and knot sums
+    else:
+        d2h = n + (0 if run.batch else 8 * R + 8 * R) + 32 * nctx   # best x, per-replica energies, argmin records
     e2e = {"value": world * n * R * K / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
-           "includes": "context creation (H2D copy, device ingest, power iteration) + solve + D2H of results"}
+           "includes": "context creation (H2D copy, device ingest, power iteration) + "
+                       + ("gradient (forward, recompute, reverse)" if run.grad else "solve") + " + D2H of results"}
 
     roof = roofline(B, w, run, path, statistics.mean(mains), main_launches)
     roof["traffic"] = NCU_TRAFFIC.get((roof["kernel"], w["name"]))
@@ -400,13 +432,15 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not run.batch:
         # calibrate on a short run, then time about 12 s of oracle work
-        R_s = min(R, 64)
-        rate0, _ = oracle_sample_rate(w, min(R, 4), min(K, 20))
-        K_s2 = int(min(K, max(20, 12.0 * rate0 / (n * R_s))))
+        R_s = min(R, 4 if run.grad else 64)
+        K_c = min(K, 4 if run.grad else 20)
+        rate0, _ = oracle_sample_rate(w, min(R, 4), K_c)
+        K_s2 = int(min(K, max(K_c, 12.0 * rate0 / (n * R_s))))
         rate, dt = oracle_sample_rate(w, R_s, K_s2)
+        what = "reverse-mode gradient over" if run.grad else "solve of"
         cpu = {"value": rate, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
-               "sample": f"{R_s} replicas x first {K_s2} of {K} steps of the same instance, FP64, one thread "
-                         f"({dt:.1f} s)"}
+               "sample": f"{what} {R_s} replicas x first {K_s2} of {K} steps of the same instance, FP64, "
+                         f"one thread ({dt:.1f} s)"}
 
     if rank == 0:
         prec_name = {0: "f32", 1: "bf16", 2: "fp8e4m3"}[w.get("prec", 0)]
@@ -426,7 +460,14 @@ def run_ours(args, rank, world, local_rank):
             "quality": {"best_energy_last_step": results[-1]},
             "wall_s_timed_region": wall,
         }
-        if not run.batch:
+        if run.grad:
+            g = run.last_grad
+            line["quality"] = {"loss": g["loss"], "d_dt": g["d_dt"], "d_kappa": g["d_kappa"],
+                               "d_knots": [float(v) for v in g["d_knots"]]}
+            line["config"]["checkpoint_every"] = w["ckpt"]
+            line["config"]["counts"] = ("forward steps: one gradient = forward, checkpointed recompute and "
+                                        "reverse sweep over K steps")
+        elif not run.batch:
             off = run.ctxs[0].info.ising_offset
             line["quality"]["best_ising_energy_last_step"] = 2 * results[-1] + off
         else:
@@ -444,7 +485,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = workload(args.workload)
-    R_s, K_s = min(w["R"], 32), min(w["K"], 1000)
+    # each step about 3 s of oracle work: up to 32 replicas (4 for the gradient) x the first K_s steps
+    R_s = min(w["R"], 4 if w["kind"] == "grad" else 32)
+    rate0, _ = oracle_sample_rate(w, R_s, min(w["K"], 2))
+    K_s = int(min(w["K"], 1000, max(1, 3.0 * rate0 / (w["n"] * R_s))))
     for _ in range(args.warmup):
         oracle_sample_rate(w, R_s, min(K_s, 20))
     times = []
@@ -453,7 +497,8 @@ def run_reference(args, rank, world):
         times.append(dt)
     total = sum(times)
     value = w["n"] * R_s * K_s * args.steps / total
-    sample = f"{R_s} replicas x first {K_s} of {w['K']} steps per step, FP64 oracle, one thread"
+    what = "reverse-mode gradient, " if w["kind"] == "grad" else ""
+    sample = f"{what}{R_s} replicas x first {K_s} of {w['K']} steps per step, FP64 oracle, one thread"
     line = {"impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",

@@ -101,10 +101,12 @@ typedef struct {
     double ising_offset;    /* Ising contexts: H(s) = 2 E(x) + ising_offset; else 0 */
 } veloxq_info;
 
-/* Device timing of the last veloxq_solve on a context, from CUDA events
- * recorded on the stream the kernels run on. */
+/* Device timing of the last veloxq_solve or veloxq_grad on a context, from
+ * CUDA events recorded on the stream the kernels run on. For veloxq_grad,
+ * ms_main is the reverse sweep (the adjoint step kernels, 3 launches per
+ * step) and path is VELOXQ_PATH_STREAM. */
 typedef struct {
-    double ms_total;        /* first to last kernel of the solve */
+    double ms_total;        /* first to last kernel of the solve (or gradient) */
     double ms_main;         /* the integration: the resident kernel, or the captured steps up to the last one */
     int64_t launches;       /* kernels this library launched for the solve */
     int32_t path;           /* veloxq_path that ran */
@@ -166,7 +168,7 @@ int veloxq_get_info(veloxq_ctx* ctx, veloxq_info* info);
  * default stream; on a non-NULL stream it runs (and is graph-captured) there. */
 int veloxq_set_stream(veloxq_ctx* ctx, void* stream);
 
-/* Timing of the last veloxq_solve on ctx (EINVAL if none ran yet). */
+/* Timing of the last veloxq_solve or veloxq_grad on ctx (EINVAL if none ran yet). */
 int veloxq_last_timing(veloxq_ctx* ctx, veloxq_timing* timing);
 
 /* ---------------------------------------------------------------------------

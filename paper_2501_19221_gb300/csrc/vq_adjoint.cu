@@ -262,7 +262,7 @@ int adj_dispatch_step(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, co
 // Checkpointed forward + reverse sweep on the streaming sparse path.
 // a_table (device) holds a_k; a_host the same values on the host.
 int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vector<float>& a_host, uint64_t seed,
-                int32_t C, double* loss, double* d_dt, double* d_c0, double* d_knots, int n_knots) {
+                int32_t C, double* loss, double* d_dt, double* d_c0, double* d_knots, int n_knots, AdjTiming* tm) {
     const int64_t n = ctx->n, nR = n * (int64_t)R;
     const int K = p.K;
     const int M = (int)div_up(K, C);                  // checkpoints: states before steps 0, C, 2C, ...
@@ -289,6 +289,18 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
     double* dkn = lossd + 8;
     const float* at = ctx->a_table.as<float>();
     cudaStream_t st = ctx->stream;
+    // events: [0] start, [1] end, then (before, after) each segment's reverse steps
+    struct Events {
+        std::vector<cudaEvent_t> e;
+        ~Events() {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } ev;
+    ev.e.assign((size_t)(2 + 2 * M), nullptr);
+    for (cudaEvent_t& x : ev.e) VQ_CUDA(cudaEventCreate(&x));
+    VQ_CUDA(cudaEventRecord(ev.e[0], st));
+    int64_t launches = 0;
     VQ_CUDA(cudaMemsetAsync(acc, 0, sizeof(double) * (size_t)(2 + K), st));
 
     // ---- forward with checkpoints (two working buffers in seg[0], seg[1]) ----
@@ -304,6 +316,7 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
         VQ_TRY(stream_step_y(ctx, R, cS, nS, cY, cY, at, k, p.dt, p.a0, p.c0, nullptr));
         std::swap(cS, nS);
     }
+    launches += 1 + K + 2;   // init, forward steps, loss and its total
     // ---- loss and seed ----
     if (ctx->w8.p) VQ_TRY(adj_dispatch_loss<int8_t>(ctx, V, R, ctx->w8.as<int8_t>(), 0.5f, cS, lam_s, lam_y, parts));
     else VQ_TRY(adj_dispatch_loss<float>(ctx, V, R, ctx->wf.as<float>(), 1.0f, cS, lam_s, lam_y, parts));
@@ -318,6 +331,8 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
         VQ_CUDA(cudaMemcpyAsync(sgY(0), ckY(m), blk, cudaMemcpyDeviceToDevice, st));
         for (int t = 0; t < k1 - k0 - 1; ++t)
             VQ_TRY(stream_step_y(ctx, R, sgS(t), sgS(t + 1), sgY(t), sgY(t + 1), at, k0 + t, p.dt, p.a0, p.c0, nullptr));
+        launches += k1 - k0 - 1 + 3 * (k1 - k0);
+        VQ_CUDA(cudaEventRecord(ev.e[2 + 2 * m], st));
         for (int k = k1 - 1; k >= k0; --k) {
             const int t = k - k0;
             if (ctx->w8.p)
@@ -329,12 +344,26 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
             k_adj_reduce<<<1, kAdjThreads, 0, st>>>(parts3, kAdjBlocks, k, acc);
             VQ_LAUNCH_CHECK("adjoint reduce");
         }
+        VQ_CUDA(cudaEventRecord(ev.e[3 + 2 * m], st));
     }
     k_adj_knots<<<1, 64, 0, st>>>(K, n_knots, acc + 2, dkn);
     VQ_LAUNCH_CHECK("adjoint knots");
+    launches += 1;
+    VQ_CUDA(cudaEventRecord(ev.e[1], st));
     std::vector<double> h((size_t)(2 + K + 8 + n_knots));
     VQ_CUDA(cudaMemcpyAsync(h.data(), acc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, st));
     VQ_CUDA(cudaStreamSynchronize(st));
+    if (tm) {
+        VQ_CUDA(cudaEventElapsedTime(&tm->ms_total, ev.e[0], ev.e[1]));
+        tm->ms_reverse = 0.f;
+        for (int m = 0; m < M; ++m) {
+            float x = 0.f;
+            VQ_CUDA(cudaEventElapsedTime(&x, ev.e[2 + 2 * m], ev.e[3 + 2 * m]));
+            tm->ms_reverse += x;
+        }
+        tm->launches = launches;
+        tm->reverse_launches = 3 * (int64_t)K;
+    }
     if (loss) *loss = ctx->K0 + h[2 + K] / (double)R;
     if (d_dt) *d_dt = h[0];
     if (d_c0) *d_c0 = h[1];

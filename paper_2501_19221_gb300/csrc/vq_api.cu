@@ -768,7 +768,14 @@ int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_s
                                t.as<float>() + 2 * ctx->n * (int64_t)replicas));
     }
     double dc0 = 0.0;
-    VQ_TRY(adjoint_run(ctx, replicas, p, a_host, seed, ckpt_every, loss, d_dt, &dc0, d_knots, nk));
+    AdjTiming tm;
+    VQ_TRY(adjoint_run(ctx, replicas, p, a_host, seed, ckpt_every, loss, d_dt, &dc0, d_knots, nk, &tm));
+    ex->timing.ms_total = tm.ms_total;
+    ex->timing.ms_main = tm.ms_reverse;
+    ex->timing.launches = tm.launches;
+    ex->timing.path = VELOXQ_PATH_STREAM;
+    ex->timing.main_launches = tm.reverse_launches;
+    ex->timed = true;
     if (d_kappa) {
         // c0 = kappa / rho(J) = 2 kappa / rho(Qoff) unless c0 was given
         const bool given = sched && sched->c0 > 0;

@@ -170,9 +170,14 @@ bool batch_supported(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const Ru
 int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p, uint64_t seed, cudaStream_t st,
               int stages, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main);
 
-// adjoint of the step (vq_adjoint.cu)
+// adjoint of the step (vq_adjoint.cu); the timing covers the whole gradient
+// and, separately, the reverse-step kernels (k_adj_a, k_adj_b, k_adj_reduce)
+struct AdjTiming {
+    float ms_total = 0.f, ms_reverse = 0.f;
+    int64_t launches = 0, reverse_launches = 0;
+};
 int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vector<float>& a_host, uint64_t seed,
-                int32_t C, double* loss, double* d_dt, double* d_c0, double* d_knots, int n_knots);
+                int32_t C, double* loss, double* d_dt, double* d_c0, double* d_knots, int n_knots, AdjTiming* tm);
 
 // dense tensor-core kernels (vq_tc.cu)
 int64_t tc_pad(int64_t n);

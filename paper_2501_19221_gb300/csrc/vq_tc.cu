@@ -4,19 +4,25 @@
 //
 // D[i][r] = sum_j Qop[i][j] Sop[r][j]: M = variables (rows of Qoff), N =
 // replicas, K = variables. Both operands are K-major (Qoff row-major, S
-// replica-major), tiles of 128 x 256 per CTA, 128-byte K blocks with the
-// 128-byte swizzle, a 4-stage TMA -> MMA pipeline.
+// replica-major), 128-byte K blocks with the 128-byte swizzle.
+// CTA pairs (clusters of 2, tcgen05 cta_group::2): a pair computes a
+// 256 x 256 tile with M = 256 MMAs issued by the even CTA. Each CTA stages
+// its own 128 rows of Qoff and its own 128 replicas of S, so a stage is
+// 32 KB per CTA and 6 stages are in flight; each CTA's tensor memory holds
+// the accumulator of its 128 rows for all 256 replicas.
 //   BF16: Qop = bf16(Qoff), Sop = bf16(s)                (kind::f16)
 //   FP8 : Qop = e4m3(Qoff_ij / q_i), q_i = amax_i / 448,
 //         Sop = e4m3(448 s)  (|s| <= 1 by the walls)       (kind::f8f6f4)
 //         F_i = acc q_i / 448
-// The kernel is persistent: one CTA per SM walks the tiles t = blockIdx.x,
-// + gridDim.x, ...; two accumulator buffers in tensor memory let the
+// The kernel is persistent: one CTA per SM, the pairs walk the pair tiles
+// t = pair, + pairs, ...; two accumulator buffers in tensor memory let the
 // epilogue of one tile overlap the main loop of the next.
-// Warp roles: warp 0 issues TMA, warp 1 allocates tensor memory and issues
-// the MMAs, warps 2-9 read the accumulator tile (a 32-lane quarter and half
-// of the columns each) and run the update for their rows. Every wait is bounded: on timeout the
-// kernel records a code in the error word and returns.
+// Warp roles: warp 0 issues TMA (both CTAs; completion is counted on the
+// even CTA's barrier), warp 1 allocates tensor memory (both CTAs) and issues
+// the MMAs (even CTA), warps 2-9 read the accumulator tile (a 32-lane quarter
+// and half of the columns each) and run the update for their rows. Every
+// wait is bounded: on timeout the kernel records a code in the error word
+// and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
@@ -30,8 +36,9 @@ namespace vq {
 
 namespace {
 
-constexpr int BM = 128, BN = 256, BKB = 128, STAGES = 4;
-constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BN * BKB, STAGE_BYTES = A_BYTES + B_BYTES;
+// BM rows per CTA (2 BM per pair), BN replicas per pair (BN / 2 staged per CTA)
+constexpr int BM = 128, BN = 256, BNH = BN / 2, BKB = 128, STAGES = 6;
+constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BNH * BKB, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
@@ -56,12 +63,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// The same with cluster-scope acquire, for barriers the peer CTA arrives on.
+__device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // Bounded wait: false (and the error word set) if the phase does not complete
 // within the budget or another thread already gave up.
+template <bool CLUSTER = false>
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
     const long long t0 = clock64();
     uint32_t spins = 0;
-    while (!mbar_try_wait(bar, parity)) {
+    while (!(CLUSTER ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity))) {
         if ((++spins & 1023u) == 0) {
             if (*(volatile int*)err) return false;
             if (clock64() - t0 > kWaitCycles) {
@@ -73,23 +93,47 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* e
     return true;
 }
 
-__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+// ---- cluster of two CTAs ----
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// shared::cluster address of the same shared variable in CTA `rank`
+__device__ __forceinline__ uint32_t mapa(uint32_t a, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(a), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t cl_addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cl_addr) : "memory");
+}
+
+// 2-D tile load into this CTA's shared memory; completion is counted on the
+// barrier at cluster address `bar_cl` (the even CTA's barrier of the pair).
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, int x, int y, uint32_t bar_cl) {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 "
+        "[%0], [%1, {%2, %3}], [%4];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cl)
         : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+// Tensor memory of a CTA pair: one warp of each CTA allocates (and frees)
+// together; both CTAs receive the same column address.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)), "r"(ncols)
                  : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
 // Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, 8-row
@@ -105,34 +149,43 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
     return d;
 }
 
-// Instruction descriptor: FP32 accumulator, A/B format, K-major, N, M.
+// Instruction descriptor: FP32 accumulator, A/B format, K-major, N, M (the
+// pair's M = 2 BM).
 template <int PREC> __host__ __device__ constexpr uint32_t instr_desc() {
     return (1u << 4)                                   // D format F32
            | ((PREC == 1 ? 1u : 0u) << 7)              // A: BF16 (f16 kind) / E4M3 (f8f6f4 kind)
            | ((PREC == 1 ? 1u : 0u) << 10)             // B: same
            | ((uint32_t)(BN >> 3) << 17)               // N
-           | ((uint32_t)(BM >> 4) << 24);              // M
+           | ((uint32_t)((2 * BM) >> 4) << 24);        // M
 }
 
+// M = 256 MMA of the pair, issued by the even CTA: A rows from both CTAs'
+// shared memory, B (replicas) likewise, the accumulator in both CTAs'
+// tensor memory.
 template <int PREC>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accum) {
     if constexpr (PREC == 1) {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
             ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
             ::"r"(d_tmem), "l"(a), "l"(b), "r"(idesc), "r"(accum)
             : "memory");
     }
 }
-__device__ __forceinline__ void umma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
+// Arrive on the barrier at the same offset in both CTAs once the MMAs issued
+// so far have completed.
+__device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
+    asm volatile(
+        "{\n\t.reg .b16 m;\n\tmov.b16 m, 3;\n\t"
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], m;\n\t}\n"
+        ::"r"(smem_u32(bar))
+        : "memory");
 }
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
@@ -186,19 +239,22 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                                                     const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;      // [2] accumulator buffer ready for the epilogue
-    uint64_t* acce = accf + 2;            // [2] accumulator buffer drained by the epilogue
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);   // even CTA: both stages landed
+    uint64_t* empty = full + STAGES;      // both CTAs: stage consumed by the MMAs
+    uint64_t* accf = empty + STAGES;      // [2] both CTAs: accumulator buffer ready for the epilogue
+    uint64_t* acce = accf + 2;            // [2] even CTA: buffer drained by both CTAs' epilogues
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(acce + 2);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const bool leader = rank == 0;
+    const int pair = blockIdx.x >> 1, pairs = gridDim.x >> 1;
     constexpr int EB = PREC == 1 ? 2 : 1;
     constexpr int BK = BKB / EB;                 // elements per K block
     constexpr int KSTEP_B = 32;                  // bytes of K per MMA (16 bf16 / 32 e4m3)
     const int num_kb = (a.n_pad + BK - 1) / BK;
-    const int MT = (a.n + BM - 1) / BM, NT = (a.R + BN - 1) / BN;
-    const int tiles = MT * NT;                   // tile t: row block t / NT, replica block t % NT
+    const int MT = (a.n + 2 * BM - 1) / (2 * BM), NT = (a.R + BN - 1) / BN;
+    const int tiles = MT * NT;                   // pair tile t: rows (t / NT) * 2BM, replicas (t % NT) * BN
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -207,14 +263,14 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 8);
+            mbar_init(&acce[b], 16);
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     if (warp == 1) tmem_alloc(tmem_slot, 2 * BN);
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();                              // both CTAs' barriers exist before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -222,54 +278,57 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-                const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+            for (int t = pair; t < tiles && ok; t += pairs) {
+                const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN + (int)rank * BNH;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     const uint32_t s = it % STAGES, u = it / STAGES;
-                    if (u > 0 && !mbar_wait(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) { ok = false; break; }
+                    if (u > 0 && !mbar_wait<true>(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) { ok = false; break; }
                     uint8_t* sa = smem + s * STAGE_BYTES;
-                    mbar_expect_tx(&full[s], STAGE_BYTES);
-                    tma_load_2d(sa, &tmA, kb * BK, m0, &full[s]);
-                    tma_load_2d(sa + A_BYTES, &tmB, kb * BK, n0, &full[s]);
+                    if (leader) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
+                    const uint32_t fb = mapa(smem_u32(&full[s]), 0);
+                    tma_load_2d_pair(sa, &tmA, kb * BK, m0, fb);
+                    tma_load_2d_pair(sa + A_BYTES, &tmB, kb * BK, n0, fb);
                     ++it;
                 }
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             constexpr uint32_t idesc = instr_desc<PREC>();
             uint32_t it = 0, tt = 0;
             bool ok = true;
-            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++tt) {
+            for (int t = pair; t < tiles && ok; t += pairs, ++tt) {
                 const uint32_t b = tt & 1u;
-                if (tt >= 2 && !mbar_wait(&acce[b], ((tt >> 1) - 1) & 1u, a.err, TC_ERR_MMA)) { ok = false; break; }
+                if (tt >= 2 && !mbar_wait<true>(&acce[b], ((tt >> 1) - 1) & 1u, a.err, TC_ERR_MMA)) { ok = false; break; }
                 tc_fence_after();
                 const uint32_t d = tmem + b * BN;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     const uint32_t s = it % STAGES, u = it / STAGES;
-                    if (!mbar_wait(&full[s], u & 1, a.err, TC_ERR_MMA)) { ok = false; break; }
+                    if (!mbar_wait<true>(&full[s], u & 1, a.err, TC_ERR_MMA)) { ok = false; break; }
                     tc_fence_after();
                     const uint8_t* sa = smem + s * STAGE_BYTES;
 #pragma unroll
                     for (int kk = 0; kk < BKB / KSTEP_B; ++kk)
                         umma<PREC>(d, smem_desc(sa + kk * KSTEP_B), smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc,
                                    (kb | kk) != 0 ? 1u : 0u);
-                    umma_commit(&empty[s]);
+                    umma_commit_pair(&empty[s]);
                     ++it;
                 }
-                if (ok) umma_commit(&accf[b]);
+                if (ok) umma_commit_pair(&accf[b]);
             }
         }
     } else {
-        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31; the
-        // first four epilogue warps take columns [0, BN/2), the next four the rest
+        // epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. +31 (this
+        // CTA's rows); the first four epilogue warps take replica columns
+        // [0, BN/2), the next four the rest
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
+        const uint32_t acce_cl = mapa(smem_u32(&acce[0]), 0);
         uint32_t tt = 0;
-        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++tt) {
+        for (int t = pair; t < tiles; t += pairs, ++tt) {
             const uint32_t b = tt & 1u;
-            const int m0 = (t / NT) * BM, n0 = (t % NT) * BN;
+            const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN;
             const int row = m0 + q * 32 + lane;
             const bool row_ok = row < a.n;
             float fscale = 1.0f, bi = 0.0f;
@@ -277,7 +336,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                 if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
                 if constexpr (!FIELD_ONLY) bi = __ldg(a.bf + row);
             }
-            if (!mbar_wait(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
+            if (!mbar_wait<true>(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
             tc_fence_after();
             constexpr int CW = 16;   // columns per tensor-memory load
 #pragma unroll 1
@@ -313,14 +372,17 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     }
                 }
             }
-            // hand the accumulator buffer back to the MMA warp
+            // hand the accumulator buffer back to the even CTA's MMA thread
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acce[b])) : "memory");
+            if (lane == 0) mbar_arrive_remote(acce_cl + b * 8);
         }
     }
+    // neither CTA leaves while the other may still read its shared memory or
+    // arrive on its barriers
     tc_fence_before();
     __syncthreads();
+    cluster_sync();
     tc_fence_after();
     if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
@@ -431,8 +493,8 @@ int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtens
     const int64_t n = ctx->n, np = tc_pad(n);
     void* qb = prec == VELOXQ_PREC_BF16 ? ctx->qoff16.p : ctx->qoff8.p;
     VQ_TRY(make_map(mq, qb, prec, n, np, BM));
-    VQ_TRY(make_map(ms0, sop0, prec, R, np, BN));
-    if (sop1) VQ_TRY(make_map(ms1, sop1, prec, R, np, BN));
+    VQ_TRY(make_map(ms0, sop0, prec, R, np, BNH));
+    if (sop1) VQ_TRY(make_map(ms1, sop1, prec, R, np, BNH));
     return VELOXQ_OK;
 }
 
@@ -473,21 +535,45 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     a.a_table = a_table;
     a.F_out = F_out;
     a.err = err;
-    // persistent: one CTA per SM (at most one per tile), tiles strided over the CTAs
+    // persistent: one CTA per SM in clusters of two (at most one pair per
+    // pair tile), pair tiles strided over the pairs
     static int sms = 0;
     if (!sms) {
         int dev = 0;
         VQ_CUDA(cudaGetDevice(&dev));
         VQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     }
-    const int64_t tiles = div_up(ctx->n, BM) * div_up(R, BN);
-    dim3 grid((unsigned)std::min<int64_t>(tiles, sms));
+    const int64_t tiles = div_up(ctx->n, 2 * BM) * div_up(R, BN);
     const bool field_only = S_nxt == nullptr;
     void (*fn)(const CUtensorMap, const CUtensorMap, const TcArgs);
     if (prec == VELOXQ_PREC_BF16) fn = field_only ? k_tc_step<1, true> : k_tc_step<1, false>;
     else fn = field_only ? k_tc_step<2, true> : k_tc_step<2, false>;
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
-    fn<<<grid, 320, TC_SMEM, ctx->stream>>>(mq, ms_cur, a);
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(320);
+    cfg.dynamicSmemBytes = TC_SMEM;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    // as many pairs as can be resident at once (one CTA per SM)
+    static int max_pairs = 0;
+    if (!max_pairs) {
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
+        int c = 0;
+        if (cudaOccupancyMaxActiveClusters(&c, fn, &cfg) != cudaSuccess || c < 1) {
+            cudaGetLastError();
+            c = sms / 2;
+        }
+        max_pairs = std::min(c, sms / 2);
+    }
+    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles, max_pairs));
+    cfg.gridDim = dim3((unsigned)(2 * pairs));
+    VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms_cur, a));
     VQ_LAUNCH_CHECK("tc step");
     return VELOXQ_OK;
 }
