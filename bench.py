@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -42,8 +43,9 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 285_952,
-    ("k_tc_step", "sk_n8192_fp8"): 176_619_520,
-    ("k_stream_step", "lattice_l100"): 4_125_188_000,
+    ("k_tc_step", "sk_n8192_fp8"): 178_763_520,
+    ("k_tc_step", "sk_n8192_bf16"): 286_354_432,
+    ("k_stream_step", "lattice_l100"): 4_126_558_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152
@@ -136,16 +138,19 @@ def oracle_problem(w):
     return O.problem_from_dense(w["Q"], w["c"])
 
 
-def oracle_sample_rate(w, R_s: int, K_s: int) -> tuple:
+def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0, barrier=None) -> tuple:
     """Spin-updates/s of the FP64 oracle (single thread) on R_s replicas x the
-    first K_s steps of the workload's schedule."""
+    first K_s steps of the workload's schedule. With a barrier, the timed run
+    starts when every process of the group has finished its set-up."""
     import oracle as O
     p = oracle_problem(w)
     rho = O.spectral_radius(p) if p.n <= 6000 else 6.0
     c0 = 2.0 / rho
-    S0, Y0 = O.init_state(p.n, R_s, 0, 0.1)
+    S0, Y0 = O.init_state(p.n, R_s, seed, 0.1)
     K = w["K"]
     knots = [0.0, (K_s - 1) / (K - 1) if K > 1 else 0.0]
+    if barrier is not None:
+        barrier.wait()
     t0 = time.perf_counter()
     if w["kind"] == "grad":
         O.bsb_grad(p, R_s, K_s, w["dt"], 1.0, c0, knots, S0, Y0)
@@ -153,6 +158,35 @@ def oracle_sample_rate(w, R_s: int, K_s: int) -> tuple:
         O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0)
     dt = time.perf_counter() - t0
     return p.n * R_s * K_s / dt, dt
+
+
+_BARRIER = None
+
+
+def _oracle_init(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_worker(job):
+    name, R_s, K_s, seed = job
+    return oracle_sample_rate(workload(name), R_s, K_s, seed, _BARRIER)
+
+
+def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
+    """The same oracle sample run as `procs` independent processes at once
+    (replica-parallel over the host cores, each process its own seed, the
+    timed runs released together): total spin-updates / the longest run."""
+    import multiprocessing as mp
+    if procs <= 1:
+        rate, dt = oracle_sample_rate(w, R_s, K_s)
+        return rate, dt, 1
+    ctx = mp.get_context("spawn")          # never fork a process that has touched the GPU
+    barrier = ctx.Barrier(procs)
+    with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier,)) as pool:
+        res = pool.map(_oracle_worker, [(w["name"], R_s, K_s, s) for s in range(procs)], chunksize=1)
+    wall = max(dt for _, dt in res)
+    return w["n"] * R_s * K_s * procs / wall, wall, procs
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -222,6 +256,10 @@ class Runner:
             self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0))
         self.n_total = sum(c.info.n for c in self.ctxs)
         self.nnz_field = sum(c.info.nnz_field for c in self.ctxs)
+        self.regular = False
+        if "sp" in w:
+            deg = np.diff(np.asarray(w["sp"].rowptr))
+            self.regular = bool(deg.size > 0 and np.all(deg == deg[0]))
 
     def solve(self, seed, want_x=False):
         if self.grad:
@@ -290,7 +328,9 @@ def roofline(B, w, runner, path, main_ms, main_launches):
                 "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x max clock",
                 "algorithmic_flops_per_launch": flops, "ms_per_launch": per}
-    hbm_bytes = 16 * n * R + 5 * runner.nnz_field + 8 * (n + 1)      # state r/w + int8 CSR + rowptr, per step
+    # state r/w + int8 couplings and columns, per step; the row pointers are
+    # read only when rows differ in length (rows of equal length start at i * degree)
+    hbm_bytes = 16 * n * R + 5 * runner.nnz_field + (0 if runner.regular else 8 * (n + 1))
     per = main_ms / max(1, main_launches)
     ach = hbm_bytes / (per / 1e3) / 1e9
     return {"kernel": "k_stream_step", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -339,6 +379,49 @@ def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200):
             out[f"speedup_{name}"] = (t32 / best["ms"]) if best else None
     ctx.destroy()
     return out
+
+
+def _tts99(t_ms: float, p: float):
+    """Time to solution with 99% confidence from one run's time and its
+    success probability: t ln(0.01) / ln(1 - p) (t itself once p >= 0.99)."""
+    if p <= 0.0:
+        return None
+    if p >= 0.99:
+        return t_ms
+    return t_ms * math.log(0.01) / math.log(1.0 - p)
+
+
+def tts_study(B, run, w, stream, seeds):
+    """TTS99 against the known ground energy: the dense n = 20 instance
+    (enumerated, tests/golden/dense_n20_ground.txt) over `seeds` solves, or
+    each Wishart instance's planted energy over `seeds` batch solves."""
+    import torch
+    times, finals = [], []
+    with torch.cuda.stream(stream):
+        for i in range(seeds):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            E = run.solve(5000 + i)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+            finals.append(list(run.last_batch_E) if run.batch else E)
+    t = float(np.median(times))
+    if not run.batch:
+        with open(os.path.join(ROOT, "tests", "golden", "dense_n20_ground.txt")) as f:
+            E_min = [int(line.split()[1]) for line in f if line.startswith("E_min")][0]
+        p = float(np.mean([E == E_min for E in finals]))
+        return {"target": "ground energy by enumeration", "E_target": E_min, "runs": seeds, "p_success": p,
+                "ms_per_run": t, "tts99_ms": _tts99(t, p)}
+    hits = np.zeros(len(run.ctxs))
+    for Es in finals:
+        for m, (E, c, e0) in enumerate(zip(Es, run.ctxs, w["E0"])):
+            hits[m] += (2 * E + c.info.ising_offset - e0) <= 1e-9 * abs(e0)
+    p = hits / seeds
+    tts = [_tts99(t, float(q)) for q in p if q > 0]
+    return {"target": "planted energy of each instance", "runs": seeds, "ms_per_batch_run": t,
+            "instances": len(p), "instances_solved": int(np.sum(p > 0)),
+            "tts99_ms_median_over_solved": float(np.median(tts)) if tts else None}
 
 
 def run_ours(args, rank, world, local_rank):
@@ -427,6 +510,9 @@ def run_ours(args, rank, world, local_rank):
     ttt = None
     if args.ttt and rank == 0:
         ttt = time_to_target(B, stream, seeds=args.ttt_seeds)
+    tts = None
+    if rank == 0 and w["name"] in ("dense_n20", "wishart_b512"):
+        tts = tts_study(B, run, w, stream, seeds=32 if w["name"] == "dense_n20" else 4)
 
     # ---- CPU baseline: the oracle, single thread, bounded sample ----
     cpu = None
@@ -436,11 +522,14 @@ def run_ours(args, rank, world, local_rank):
         K_c = min(K, 4 if run.grad else 20)
         rate0, _ = oracle_sample_rate(w, min(R, 4), K_c)
         K_s2 = int(min(K, max(K_c, 12.0 * rate0 / (n * R_s))))
-        rate, dt = oracle_sample_rate(w, R_s, K_s2)
+        rate1, dt1 = oracle_sample_rate(w, R_s, K_s2)
+        procs = os.cpu_count() or 1
+        rate, dt, used = oracle_parallel_rate(w, R_s, K_s2, procs)
         what = "reverse-mode gradient over" if run.grad else "solve of"
-        cpu = {"value": rate, "unit": "spin-updates/s", "cores": 1, "kind": "oracle",
+        cpu = {"value": rate, "unit": "spin-updates/s", "cores": used, "kind": "oracle",
                "sample": f"{what} {R_s} replicas x first {K_s2} of {K} steps of the same instance, FP64, "
-                         f"one thread ({dt:.1f} s)"}
+                         f"{used} independent processes at once (replica-parallel, {dt:.1f} s wall)",
+               "single_thread": {"value": rate1, "sample_s": dt1}}
 
     if rank == 0:
         prec_name = {0: "f32", 1: "bf16", 2: "fp8e4m3"}[w.get("prec", 0)]
@@ -456,6 +545,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas-only x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "time_to_target": ttt,
+            "tts99": tts,
             "clocks": clk,
             "quality": {"best_energy_last_step": results[-1]},
             "wall_s_timed_region": wall,
@@ -489,23 +579,25 @@ def run_reference(args, rank, world):
     R_s = min(w["R"], 4 if w["kind"] == "grad" else 32)
     rate0, _ = oracle_sample_rate(w, R_s, min(w["K"], 2))
     K_s = int(min(w["K"], 1000, max(1, 3.0 * rate0 / (w["n"] * R_s))))
+    procs = os.cpu_count() or 1
     for _ in range(args.warmup):
         oracle_sample_rate(w, R_s, min(K_s, 20))
     times = []
     for _ in range(args.steps):
-        _, dt = oracle_sample_rate(w, R_s, K_s)
+        _, dt, used = oracle_parallel_rate(w, R_s, K_s, procs)
         times.append(dt)
     total = sum(times)
-    value = w["n"] * R_s * K_s * args.steps / total
+    value = w["n"] * R_s * K_s * used * args.steps / total
     what = "reverse-mode gradient, " if w["kind"] == "grad" else ""
-    sample = f"{what}{R_s} replicas x first {K_s} of {w['K']} steps per step, FP64 oracle, one thread"
+    sample = (f"{what}{R_s} replicas x first {K_s} of {w['K']} steps per step in each of {used} independent "
+              f"processes at once, FP64 oracle")
     line = {"impl": "reference", "metric": "spin-updates/s", "value": value, "unit": "spin-updates/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": w["name"], "instance": w["desc"], "n": w["n"], "replicas": w["R"],
                        "integration_steps": w["K"], "readout_every": w["readout_every"]},
-            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 

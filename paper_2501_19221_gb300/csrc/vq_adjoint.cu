@@ -243,7 +243,8 @@ void adj_step_v(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const fl
 template <typename WT>
 int adj_dispatch_loss(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const float* S, float* ls, float* ly,
                       double* parts) {
-    if (c->stream_unroll == 4) adj_loss_v<WT, 4>(c, V, R, w, ws, S, ls, ly, parts);
+    if (c->stream_unroll == 6 && c->uniform_deg == 6) adj_loss_v<WT, 6>(c, V, R, w, ws, S, ls, ly, parts);
+    else if (c->stream_unroll == 4) adj_loss_v<WT, 4>(c, V, R, w, ws, S, ls, ly, parts);
     else adj_loss_v<WT, 1>(c, V, R, w, ws, S, ls, ly, parts);
     VQ_LAUNCH_CHECK("adjoint loss");
     return VELOXQ_OK;
@@ -251,7 +252,9 @@ int adj_dispatch_loss(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, co
 template <typename WT>
 int adj_dispatch_step(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const float* Sk, const float* Yk, float a_k,
                       float dt, float a0, float c0, float* ls, float* ly, float* gp, float* gs, double* parts3) {
-    if (c->stream_unroll == 4) adj_step_v<WT, 4>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
+    if (c->stream_unroll == 6 && c->uniform_deg == 6)
+        adj_step_v<WT, 6>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
+    else if (c->stream_unroll == 4) adj_step_v<WT, 4>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
     else adj_step_v<WT, 1>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
     VQ_LAUNCH_CHECK("adjoint step");
     return VELOXQ_OK;

@@ -115,7 +115,8 @@ struct veloxq_ctx {
     vq::DevBuf s_a, s_b, y, f, ework, best_e, best_bits, flags, a_table, xout, misc;
     vq::DevBuf sop_a, sop_b;      // tensor-core operand copies of S (ping-pong)
     vq::DevBuf errw;              // device error word of bounded waits
-    int stream_unroll = 0;        // gather variant of the streaming kernels (0: not tuned yet)
+    int stream_unroll = 0;        // gather variant of the streaming kernels: 1, 4, or 6 (rows of exactly
+                                  // 6 couplings); 0: not tuned yet
     int32_t stream_tuned_R = -1;  // replica count the variant was tuned for
 };
 
@@ -334,6 +335,27 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
                                             int64_t i, float (&acc)[V], int udeg = -1) {
 #pragma unroll
     for (int l = 0; l < V; ++l) acc[l] = 0.0f;
+    if constexpr (UNROLL == 6) {
+        // every row holds exactly 6 couplings (udeg == 6, e.g. cubic
+        // lattices): all six columns, then all six neighbour vectors are in
+        // flight at once; the sum is taken in CSR order as in the loops below
+        const int64_t p0 = i * 6;
+        int32_t j[6];
+        float wv[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            j[u] = __ldg(col + p0 + u);
+            wv[u] = wval(__ldg(w + p0 + u));
+        }
+        float sj[6][V];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) vload<V>(X + (int64_t)j[u] * R + off, sj[u]);
+#pragma unroll
+        for (int u = 0; u < 6; ++u)
+#pragma unroll
+            for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
+        return;
+    }
     // rows of a regular graph start at i * degree: no row pointer is read
     const int64_t p0 = udeg >= 0 ? i * udeg : __ldg(rp + i);
     const int64_t p1 = udeg >= 0 ? p0 + udeg : __ldg(rp + i + 1);

@@ -150,18 +150,16 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
     const int32_t* cl = ctx->col.as<int32_t>();
     const float* bf = ctx->bf.as<float>();
     cudaStream_t st = ctx->stream;
-#define VQ_STEP(VV, WT, WPTR, SC)                                                                                   \
-    do {                                                                                                            \
-        if (unroll == 4)                                                                                            \
-            k_stream_step<VV, WT, FIELD_ONLY, 4><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
-                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out,  \
-                                                                    ctx->uniform_deg);                               \
-        else                                                                                                        \
-            k_stream_step<VV, WT, FIELD_ONLY, 1><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
-                                                                    Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out,  \
-                                                                    ctx->uniform_deg);                               \
+#define VQ_STEP_U(VV, WT, WPTR, SC, U)                                                                               \
+    k_stream_step<VV, WT, FIELD_ONLY, U><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, Y_in, Y_out, \
+                                                            bf, a_table, k, dt, a0, c0, F_out, ctx->uniform_deg)
+#define VQ_STEP(VV, WT, WPTR, SC)                                   \
+    do {                                                            \
+        if (unroll == 6) VQ_STEP_U(VV, WT, WPTR, SC, 6);            \
+        else if (unroll == 4) VQ_STEP_U(VV, WT, WPTR, SC, 4);       \
+        else VQ_STEP_U(VV, WT, WPTR, SC, 1);                        \
     } while (0)
-    const int unroll = ctx->stream_unroll == 4 ? 4 : 1;
+    const int unroll = (ctx->stream_unroll == 6 && ctx->uniform_deg == 6) ? 6 : ctx->stream_unroll == 4 ? 4 : 1;
     if (ctx->w8.p) {
         const int8_t* w = ctx->w8.as<int8_t>();
         if (V == 4) VQ_STEP(4, int8_t, w, 0.5f); else if (V == 2) VQ_STEP(2, int8_t, w, 0.5f); else VQ_STEP(1, int8_t, w, 0.5f);
@@ -170,6 +168,7 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
         if (V == 4) VQ_STEP(4, float, w, 1.0f); else if (V == 2) VQ_STEP(2, float, w, 1.0f); else VQ_STEP(1, float, w, 1.0f);
     }
 #undef VQ_STEP
+#undef VQ_STEP_U
     VQ_LAUNCH_CHECK("stream_step");
     return VELOXQ_OK;
 }
@@ -204,7 +203,8 @@ int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y
     int pick = 1;
     VQ_TRY(launch_init_state(ctx, R, 1, 0.1f, LAYOUT_NR, S_a, Y));
     const float* at = ctx->a_table.as<float>();
-    for (int u : {1, 4}) {
+    for (int u : {1, 4, 6}) {
+        if (u == 6 && ctx->uniform_deg != 6) continue;
         ctx->stream_unroll = u;
         VQ_TRY(launch_step<false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr));   // warm
         VQ_CUDA(cudaEventRecord(e0, ctx->stream));

@@ -188,19 +188,6 @@ __device__ __forceinline__ void umma_commit_pair(uint64_t* bar) {
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-          "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-          "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-          "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -255,6 +242,9 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     const int num_kb = (a.n_pad + BK - 1) / BK;
     const int MT = (a.n + 2 * BM - 1) / (2 * BM), NT = (a.R + BN - 1) / BN;
     const int tiles = MT * NT;                   // pair tile t: rows (t / NT) * 2BM, replicas (t % NT) * BN
+    // Odd steps walk the tiles in reverse, so a step starts on the tiles whose
+    // state the previous step wrote last (still in L2).
+    const bool rev = (a.k & 1) != 0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -278,7 +268,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int t = pair; t < tiles && ok; t += pairs) {
+            for (int tw = pair; tw < tiles && ok; tw += pairs) {
+                const int t = rev ? tiles - 1 - tw : tw;
                 const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN + (int)rank * BNH;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     const uint32_t s = it % STAGES, u = it / STAGES;
@@ -297,7 +288,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
             constexpr uint32_t idesc = instr_desc<PREC>();
             uint32_t it = 0, tt = 0;
             bool ok = true;
-            for (int t = pair; t < tiles && ok; t += pairs, ++tt) {
+            for (int tw = pair; tw < tiles && ok; tw += pairs, ++tt) {
                 const uint32_t b = tt & 1u;
                 if (tt >= 2 && !mbar_wait<true>(&acce[b], ((tt >> 1) - 1) & 1u, a.err, TC_ERR_MMA)) { ok = false; break; }
                 tc_fence_after();
@@ -326,8 +317,9 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
         const uint32_t acce_cl = mapa(smem_u32(&acce[0]), 0);
         uint32_t tt = 0;
-        for (int t = pair; t < tiles; t += pairs, ++tt) {
+        for (int tw = pair; tw < tiles; tw += pairs, ++tt) {
             const uint32_t b = tt & 1u;
+            const int t = rev ? tiles - 1 - tw : tw;
             const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN;
             const int row = m0 + q * 32 + lane;
             const bool row_ok = row < a.n;
@@ -336,17 +328,15 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                 if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
                 if constexpr (!FIELD_ONLY) bi = __ldg(a.bf + row);
             }
-            if (!mbar_wait<true>(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
-            tc_fence_after();
             constexpr int CW = 16;   // columns per tensor-memory load
-#pragma unroll 1
-            for (int c = half * (BN / (2 * CW)); c < (half + 1) * (BN / (2 * CW)); ++c) {
-                uint32_t v[CW];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)(c * CW), v);
-                const int r0 = n0 + c * CW;
-                // every load of the chunk is issued before any use (no early exit)
-                float sv[CW], yv[CW];
+            const int c_begin = half * (BN / (2 * CW)), c_end = c_begin + BN / (2 * CW);   // 8 chunks, even
+            // Positions and momenta of a chunk: loaded one chunk ahead of its
+            // use (the first before the accumulator is ready), so two chunks'
+            // loads are in flight while one is updated.
+            float sv0[CW], yv0[CW], sv1[CW], yv1[CW];
+            auto load_chunk = [&](int c, float (&sv)[CW], float (&yv)[CW]) {
                 if constexpr (!FIELD_ONLY) {
+                    const int r0 = n0 + c * CW;
 #pragma unroll
                     for (int j = 0; j < CW; ++j) {
                         const bool ok = row_ok && r0 + j < a.R;
@@ -355,6 +345,11 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                         yv[j] = ok ? a.Y[p] : 0.0f;
                     }
                 }
+            };
+            auto update_chunk = [&](int c, const float (&sv)[CW], const float (&yv)[CW]) {
+                uint32_t v[CW];
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)(c * CW), v);
+                const int r0 = n0 + c * CW;
 #pragma unroll
                 for (int j = 0; j < CW; ++j) {
                     const bool ok = row_ok && r0 + j < a.R;
@@ -371,6 +366,16 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                         }
                     }
                 }
+            };
+            load_chunk(c_begin, sv0, yv0);
+            if (!mbar_wait<true>(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = c_begin; c < c_end; c += 2) {
+                load_chunk(c + 1, sv1, yv1);
+                update_chunk(c, sv0, yv0);
+                if (c + 2 < c_end) load_chunk(c + 2, sv0, yv0);
+                update_chunk(c + 1, sv1, yv1);
             }
             // hand the accumulator buffer back to the even CTA's MMA thread
             tc_fence_before();

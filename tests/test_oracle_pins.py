@@ -428,3 +428,17 @@ def test_field_dense_rows_equals_full_field():
     full = O.field(O.problem_from_dense(Q), S)
     assert np.allclose(O.field_dense_rows(Q, S, rows), full[:, rows], atol=1e-12)
     assert np.all(O.abs_field_dense_rows(Q, S, rows) >= np.abs(full[:, rows]) - 1e-12)
+
+
+def test_dense_n20_ground_file_matches_enumeration():
+    """tests/golden/dense_n20_ground.txt (written by make_dense_n20_ground.py)
+    is the oracle's exhaustive minimum of the seeded dense n = 20 instance."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "dense_n20_ground.txt")
+    rec = dict(line.split(None, 1) for line in open(path) if not line.startswith("#"))
+    Q, c = I.dense_int_qubo(20, seed=0)
+    p = O.problem_from_dense(Q, c)
+    E, x, count = O.bruteforce(p)
+    assert int(rec["E_min"]) == E and int(rec["minimisers"]) == count
+    xs = np.array([int(ch) for ch in rec["x_min"].strip()], dtype=np.uint8)
+    assert O.energy(p, xs[None, :])[0] == E
