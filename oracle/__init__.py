@@ -63,6 +63,10 @@ def _load():
             "oracle_field": (None, [i64, i64, P, P, P, i32, P, P]),
             "oracle_schedule": (None, [i32, i32, P, P]),
             "oracle_bsb_update": (None, [i64, i32, P, P, f64, f64, f64, f64, P, P]),
+            "oracle_update": (None, [i32, i64, i32, P, P, f64, f64, f64, f64, f64, P, P]),
+            "oracle_field_operand": (None, [i32, i64, P, P]),
+            "oracle_run": (ctypes.c_int, [i32, f64, i64, i64, P, P, P, P, P, P, i32, i32, f64, f64, f64,
+                                          i32, P, i32, P, P, i32, P, P, P, P, P, P, P, P, P]),
             "oracle_bsb_run": (ctypes.c_int, [i64, i64, P, P, P, P, P, P, i32, i32, f64, f64, f64,
                                               i32, P, i32, P, P, i32, P, P, P, P, P, P, P, P, P]),
             "oracle_relaxed_energy": (None, [i64, i64, P, P, P, P, i32, P, P]),
@@ -357,10 +361,46 @@ def bsb_step(p: Problem, S, Y, a_k, dt, a0, c0):
     return S1, Y1, F
 
 
+METHODS = {"bsb": 0, "asb": 1, "pa": 2}
+
+
+def field_operand(method: str, S) -> np.ndarray:
+    """The state the field multiplies: S itself (SB forms) or the binarised
+    spins, +1 where x > 0 and -1 elsewhere (PA)."""
+    lib = _load()
+    S = np.ascontiguousarray(np.atleast_2d(S), dtype=np.float64)
+    out = np.zeros_like(S)
+    lib.oracle_field_operand(METHODS[method], S.size, _p(S), _p(out))
+    return out
+
+
+def update(method: str, F, b, a_k, dt, a0, c0, S, Y, alpha: float = 0.9):
+    """One update of `method` ("bsb", "asb" or "pa") given the field F of the
+    method's operand (returns new float64 copies)."""
+    lib = _load()
+    S = np.ascontiguousarray(np.atleast_2d(S), dtype=np.float64).copy()
+    Y = np.ascontiguousarray(np.atleast_2d(Y), dtype=np.float64).copy()
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    R, n = S.shape
+    lib.oracle_update(METHODS[method], n, R, _p(F), _p(b), a_k, dt, a0, c0, alpha, _p(S), _p(Y))
+    return S, Y
+
+
+def step(method: str, p: Problem, S, Y, a_k, dt, a0, c0, alpha: float = 0.9):
+    """Field of the method's operand, then the update. Returns (S, Y, F)."""
+    b, _ = bias(p)
+    F = field(p, field_operand(method, S))
+    S1, Y1 = update(method, F, b, a_k, dt, a0, c0, S, Y, alpha)
+    return S1, Y1, F
+
+
 def bsb_run(p: Problem, R: int, K: int, dt: float, a0: float, c0: float,
             knots: Sequence[float], readout_every: int, S0: np.ndarray, Y0: np.ndarray,
-            n_snap: int = 0) -> dict:
-    """K ballistic-SB steps with readouts, exact energies and best-so-far.
+            n_snap: int = 0, method: str = "bsb", alpha: float = 0.9) -> dict:
+    """K steps of `method` (ballistic SB by default; "asb" adiabatic SB, "pa"
+    Parallel Annealing with momentum alpha) with readouts, exact energies and
+    best-so-far.
 
     Returns per-replica best energies/vectors/steps, the final state, and the
     first ``n_snap`` fields and states if asked for.
@@ -379,10 +419,10 @@ def bsb_run(p: Problem, R: int, K: int, dt: float, a0: float, c0: float,
     best_E_i64 = np.zeros(R, dtype=np.int64) if p.integer else None
     best_x = np.zeros((R, n), dtype=np.uint8)
     best_step = np.zeros(R, dtype=np.int32)
-    rc = lib.oracle_bsb_run(n, p.nnz, _p(p.er), _p(p.ec), _p(p.ev), _p(p.c), _p(p.ev_i64), _p(p.c_i64),
-                            R, K, dt, a0, c0, kn.shape[0], _p(kn), readout_every, _p(S0), _p(Y0),
-                            n_snap, _p(F_snap), _p(S_snap), _p(Y_snap), _p(S_fin), _p(Y_fin),
-                            _p(best_E), _p(best_E_i64), _p(best_x), _p(best_step))
+    rc = lib.oracle_run(METHODS[method], alpha, n, p.nnz, _p(p.er), _p(p.ec), _p(p.ev), _p(p.c),
+                        _p(p.ev_i64), _p(p.c_i64), R, K, dt, a0, c0, kn.shape[0], _p(kn), readout_every,
+                        _p(S0), _p(Y0), n_snap, _p(F_snap), _p(S_snap), _p(Y_snap), _p(S_fin), _p(Y_fin),
+                        _p(best_E), _p(best_E_i64), _p(best_x), _p(best_step))
     if rc != 0:
         raise MemoryError("oracle_bsb_run failed to allocate")
     r_best = int(np.argmin(best_E_i64 if p.integer else best_E))   # lowest replica index on ties

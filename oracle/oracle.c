@@ -29,6 +29,20 @@
  *    counter (i_lo, i_hi, r, 0) and key (seed_lo, seed_hi); word 0 draws s,
  *    word 1 draws y; u = (w >> 8) 2^-24 and v = sigma0 (2u - 1) in float32.
  *
+ *  - Two further integrators on the same field (method codes 1 and 2):
+ *    adiabatic SB exactly as App. B prints it (the quartic potential term,
+ *    no walls):
+ *        y    <- y + dt (-(s^2 + a0 - a_k) s + c0 phi),  s <- s + dt a0 y
+ *    and Parallel Annealing (App. B, "PA"): analog spins x in [-1, 1], the
+ *    target gradient taken at the binarised spins sigma = sign(x) (read as
+ *    +1 for x > 0 and -1 otherwise, the same rule as the readout), the
+ *    initial Hamiltonian sum x^2/2 weighted by lambda_k, momentum and
+ *    clipping:
+ *        F     = Qoff sigma,  g = lambda_k x + c0 (F + b)/2  (= lambda_k x - c0 phi)
+ *        m    <- alpha m - dt g,  x <- clip(x + m, -1, 1)
+ *    with lambda_k = (a0 - a_k)/a0 falling from 1 to 0 along the same
+ *    schedule. (x, m) use the storage of (s, y); the readout is x = [x > 0].
+ *
  * All state arrays are replica-major: element (r, i) lives at r*n + i.
  * Couplings are passed as a coordinate list (er, ec, ev): every stored entry
  * of Q, diagonal included, exactly as given.
@@ -308,6 +322,57 @@ void oracle_bsb_update(int64_t n, int32_t R, const double* F, const double* b, d
         }
 }
 
+/* One adiabatic-SB update as App. B prints it (eq. sbm with the quartic
+ * potential, no walls), given the field F of the current state. */
+void oracle_asb_update(int64_t n, int32_t R, const double* F, const double* b, double a_k,
+                       double dt, double a0, double c0, double* S, double* Y)
+{
+    for (int32_t r = 0; r < R; ++r)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t p = (int64_t)r * n + i;
+            double s = S[p];
+            double phi = -0.5 * (F[p] + b[i]);
+            double y = Y[p] + dt * (-(s * s + a0 - a_k) * s + c0 * phi);
+            S[p] = s + dt * a0 * y;
+            Y[p] = y;
+        }
+}
+
+/* One Parallel-Annealing update (App. B: gradient step with momentum and
+ * clipping on the analog spins), given the field F of the binarised spins
+ * and lambda_k. X holds the analog spins, M the momenta. */
+void oracle_pa_update(int64_t n, int32_t R, const double* F, const double* b, double lam,
+                      double dt, double alpha, double c0, double* X, double* M)
+{
+    for (int32_t r = 0; r < R; ++r)
+        for (int64_t i = 0; i < n; ++i) {
+            int64_t p = (int64_t)r * n + i;
+            double g = lam * X[p] + c0 * 0.5 * (F[p] + b[i]);
+            double m = alpha * M[p] - dt * g;
+            double x = X[p] + m;
+            if (x > 1.0) x = 1.0;
+            if (x < -1.0) x = -1.0;
+            X[p] = x;
+            M[p] = m;
+        }
+}
+
+/* The field operand of a method: the state itself (SB forms) or its
+ * binarised spins, +1 where x > 0 and -1 elsewhere (PA). */
+void oracle_field_operand(int32_t method, int64_t nR, const double* S, double* out)
+{
+    for (int64_t p = 0; p < nR; ++p) out[p] = method == 2 ? (S[p] > 0.0 ? 1.0 : -1.0) : S[p];
+}
+
+/* One update of the given method (0 ballistic SB, 1 adiabatic SB, 2 PA). */
+void oracle_update(int32_t method, int64_t n, int32_t R, const double* F, const double* b, double a_k,
+                   double dt, double a0, double c0, double alpha, double* S, double* Y)
+{
+    if (method == 1) oracle_asb_update(n, R, F, b, a_k, dt, a0, c0, S, Y);
+    else if (method == 2) oracle_pa_update(n, R, F, b, (a0 - a_k) / a0, dt, alpha, c0, S, Y);
+    else oracle_bsb_update(n, R, F, b, a_k, dt, a0, c0, S, Y);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Full run with readout, exact energy and best-so-far                        */
 /* ------------------------------------------------------------------------ */
@@ -317,23 +382,28 @@ void oracle_bsb_update(int64_t n, int32_t R, const double* F, const double* b, d
  * ev_i64/c_i64 (may be NULL) switch the energy to exact int64.
  * Snapshots (if n_snap > 0): F_snap[k] is the field used in step k, S_snap[k]
  * and Y_snap[k] the state after step k, each [R][n], for k < n_snap. */
-int oracle_bsb_run(int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec, const double* ev,
-                   const double* c, const int64_t* ev_i64, const int64_t* c_i64,
-                   int32_t R, int32_t K, double dt, double a0, double c0,
-                   int32_t n_knots, const double* knots, int32_t readout_every,
-                   const float* S0, const float* Y0,
-                   int32_t n_snap, double* F_snap, double* S_snap, double* Y_snap,
-                   double* S_fin, double* Y_fin,
-                   double* best_E, int64_t* best_E_i64, uint8_t* best_x, int32_t* best_step)
+/* The run of any method (0 ballistic SB, 1 adiabatic SB, 2 PA; alpha is
+ * the PA momentum). For PA the snapshots F_snap hold the field of the
+ * binarised spins. */
+int oracle_run(int32_t method, double alpha,
+               int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec, const double* ev,
+               const double* c, const int64_t* ev_i64, const int64_t* c_i64,
+               int32_t R, int32_t K, double dt, double a0, double c0,
+               int32_t n_knots, const double* knots, int32_t readout_every,
+               const float* S0, const float* Y0,
+               int32_t n_snap, double* F_snap, double* S_snap, double* Y_snap,
+               double* S_fin, double* Y_fin,
+               double* best_E, int64_t* best_E_i64, uint8_t* best_x, int32_t* best_step)
 {
     const int64_t nR = n * (int64_t)R;
     double* S = (double*)malloc(sizeof(double) * (size_t)nR);
     double* Y = (double*)malloc(sizeof(double) * (size_t)nR);
     double* F = (double*)malloc(sizeof(double) * (size_t)nR);
+    double* O = (double*)malloc(sizeof(double) * (size_t)nR);
     double* b = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
     double* a = (double*)malloc(sizeof(double) * (size_t)(K > 0 ? K : 1));
     uint8_t* x = (uint8_t*)malloc((size_t)(n > 0 ? n : 1));
-    if (!S || !Y || !F || !b || !a || !x) return -2;
+    if (!S || !Y || !F || !O || !b || !a || !x) return -2;
     double K0;
     oracle_bias(n, nnz, er, ec, ev, c, b, &K0);
     oracle_schedule(K, n_knots, knots, a);
@@ -344,9 +414,10 @@ int oracle_bsb_run(int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec,
         if (best_step) best_step[r] = -1;
     }
     for (int32_t k = 0; k < K; ++k) {
-        oracle_field(n, nnz, er, ec, ev, R, S, F);
+        oracle_field_operand(method, nR, S, O);
+        oracle_field(n, nnz, er, ec, ev, R, O, F);
         if (k < n_snap && F_snap) memcpy(F_snap + (int64_t)k * nR, F, sizeof(double) * (size_t)nR);
-        oracle_bsb_update(n, R, F, b, a[k], dt, a0, c0, S, Y);
+        oracle_update(method, n, R, F, b, a[k], dt, a0, c0, alpha, S, Y);
         if (k < n_snap && S_snap) memcpy(S_snap + (int64_t)k * nR, S, sizeof(double) * (size_t)nR);
         if (k < n_snap && Y_snap) memcpy(Y_snap + (int64_t)k * nR, Y, sizeof(double) * (size_t)nR);
         int readout = (k == K - 1) || (readout_every > 0 && ((k + 1) % readout_every) == 0);
@@ -371,8 +442,23 @@ int oracle_bsb_run(int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec,
     }
     if (S_fin) memcpy(S_fin, S, sizeof(double) * (size_t)nR);
     if (Y_fin) memcpy(Y_fin, Y, sizeof(double) * (size_t)nR);
-    free(S); free(Y); free(F); free(b); free(a); free(x);
+    free(S); free(Y); free(F); free(O); free(b); free(a); free(x);
     return 0;
+}
+
+/* The ballistic-SB run (method 0). */
+int oracle_bsb_run(int64_t n, int64_t nnz, const int64_t* er, const int64_t* ec, const double* ev,
+                   const double* c, const int64_t* ev_i64, const int64_t* c_i64,
+                   int32_t R, int32_t K, double dt, double a0, double c0,
+                   int32_t n_knots, const double* knots, int32_t readout_every,
+                   const float* S0, const float* Y0,
+                   int32_t n_snap, double* F_snap, double* S_snap, double* Y_snap,
+                   double* S_fin, double* Y_fin,
+                   double* best_E, int64_t* best_E_i64, uint8_t* best_x, int32_t* best_step)
+{
+    return oracle_run(0, 0.0, n, nnz, er, ec, ev, c, ev_i64, c_i64, R, K, dt, a0, c0, n_knots, knots,
+                      readout_every, S0, Y0, n_snap, F_snap, S_snap, Y_snap, S_fin, Y_fin, best_E, best_E_i64,
+                      best_x, best_step);
 }
 
 /* Relaxed energy per replica: 1/4 s^T Qoff s + 1/2 b^T s + K0 (identity of

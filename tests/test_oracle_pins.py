@@ -442,3 +442,115 @@ def test_dense_n20_ground_file_matches_enumeration():
     assert int(rec["E_min"]) == E and int(rec["minimisers"]) == count
     xs = np.array([int(ch) for ch in rec["x_min"].strip()], dtype=np.uint8)
     assert O.energy(p, xs[None, :])[0] == E
+
+
+# ---------------------------------------------------------------- adiabatic SB (App. B as printed)
+def test_asb_small_amplitude_equals_linear_map():
+    """At amplitude 1e-5 the quartic term is below rounding of the linear
+    part, so adiabatic SB follows the same 2x2 map as the ballistic form
+    (catches a wrong sign or order in the linear part of the aSB update)."""
+    n, R, K = 4, 2, 30
+    p = O.problem_from_dense(np.zeros((n, n), dtype=np.int64))
+    S0, Y0 = O.init_state(n, R, seed=2, sigma0=1e-5)
+    dt, a0 = 0.3, 1.0
+    out = O.bsb_run(p, R, K, dt, a0, 0.7, [0.0, a0], 0, S0, Y0, n_snap=K, method="asb")
+    a = O.schedule(K, [0.0, a0])
+    s, y = S0.astype(np.float64).copy(), Y0.astype(np.float64).copy()
+    for k in range(K):
+        s, y = (1 - dt * dt * a0 * (a0 - a[k])) * s + dt * a0 * y, -dt * (a0 - a[k]) * s + y
+        # the quartic term contributes below 1e-13 over the run; a wrong linear term O(1e-6)
+        assert np.allclose(out["S_snap"][k], s, rtol=0, atol=1e-12)
+
+
+def test_asb_quartic_well_fixed_point_and_no_walls():
+    """With a_k = 3 a0 constant and c0 = 0 the potential s^4/4 + (a0 - a_k)
+    s^2/2 has its minima at s = +-sqrt(a_k - a0) = +-sqrt(2) > 1: a state
+    resting there stays (no walls; catches a missing or mis-signed cubic
+    term, or a wall applied to the adiabatic form)."""
+    n, R, K = 3, 2, 50
+    p = O.problem_from_dense(np.zeros((n, n), dtype=np.int64))
+    r2 = np.sqrt(2.0)
+    S0 = np.array([[r2, -r2, r2], [-r2, r2, -r2]], dtype=np.float32)
+    Y0 = np.zeros_like(S0)
+    out = O.bsb_run(p, R, K, 0.1, 1.0, 0.0, [3.0, 3.0], 0, S0, Y0, method="asb")
+    s32 = S0.astype(np.float64)
+    # the float32 start is within 2^-24 of the minimum: it stays there to O(1e-7)
+    assert np.allclose(out["S"], s32, atol=1e-6)
+    assert np.all(np.abs(out["S"]) > 1.4)
+
+
+def test_asb_anharmonic_energy_is_conserved():
+    """a_k = a0 and c0 = 0: a pure quartic oscillator. Symplectic Euler keeps
+    the modified energy a0 y^2/2 + s^4/4 - (dt a0/2) y s^3 within O(dt^2) with
+    no drift over 20 000 steps (a dropped cubic makes s drift linearly; a
+    wrong sign makes it run away)."""
+    n, R, K = 1, 1, 20000
+    p = O.problem_from_dense(np.zeros((n, n), dtype=np.int64))
+    S0 = np.array([[0.8]], dtype=np.float32)
+    Y0 = np.array([[0.0]], dtype=np.float32)
+    dt, a0 = 0.01, 1.0
+    out = O.bsb_run(p, R, K, dt, a0, 0.0, [a0, a0], 0, S0, Y0, n_snap=K, method="asb")
+    s, y = out["S_snap"][:, 0, 0], out["Y_snap"][:, 0, 0]
+    H = a0 * y * y / 2 + s ** 4 / 4 - dt * a0 / 2 * y * s ** 3
+    H0 = 0.8 ** 4 / 4
+    assert np.max(np.abs(H - H0)) < 5 * dt * dt
+    assert np.max(np.abs(s)) <= 0.8 + 1e-3 and np.min(s) < -0.79   # it oscillates between the turning points
+
+
+# ---------------------------------------------------------------- Parallel Annealing (App. B)
+def test_pa_uncoupled_heavy_ball_closed_form():
+    """Q = 0, c = 0, lambda constant: g = lambda x and (x, m) follows the
+    heavy-ball matrix [[1 - dt lambda, alpha], [-dt lambda, alpha]], powered
+    by numpy (catches a wrong momentum order or a gradient sign)."""
+    n, R, K = 4, 3, 60
+    p = O.problem_from_dense(np.zeros((n, n), dtype=np.int64))
+    S0, Y0 = O.init_state(n, R, seed=4, sigma0=0.2)
+    dt, a0, alpha = 0.3, 1.0, 0.8
+    knots = [0.4, 0.4]                     # a_k = 0.4, lambda = (a0 - a_k)/a0 = 0.6
+    lam = 0.6
+    out = O.bsb_run(p, R, K, dt, a0, 0.5, knots, 0, S0, Y0, n_snap=K, method="pa", alpha=alpha)
+    A = np.array([[1 - dt * lam, alpha], [-dt * lam, alpha]])
+    v0 = np.stack([S0.astype(np.float64).ravel(), Y0.astype(np.float64).ravel()])
+    for k in (0, 1, 7, K - 1):
+        v = np.linalg.matrix_power(A, k + 1) @ v0
+        assert np.allclose(out["S_snap"][k].ravel(), v[0], atol=1e-13)
+        assert np.allclose(out["Y_snap"][k].ravel(), v[1], atol=1e-13)
+
+
+def test_pa_clips_position_keeps_momentum():
+    """x + m beyond [-1, 1] is clipped; the momentum is kept (the paper clips
+    x only)."""
+    F = np.zeros((1, 3))
+    b = np.zeros(3)
+    X = np.array([[0.9, -0.9, 0.2]])
+    M = np.array([[0.5, -0.5, 0.1]])
+    X1, M1 = O.update("pa", F, b, 1.0, 0.5, 1.0, 1.0, X, M, alpha=0.9)   # a_k = a0: lambda = 0, g = 0
+    assert X1.tolist() == [[1.0, -1.0, 0.2 + 0.9 * 0.1]]
+    assert M1.tolist() == [[0.9 * 0.5, -0.9 * 0.5, 0.9 * 0.1]]
+
+
+def test_pa_field_uses_binarised_spins():
+    """The PA target gradient is taken at sign(x): the field of a 2-spin
+    coupling by hand, and invariance under positive rescaling of x (catches a
+    field of x instead of sign(x), or sign(0) read as +1)."""
+    p = O.problem_from_dense(np.array([[0, 1], [1, 0]], dtype=np.int64))
+    X = np.array([[0.3, -0.7], [0.0, 0.5]])
+    Y = np.zeros_like(X)
+    _, _, F = O.step("pa", p, X, Y, 0.0, 0.1, 1.0, 1.0)
+    assert F.tolist() == [[-1.0, 1.0], [1.0, -1.0]]     # sign(0) = -1
+    _, _, F2 = O.step("pa", p, 0.25 * X, Y, 0.0, 0.1, 1.0, 1.0)
+    assert np.array_equal(F, F2)
+
+
+def test_pa_ground_state_is_a_fixed_point():
+    """lambda = 0 (a_k = a0), alpha = 0: x = 2 x* - 1 at the enumerated ground
+    state x* is a fixed point, since every coordinate's gradient pushes it
+    further out against the clip (catches a sign error in the target
+    gradient, which would flip spins away from the minimum)."""
+    Q, c = I.dense_int_qubo(20, seed=0)
+    p = O.problem_from_dense(Q, c)
+    Emin, xmin, _ = O.bruteforce(p)
+    X0 = (2.0 * xmin.astype(np.float32) - 1.0)[None, :]
+    out = O.bsb_run(p, 1, 25, 0.1, 1.0, 0.1, [1.0, 1.0], 5, X0, np.zeros_like(X0), method="pa", alpha=0.0)
+    assert np.array_equal(out["S"], X0.astype(np.float64))
+    assert out["best_E_i64"][0] == Emin
