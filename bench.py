@@ -155,7 +155,7 @@ def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0, barrier=None) -> tu
     if w["kind"] == "grad":
         O.bsb_grad(p, R_s, K_s, w["dt"], 1.0, c0, knots, S0, Y0)
     else:
-        O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0)
+        O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0, method=w.get("method", "bsb"))
     dt = time.perf_counter() - t0
     return p.n * R_s * K_s / dt, dt
 
@@ -169,8 +169,8 @@ def _oracle_init(barrier):
 
 
 def _oracle_worker(job):
-    name, R_s, K_s, seed = job
-    return oracle_sample_rate(workload(name), R_s, K_s, seed, _BARRIER)
+    name, method, R_s, K_s, seed = job
+    return oracle_sample_rate(dict(workload(name), method=method), R_s, K_s, seed, _BARRIER)
 
 
 def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
@@ -184,7 +184,8 @@ def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
     ctx = mp.get_context("spawn")          # never fork a process that has touched the GPU
     barrier = ctx.Barrier(procs)
     with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier,)) as pool:
-        res = pool.map(_oracle_worker, [(w["name"], R_s, K_s, s) for s in range(procs)], chunksize=1)
+        res = pool.map(_oracle_worker, [(w["name"], w.get("method", "bsb"), R_s, K_s, s) for s in range(procs)],
+                       chunksize=1)
     wall = max(dt for _, dt in res)
     return w["n"] * R_s * K_s * procs / wall, wall, procs
 
@@ -242,7 +243,7 @@ class ClockSampler:
 class Runner:
     """One workload on the library: a context (or a batch of them) and a solve."""
 
-    def __init__(self, B, w, stream):
+    def __init__(self, B, w, stream, method: int = 0):
         self.B, self.w = B, w
         self.batch = w["kind"] == "batch"
         made = create(B, w)
@@ -253,7 +254,7 @@ class Runner:
         if self.grad:
             self.sched = B.make_schedule(readout_every=0, dt=w["dt"], knots=w["knots"])
         else:
-            self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0))
+            self.sched = B.make_schedule(readout_every=w["readout_every"], prec=w.get("prec", 0), method=method)
         self.n_total = sum(c.info.n for c in self.ctxs)
         self.nnz_field = sum(c.info.nnz_field for c in self.ctxs)
         self.regular = False
@@ -436,9 +437,11 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     w = workload(args.workload)
+    w["method"] = args.method
     R, K = w["R"], w["K"]
+    method = {"bsb": 0, "asb": 1, "pa": 2}[args.method]
     stream = torch.cuda.Stream()
-    run = Runner(B, w, stream)
+    run = Runner(B, w, stream, method)
     n = run.n_total
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     seed0 = 1000 * rank
@@ -491,7 +494,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for i in range(e2e_iters):
-        r2 = Runner(B, pw, stream)
+        r2 = Runner(B, pw, stream, method)
         r2.solve(seed0 + 77 + i, want_x=True)
         r2.destroy()
     e2e_s = (time.perf_counter() - t0) / e2e_iters
@@ -541,6 +544,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": w["name"], "instance": w["desc"], "n": n, "nnz_field": run.nnz_field,
                        "replicas": R, "integration_steps": K, "readout_every": w["readout_every"],
                        "path": {1: "resident", 2: "stream", 3: "dense"}.get(path, str(path)),
+                       "method": args.method,
                        "state": "f32", "l2": "flushed by a 256 MiB write before each timed step",
                        "parallelism": f"replicas-only x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
@@ -575,6 +579,7 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     w = workload(args.workload)
+    w["method"] = args.method
     # each step about 3 s of oracle work: up to 32 replicas (4 for the gradient) x the first K_s steps
     R_s = min(w["R"], 4 if w["kind"] == "grad" else 32)
     rate0, _ = oracle_sample_rate(w, R_s, min(w["K"], 2))
@@ -595,7 +600,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": w["name"], "instance": w["desc"], "n": w["n"], "replicas": w["R"],
+            "config": {"workload": w["name"], "instance": w["desc"], "method": args.method, "n": w["n"], "replicas": w["R"],
                        "integration_steps": w["K"], "readout_every": w["readout_every"]},
             "cpu_baseline": {"value": value, "unit": "spin-updates/s", "cores": used, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "spin-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -609,6 +614,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="chimera_c16")
+    ap.add_argument("--method", default="bsb", choices=["bsb", "asb", "pa"],
+                    help="integrator (App. B): ballistic SB (default), adiabatic SB, Parallel Annealing")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ttt", dest="ttt", action="store_true", default=True,
                     help="measure time-to-target of BF16/FP8 against FP32 on the dense SK instance (default on)")

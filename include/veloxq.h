@@ -60,8 +60,9 @@ typedef enum { VELOXQ_I8 = 0, VELOXQ_I32 = 1, VELOXQ_F32 = 2, VELOXQ_F64 = 3 } v
 
 /* Operand precision of the dense local-field product F = Qoff S. FP32 runs on
  * the CUDA cores; BF16 and FP8 (E4M3 with one FP32 scale per row of Qoff and
- * one per replica of S) run on the tcgen05 tensor cores; all accumulate in
- * FP32. Sparse contexts always use FP32 (or exact int8 couplings). */
+ * the fixed scale 448 for S, whose entries the walls keep in [-1, 1]) run on
+ * the tcgen05 tensor cores; all accumulate in FP32. Sparse contexts always
+ * use FP32 (or exact int8 couplings). */
 typedef enum { VELOXQ_PREC_FP32 = 0, VELOXQ_PREC_BF16 = 1, VELOXQ_PREC_FP8 = 2 } veloxq_prec;
 
 /* Kernel path selection (VELOXQ_PATH_AUTO picks by size and format). */
@@ -71,6 +72,22 @@ typedef enum {
     VELOXQ_PATH_STREAM = 2,    /* sparse rows, one fused launch per step, state in HBM */
     VELOXQ_PATH_DENSE = 3      /* dense Q, one fused field+update launch per step */
 } veloxq_path;
+
+/* Integrator (App. B). Each step forms the field F = Qoff o of an operand o
+ * of the state (s, y) and applies one update, with phi = -(F + b)/2:
+ *   BSB: ballistic simulated bifurcation (default). o = s;
+ *        y <- y + dt(-(a0 - a_k) s + c0 phi), s <- s + dt a0 y, and
+ *        |s| > 1 => s = sign(s), y = 0.
+ *   ASB: adiabatic simulated bifurcation as App. B prints it (quartic
+ *        potential, no walls). o = s;
+ *        y <- y + dt(-(s^2 + a0 - a_k) s + c0 phi), s <- s + dt a0 y.
+ *        Not available with VELOXQ_PREC_FP8 (|s| is unbounded).
+ *   PA:  Parallel Annealing (App. B): s holds the analog spins x, y the
+ *        momenta m; o = sign(s) (+1 where s > 0, else -1);
+ *        g = lambda_k s - c0 phi with lambda_k = (a0 - a_k)/a0,
+ *        m <- momentum m - dt g, x <- clip(x + m, -1, 1).
+ * The readout is x = [s > 0] for all three. veloxq_grad needs BSB. */
+typedef enum { VELOXQ_METHOD_BSB = 0, VELOXQ_METHOD_ASB = 1, VELOXQ_METHOD_PA = 2 } veloxq_method;
 
 /* Integration schedule. App. B fixes a0 = 1, c0 = 1/lambda_max(J) and a(t)
  * increasing linearly through the bifurcation at a(t) ~ a0; the rest is not
@@ -88,6 +105,8 @@ typedef struct {
     int32_t readout_every;  /* read out every this many steps (and after the last); 0 => last only */
     veloxq_prec prec;       /* dense field operand precision; default FP32 */
     veloxq_path path;       /* default AUTO */
+    veloxq_method method;   /* integrator; default BSB */
+    float momentum;         /* PA momentum alpha in [0, 1); default 0.9 */
 } veloxq_schedule;
 
 /* Context facts computed at creation. */
@@ -203,7 +222,8 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
  * 0, the whole batch runs as ONE persistent tensor-core launch (instances
  * assigned to CTAs longest-first; pipeline depth picked by timing a short
  * probe the first time a batch shape is seen), followed by the exact
- * final-readout energies; otherwise each context is solved in turn. */
+ * final-readout energies; otherwise each context is solved in turn. Every
+ * integrator (sched->method) runs in both forms. */
 
 /* Final state of context ctx after the last veloxq_solve_batch that ran the
  * persistent batched kernel (BF16 dense instances, readout only after the

@@ -23,6 +23,7 @@ VELOXQ_OK, VELOXQ_EINVAL, VELOXQ_ENOMEM, VELOXQ_ECUDA, VELOXQ_ETIMEDOUT, VELOXQ_
 VELOXQ_I8, VELOXQ_I32, VELOXQ_F32, VELOXQ_F64 = 0, 1, 2, 3
 VELOXQ_PREC_FP32, VELOXQ_PREC_BF16, VELOXQ_PREC_FP8 = 0, 1, 2
 VELOXQ_PATH_AUTO, VELOXQ_PATH_RESIDENT, VELOXQ_PATH_STREAM, VELOXQ_PATH_DENSE = 0, 1, 2, 3
+VELOXQ_METHOD_BSB, VELOXQ_METHOD_ASB, VELOXQ_METHOD_PA = 0, 1, 2
 
 _VT = {np.dtype(np.int8): VELOXQ_I8, np.dtype(np.int32): VELOXQ_I32,
        np.dtype(np.float32): VELOXQ_F32, np.dtype(np.float64): VELOXQ_F64}
@@ -40,7 +41,8 @@ class Schedule(ctypes.Structure):
     _fields_ = [("dt", ctypes.c_float), ("a0", ctypes.c_float), ("kappa", ctypes.c_float),
                 ("c0", ctypes.c_float), ("sigma0", ctypes.c_float), ("n_knots", ctypes.c_int32),
                 ("a_knots", ctypes.POINTER(ctypes.c_float)), ("readout_every", ctypes.c_int32),
-                ("prec", ctypes.c_int), ("path", ctypes.c_int)]
+                ("prec", ctypes.c_int), ("path", ctypes.c_int), ("method", ctypes.c_int),
+                ("momentum", ctypes.c_float)]
 
 
 class Info(ctypes.Structure):

@@ -89,6 +89,11 @@ int resolve(const veloxq_ctx* ctx, const veloxq_schedule* s_in, int32_t K, RunPa
     if (s.readout_every < 0) return fail(VELOXQ_EINVAL, "schedule readout_every must be >= 0");
     if (s.prec < VELOXQ_PREC_FP32 || s.prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
     if (s.path < VELOXQ_PATH_AUTO || s.path > VELOXQ_PATH_DENSE) return fail(VELOXQ_EINVAL, "unknown path");
+    if (s.method < VELOXQ_METHOD_BSB || s.method > VELOXQ_METHOD_PA) return fail(VELOXQ_EINVAL, "unknown method");
+    if (!(std::isfinite(s.momentum) && s.momentum >= 0 && s.momentum < 1))
+        return fail(VELOXQ_EINVAL, "schedule momentum must be in [0, 1)");
+    if (s.method == VELOXQ_METHOD_ASB && s.prec == VELOXQ_PREC_FP8)
+        return fail(VELOXQ_EUNSUPPORTED, "adiabatic SB leaves [-1, 1]: no FP8 operand with a fixed scale");
     p->dt = s.dt;
     p->a0 = s.a0;
     p->sigma0 = s.sigma0;
@@ -100,6 +105,8 @@ int resolve(const veloxq_ctx* ctx, const veloxq_schedule* s_in, int32_t K, RunPa
     p->readout_every = s.readout_every;
     p->prec = s.prec;
     p->path = s.path;
+    p->method = (int)s.method;
+    p->alpha = s.momentum;
     p->knots.clear();
     if (s.n_knots > 0) {
         for (int j = 0; j < s.n_knots; ++j) {
@@ -204,11 +211,11 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
         if (tc) {
             const int c = k & 1;   // operand of this step in sop[c], next one into sop[c ^ 1]
             VQ_TRY(tc_step(ctx, p.prec, R, tc->mq, tc->ms[c], cur, nxt, Y, tc->sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
-                           nullptr, ctx->errw.as<int>()));
+                           nullptr, ctx->errw.as<int>(), rule_of(p)));
         } else if (path == VELOXQ_PATH_DENSE) {
-            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr, rule_of(p)));
         } else {
-            VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr));
+            VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr, rule_of(p)));
         }
         std::swap(cur, nxt);
         // an event node of the graph (a plain record during capture would only order streams)
@@ -257,6 +264,8 @@ void veloxq_schedule_default(veloxq_schedule* s) {
     s->readout_every = 50;
     s->prec = VELOXQ_PREC_FP32;
     s->path = VELOXQ_PATH_AUTO;
+    s->method = VELOXQ_METHOD_BSB;
+    s->momentum = 0.9f;
 }
 
 const char* veloxq_last_error(void) { return g_err.c_str(); }
@@ -435,7 +444,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         VQ_TRY(launch_init_state(ctx, replicas, seed, p.sigma0, lay, ctx->s_a.as<float>(), ctx->y.as<float>()));
         if (use_tc) {
             VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
-            VQ_TRY(tc_quant_s(ctx, p.prec, replicas, ctx->s_a.as<float>(), tc.sop[0]));
+            VQ_TRY(tc_quant_s(ctx, p.prec, replicas, ctx->s_a.as<float>(), tc.sop[0], rule_of(p)));
         }
         VQ_CUDA(cudaMemsetAsync(ctx->best_e.p, 0x7f, sizeof(int64_t) * R, ctx->stream));
         VQ_CUDA(cudaMemsetAsync(ctx->best_bits.p, 0, sizeof(uint32_t) * R * nw, ctx->stream));
@@ -448,7 +457,8 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
                                      (uint64_t)(uintptr_t)ctx->best_e.p, (uint64_t)(uintptr_t)ctx->best_bits.p,
                                      (uint64_t)(uintptr_t)ctx->flags.p, (uint64_t)(uintptr_t)ctx->misc.p,
                                      (uint64_t)(uintptr_t)ctx->xout.p, (uint64_t)(uintptr_t)ctx->a_table.p};
-        float fp[3] = {p.dt, p.a0, p.c0};
+        key.push_back((uint64_t)p.method);
+        float fp[4] = {p.dt, p.a0, p.c0, p.alpha};
         for (float f : fp) {
             uint32_t u;
             std::memcpy(&u, &f, 4);
@@ -701,11 +711,11 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
             TcRun tc;
             VQ_TRY(tc_setup(ctx, p.prec, R, &tc));
             VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
-            VQ_TRY(tc_quant_s(ctx, p.prec, R, cur, tc.sop[0]));
+            VQ_TRY(tc_quant_s(ctx, p.prec, R, cur, tc.sop[0], rule_of(p)));
             int c = 0;
             for (int k = k_begin; k < k_end; ++k) {
                 VQ_TRY(tc_step(ctx, p.prec, R, tc.mq, tc.ms[c], cur, nxt, Y, tc.sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
-                               k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>()));
+                               k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>(), rule_of(p)));
                 std::swap(cur, nxt);
                 c ^= 1;
             }
@@ -713,7 +723,8 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
             return check_err_word(ctx);
         }
         for (int k = k_begin; k < k_end; ++k) {
-            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, k == k_end - 1 ? F_last : nullptr));
+            VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, k == k_end - 1 ? F_last : nullptr,
+                              rule_of(p)));
             std::swap(cur, nxt);
         }
         VQ_CUDA(cudaMemcpyAsync(S, cur, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -725,7 +736,7 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
     VQ_TRY(launch_transpose(ctx->stream, Y, ctx->y.as<float>(), R, n));
     for (int k = k_begin; k < k_end; ++k) {
         VQ_TRY(stream_step(ctx, R, cur, nxt, ctx->y.as<float>(), at, k, p.dt, p.a0, p.c0,
-                           k == k_end - 1 && F_last ? ctx->f.as<float>() : nullptr));
+                           k == k_end - 1 && F_last ? ctx->f.as<float>() : nullptr, rule_of(p)));
         std::swap(cur, nxt);
     }
     VQ_TRY(launch_transpose(ctx->stream, cur, S, n, R));
@@ -744,6 +755,7 @@ int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_s
     VQ_TRY(resolve(ctx, sched, steps, &p));
     if (ctx->dense || !ctx->has_csr)
         return fail(VELOXQ_EUNSUPPORTED, "the adjoint kernels run on sparse (CSR) contexts");
+    if (p.method != VELOXQ_METHOD_BSB) return fail(VELOXQ_EUNSUPPORTED, "the adjoint is of the ballistic-SB step");
     const int nk = (int)p.knots.size();
     if (nk > 64) return fail(VELOXQ_EINVAL, "at most 64 schedule knots");
     CtxExtra* ex = extra(ctx);

@@ -125,10 +125,12 @@ struct BatchArgs {
     uint64_t seed;
     const float* a_table;
     int* err;
+    int method;                 // veloxq_method (the operand is sign(s) for PA)
+    float alpha;                // PA momentum
 };
 
 template <int STAGES>
-__global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int R = a.R;
@@ -244,13 +246,14 @@ __global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
                 in.S[e] = s0;
                 in.Y[e] = y0;
                 *reinterpret_cast<__nv_bfloat16*>(in.sop0 + (size_t)(i >> 6) * R * TILE_KB + swz(r, i & 63)) =
-                    __float2bfloat16_rn(s0);
+                    __float2bfloat16_rn(vqd::field_operand(a.method, s0));
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
             epi_bar();
             if (et == 0) mb_arrive(stepr);
             for (int k = 0; k < a.K && ok; ++k) {
                 const float a_k = __ldg(a.a_table + k);
+                const float lam = vqd::pa_lambda(a_k, a.a0);
                 uint8_t* sop_n = (k & 1) ? in.sop0 : in.sop1;
                 for (int mt = 0; mt < in.MT; ++mt) {
                     const uint32_t b = tt & 1u;
@@ -272,14 +275,16 @@ __global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             float s = sv[j], y = yv[j];
-                            vqd::bsb_update(__uint_as_float(v[j]), bi, a_k, a.dt, a.a0, in.c0, s, y);
+                            vqd::step_update(a.method, __uint_as_float(v[j]), bi, a_k, lam, a.dt, a.a0, in.c0, a.alpha,
+                                             s, y);
                             if (row_ok) {
                                 const int r = c * 16 + j;
                                 const int64_t p = (int64_t)r * n + row;
                                 in.S[p] = s;
                                 in.Y[p] = y;
                                 *reinterpret_cast<__nv_bfloat16*>(sop_n + (size_t)(row >> 6) * R * TILE_KB +
-                                                                  swz(r, row & 63)) = __float2bfloat16_rn(s);
+                                                                  swz(r, row & 63)) =
+                                    __float2bfloat16_rn(vqd::field_operand(a.method, s));
                             }
                         }
                     }
@@ -410,6 +415,8 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
     a.seed = seed;
     a.a_table = ctxs[0]->a_table.as<float>();
     a.err = d_err;
+    a.method = p.method;
+    a.alpha = p.alpha;
     cudaEvent_t e0, e1;
     VQ_CUDA(cudaEventCreate(&e0));
     VQ_CUDA(cudaEventCreate(&e1));

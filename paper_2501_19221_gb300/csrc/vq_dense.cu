@@ -16,7 +16,7 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
                                                     const float* __restrict__ Qoff, float* __restrict__ S_nxt,
                                                     float* __restrict__ Y, const float* __restrict__ bf,
                                                     const float* __restrict__ a_table, int k, float dt, float a0,
-                                                    float c0, float* __restrict__ F_out) {
+                                                    float c0, float* __restrict__ F_out, int method, float alpha) {
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int tid = threadIdx.x;
@@ -36,7 +36,8 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
         const int64_t gr = m0 + a_row;
         const int64_t gk = (int64_t)kt * BK + a_k;
 #pragma unroll
-        for (int q = 0; q < 4; ++q) ra[q] = (gr < R && gk + q < n) ? __ldg(S_cur + gr * n + gk + q) : 0.0f;
+        for (int q = 0; q < 4; ++q)
+            ra[q] = (gr < R && gk + q < n) ? vqd::field_operand(method, __ldg(S_cur + gr * n + gk + q)) : 0.0f;
         const int64_t bk = (int64_t)kt * BK + b_k;
         const int64_t bc = n0 + b_col;
 #pragma unroll
@@ -77,6 +78,7 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
     }
     // ---- epilogue: field -> update (per output element) ----
     const float a_kv = FIELD_ONLY ? 0.0f : __ldg(a_table + k);
+    const float lam = FIELD_ONLY ? 0.0f : vqd::pa_lambda(a_kv, a0);
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
         const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
@@ -90,7 +92,7 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
             if (F_out) F_out[p] = F;
             if constexpr (!FIELD_ONLY) {
                 float s = S_cur[p], yv = Y[p];
-                vqd::bsb_update(F, __ldg(bf + c), a_kv, dt, a0, c0, s, yv);
+                vqd::step_update(method, F, __ldg(bf + c), a_kv, lam, dt, a0, c0, alpha, s, yv);
                 S_nxt[p] = s;
                 Y[p] = yv;
             }
@@ -179,11 +181,12 @@ __global__ void __launch_bounds__(256) k_dense_energy(int64_t R, int32_t n, cons
 
 template <bool FIELD_ONLY>
 int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table,
-                      int k, float dt, float a0, float c0, float* F_out) {
+                      int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
     const int32_t n = (int32_t)ctx->n;
     dim3 g((unsigned)div_up(n, BN), (unsigned)div_up(R, BM));
     k_dense_step<FIELD_ONLY><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
-                                                         ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out);
+                                                         ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out,
+                                                         rule.method, rule.alpha);
     VQ_LAUNCH_CHECK("dense_step");
     return VELOXQ_OK;
 }
@@ -217,12 +220,12 @@ int launch_dense_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_
 }  // namespace
 
 int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
-               float dt, float a0, float c0, float* F_out) {
-    return launch_dense_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out);
+               float dt, float a0, float c0, float* F_out, const Rule& rule) {
+    return launch_dense_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out, rule);
 }
 
 int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
-    return launch_dense_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+    return launch_dense_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F, Rule());
 }
 
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts) {

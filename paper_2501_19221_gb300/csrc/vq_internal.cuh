@@ -65,6 +65,8 @@ struct RunParams {
     int32_t readout_every;
     veloxq_prec prec;
     veloxq_path path;
+    int method;                 // veloxq_method
+    float alpha;                // PA momentum
     std::vector<double> knots;  // at least 1
 };
 
@@ -142,13 +144,21 @@ int launch_best_bits(veloxq_ctx* ctx, int32_t R, Layout layout, const float* S, 
 int launch_argmin_unpack(veloxq_ctx* ctx, int32_t R, const int64_t* best, const uint32_t* bits,
                          int64_t* misc, uint8_t* x);
 
+// The integrator of a step (veloxq_method) and PA's momentum.
+struct Rule {
+    int method = 0;
+    float alpha = 0.f;
+};
+inline Rule rule_of(const RunParams& p) { return Rule{p.method, p.alpha}; }
+
 // sparse streaming kernels (vq_stream.cu)
 int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y,
-                const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+                const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule = Rule());
 int stream_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int stream_step_y(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
-                  const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+                  const float* a_table, int k, float dt, float a0, float c0, float* F_out,
+                  const Rule& rule = Rule());
 int vec_width(int32_t R);
 int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y);
 
@@ -160,7 +170,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, uint64_t seed, 
 
 // dense kernels (vq_dense.cu)
 int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y,
-               const float* a_table, int k, float dt, float a0, float c0, float* F_out);
+               const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule = Rule());
 int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
@@ -185,11 +195,11 @@ int64_t tc_pad(int64_t n);
 int tc_prepare_q(veloxq_ctx* ctx, int prec);
 int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtensorMap* mq, CUtensorMap* ms0,
             CUtensorMap* ms1);
-int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop);
+int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule = Rule());
 size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R);
 int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
             float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
-            float* F_out, int* err);
+            float* F_out, int* err, const Rule& rule = Rule());
 int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
 
 }  // namespace vq
@@ -304,6 +314,46 @@ __device__ __forceinline__ void bsb_update2(float F0, float F1, float b, float a
     if (fabsf(sh1) > 1.0f) { s1 = copysignf(1.0f, sh1); y1 = 0.0f; } else { s1 = sh1; y1 = yh1; }
 }
 
+// ---- the other integrators (veloxq_method): adiabatic SB as printed and
+// Parallel Annealing; every kernel applies the same operation order ----
+enum { METHOD_BSB = 0, METHOD_ASB = 1, METHOD_PA = 2 };
+
+// Field operand of the state: s itself, or PA's binarised spin (+1 where
+// s > 0, -1 elsewhere: the readout's rule).
+__device__ __forceinline__ float pa_sign(float s) { return s > 0.0f ? 1.0f : -1.0f; }
+__device__ __forceinline__ float field_operand(int method, float s) { return method == METHOD_PA ? pa_sign(s) : s; }
+
+// lambda_k = (a0 - a_k)/a0 of Parallel Annealing
+__device__ __forceinline__ float pa_lambda(float a_k, float a0) { return __fdiv_rn(__fsub_rn(a0, a_k), a0); }
+
+// y <- y + dt(-(s^2 + a0 - a_k) s + c0 phi), s <- s + dt a0 y (no walls)
+__device__ __forceinline__ void asb_update(float F, float b, float a_k, float dt, float a0, float c0, float& s,
+                                           float& y) {
+    const float t = __fadd_rn(F, b);
+    const float coef = __fadd_rn(__fmul_rn(s, s), __fsub_rn(a0, a_k));
+    const float drive = fmaf(__fmul_rn(-0.5f, c0), t, -__fmul_rn(coef, s));
+    const float yh = fmaf(dt, drive, y);
+    s = fmaf(__fmul_rn(dt, a0), yh, s);
+    y = yh;
+}
+
+// g = lambda x + c0 (F + b)/2, m <- alpha m - dt g, x <- clip(x + m, -1, 1)
+__device__ __forceinline__ void pa_update(float F, float b, float lam, float dt, float alpha, float c0, float& x,
+                                          float& m) {
+    const float t = __fadd_rn(F, b);
+    const float g = fmaf(lam, x, __fmul_rn(__fmul_rn(0.5f, c0), t));
+    m = fmaf(alpha, m, -__fmul_rn(dt, g));
+    x = fminf(fmaxf(__fadd_rn(x, m), -1.0f), 1.0f);
+}
+
+// One update of the given method; lam is pa_lambda(a_k, a0) (PA only).
+__device__ __forceinline__ void step_update(int method, float F, float b, float a_k, float lam, float dt, float a0,
+                                            float c0, float alpha, float& s, float& y) {
+    if (method == METHOD_PA) pa_update(F, b, lam, dt, alpha, c0, s, y);
+    else if (method == METHOD_ASB) asb_update(F, b, a_k, dt, a0, c0, s, y);
+    else bsb_update(F, b, a_k, dt, a0, c0, s, y);
+}
+
 // Vector loads/stores of V consecutive replicas.
 template <int V> __device__ __forceinline__ void vload(const float* p, float (&v)[V]) {
     if constexpr (V == 4) { const float4 t = __ldg(reinterpret_cast<const float4*>(p)); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
@@ -329,7 +379,13 @@ __device__ __forceinline__ float wval(int8_t w) { return (float)w; }
 // couplings per round so that their gathers are in flight together (a slot
 // past the row end reads row i itself with weight 0 and adds an exact 0);
 // UNROLL = 1 is the plain loop. Both give the same sums.
-template <int V, typename WT, int UNROLL>
+// acc = sum over row i of w_ij o(X_j) for V replicas, o the identity or (SIGN)
+// PA's binarised spin.
+template <int V> __device__ __forceinline__ void sign_vec(float (&v)[V]) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = pa_sign(v[l]);
+}
+template <int V, typename WT, int UNROLL, bool SIGN = false>
 __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const WT* __restrict__ w, const float* X, int32_t R, int64_t off,
                                             int64_t i, float (&acc)[V], int udeg = -1) {
@@ -350,6 +406,10 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
         float sj[6][V];
 #pragma unroll
         for (int u = 0; u < 6; ++u) vload<V>(X + (int64_t)j[u] * R + off, sj[u]);
+        if constexpr (SIGN) {
+#pragma unroll
+            for (int u = 0; u < 6; ++u) sign_vec<V>(sj[u]);
+        }
 #pragma unroll
         for (int u = 0; u < 6; ++u)
 #pragma unroll
@@ -365,6 +425,7 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
             const float wv = wval(__ldg(w + p));
             float sj[V];
             vload<V>(X + j * R + off, sj);
+            if constexpr (SIGN) sign_vec<V>(sj);
 #pragma unroll
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
         }
@@ -381,6 +442,10 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
         float sj[4][V];
 #pragma unroll
         for (int u = 0; u < 4; ++u) vload<V>(X + j[u] * R + off, sj[u]);
+        if constexpr (SIGN) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sign_vec<V>(sj[u]);
+        }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll

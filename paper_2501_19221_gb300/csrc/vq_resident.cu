@@ -10,13 +10,18 @@ namespace {
 
 using namespace resident;
 
-KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, bool ell) {
-    switch (rc) {
-        case 1: return resident_pick_rc1(rpt, csr_smem, packed, ell);
-        case 2: return resident_pick_rc2(rpt, csr_smem, packed, ell);
-        case 4: return resident_pick_rc4(rpt, csr_smem, packed, ell);
-        default: return resident_pick_rc8(rpt, csr_smem, packed, ell);
+KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, bool ell, int method) {
+#define VQ_PICK_RC(M)                                                           \
+    switch (rc) {                                                               \
+        case 1: return resident_pick_rc1_m##M(rpt, csr_smem, packed, ell);    \
+        case 2: return resident_pick_rc2_m##M(rpt, csr_smem, packed, ell);    \
+        case 4: return resident_pick_rc4_m##M(rpt, csr_smem, packed, ell);    \
+        default: return resident_pick_rc8_m##M(rpt, csr_smem, packed, ell);   \
     }
+    if (method == VELOXQ_METHOD_PA) { VQ_PICK_RC(2) }
+    if (method == VELOXQ_METHOD_ASB) { VQ_PICK_RC(1) }
+    VQ_PICK_RC(0)
+#undef VQ_PICK_RC
 }
 
 struct ResPlan {
@@ -101,6 +106,8 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed,
     a.readout_every = best_e ? rp.readout_every : -1;
     a.nwords = (int32_t)div_up(ctx->n, 32);
     a.ell_d = p.ell_d;
+    a.method = rp.method;
+    a.alpha = rp.alpha;
     a.dt = rp.dt;
     a.a0 = rp.a0;
     a.c0 = rp.c0;
@@ -120,7 +127,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed,
     a.F_out = F_out;
     a.best_e = best_e;
     a.best_bits = best_bits;
-    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d > 0);
+    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d > 0, rp.method);
     if (!fn) return fail(VELOXQ_EUNSUPPORTED, "no resident kernel variant for this plan");
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     fn<<<(unsigned)div_up(R, p.rc), p.threads, p.smem, ctx->stream>>>(a);

@@ -1,0 +1,9 @@
+// vq_resident_bsb_rc2.cu -- resident-kernel variants of the ballistic form with 2
+// replica(s) per CTA.
+#include "vq_resident_kernel.cuh"
+
+namespace vq {
+
+VQ_RESIDENT_PICK(2, 0) { return resident::pick_rpt<2, 0>(rpt, csr_smem, packed, ell); }
+
+}  // namespace vq

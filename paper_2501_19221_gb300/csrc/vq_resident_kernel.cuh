@@ -26,6 +26,8 @@ constexpr int kSmemMax = 232448;   // 227 KB opt-in per CTA
 struct ResArgs {
     int32_t n, R, K, k_begin, k_end, readout_every, nwords;
     int32_t ell_d;         // ELL layout: slots per row (even), else 0
+    int32_t method;        // veloxq_method
+    float alpha;           // PA momentum
     float dt, a0, c0, sigma0;
     uint64_t seed;
     const int64_t* rowptr;
@@ -156,8 +158,16 @@ template <int RC> __device__ __forceinline__ void acc_fma(float (&acc)[RC], floa
 
 __device__ __forceinline__ float ent_w(uint32_t e) { return __half2float(__ushort_as_half((unsigned short)(e >> 16))); }
 
-template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, bool ELL>
+template <int RC> __device__ __forceinline__ void sign_row(float (&v)[RC]) {
+#pragma unroll
+    for (int r = 0; r < RC; ++r) v[r] = vqd::pa_sign(v[r]);
+}
+
+// METHOD: the integrator (veloxq_method). For PA the state buffers hold the
+// analog spins x and the field is of their binarised spins.
+template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, bool ELL, int METHOD>
 __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
+    constexpr bool SIGN = METHOD == vqd::METHOD_PA;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n;
     const int T = blockDim.x;
@@ -248,6 +258,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                         float s0[RC], s1[RC];
                         ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
                         ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
+                        if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); }
                         acc_fma<RC>(acc, ent_w(e0), s0);
                         acc_fma<RC>(acc, ent_w(e1), s1);
                     }
@@ -268,13 +279,21 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                             else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
                             ld_row<RC>(sc, j, sj);
                         }
+                        if constexpr (SIGN) sign_row<RC>(sj);
                         acc_fma<RC>(acc, w, sj);
                     }
                 }
                 float s[RC];
                 ld_row<RC>(sc, i, s);
                 const float b = bsh[i];
-                if constexpr (RC >= 2) {
+                if constexpr (METHOD == vqd::METHOD_PA) {
+                    const float lam = vqd::pa_lambda(a_k, a.a0);
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) vqd::pa_update(acc[r], b, lam, a.dt, a.alpha, a.c0, s[r], y[q][r]);
+                } else if constexpr (METHOD == vqd::METHOD_ASB) {
+#pragma unroll
+                    for (int r = 0; r < RC; ++r) vqd::asb_update(acc[r], b, a_k, a.dt, a.a0, a.c0, s[r], y[q][r]);
+                } else if constexpr (RC >= 2) {
 #pragma unroll
                     for (int r = 0; r < RC; r += 2)
                         vqd::bsb_update2(acc[r], acc[r + 1], b, a_k, a.dt, a.a0, a.c0, s[r], s[r + 1], y[q][r],
@@ -414,33 +433,36 @@ using KFn = void (*)(const ResArgs);
 
 // 1024-thread CTAs keep at most 8 momenta per thread in registers (64-register
 // cap); 512-thread CTAs up to 32.
-template <int RC, int RPT> KFn pick_csr(bool csr_smem, bool packed, bool ell) {
+template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, bool ell) {
     constexpr int MAXT = (RC * RPT <= 8) ? 1024 : 512;
     if constexpr (RC * RPT > 32) {
         return nullptr;   // never planned (the momenta do not fit in registers)
     } else {
-        if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, false>;
-        if (ell) return k_resident<RC, RPT, true, true, MAXT, true>;
-        return packed ? k_resident<RC, RPT, true, true, MAXT, false> : k_resident<RC, RPT, true, false, MAXT, false>;
+        if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, false, METHOD>;
+        if (ell) return k_resident<RC, RPT, true, true, MAXT, true, METHOD>;
+        return packed ? k_resident<RC, RPT, true, true, MAXT, false, METHOD>
+                      : k_resident<RC, RPT, true, false, MAXT, false, METHOD>;
     }
 }
 
-template <int RC> KFn pick_rpt(int rpt, bool csr_smem, bool packed, bool ell) {
+// the variants of one replica count per CTA and one integrator
+template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, bool ell) {
     switch (rpt) {
-        case 1: return pick_csr<RC, 1>(csr_smem, packed, ell);
-        case 2: return pick_csr<RC, 2>(csr_smem, packed, ell);
-        case 4: return pick_csr<RC, 4>(csr_smem, packed, ell);
-        case 8: return pick_csr<RC, 8>(csr_smem, packed, ell);
-        default: return pick_csr<RC, 16>(csr_smem, packed, ell);
+        case 1: return pick_csr<RC, 1, METHOD>(csr_smem, packed, ell);
+        case 2: return pick_csr<RC, 2, METHOD>(csr_smem, packed, ell);
+        case 4: return pick_csr<RC, 4, METHOD>(csr_smem, packed, ell);
+        case 8: return pick_csr<RC, 8, METHOD>(csr_smem, packed, ell);
+        default: return pick_csr<RC, 16, METHOD>(csr_smem, packed, ell);
     }
 }
 
 }  // namespace resident
 
-// one per replica count per CTA (vq_resident_rc*.cu)
-resident::KFn resident_pick_rc1(int rpt, bool csr_smem, bool packed, bool ell);
-resident::KFn resident_pick_rc2(int rpt, bool csr_smem, bool packed, bool ell);
-resident::KFn resident_pick_rc4(int rpt, bool csr_smem, bool packed, bool ell);
-resident::KFn resident_pick_rc8(int rpt, bool csr_smem, bool packed, bool ell);
+// one per replica count per CTA and integrator (vq_resident_*.cu, compiled in parallel)
+#define VQ_RESIDENT_PICK(RC, M) \
+    resident::KFn resident_pick_rc##RC##_m##M(int rpt, bool csr_smem, bool packed, bool ell)
+VQ_RESIDENT_PICK(1, 0); VQ_RESIDENT_PICK(2, 0); VQ_RESIDENT_PICK(4, 0); VQ_RESIDENT_PICK(8, 0);
+VQ_RESIDENT_PICK(1, 1); VQ_RESIDENT_PICK(2, 1); VQ_RESIDENT_PICK(4, 1); VQ_RESIDENT_PICK(8, 1);
+VQ_RESIDENT_PICK(1, 2); VQ_RESIDENT_PICK(2, 2); VQ_RESIDENT_PICK(4, 2); VQ_RESIDENT_PICK(8, 2);
 
 }  // namespace vq

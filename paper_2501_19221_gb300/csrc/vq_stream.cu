@@ -18,15 +18,16 @@ using vqd::vstore;
 using vqd::wval;
 
 // One thread per (variable i, vector v of V replicas). Y_in and Y_out may be
-// the same buffer (in-place update).
-template <int V, typename WT, bool FIELD_ONLY, int UNROLL>
+// the same buffer (in-place update). SIGN: the field is of PA's binarised
+// spins; method selects the update (veloxq_method).
+template <int V, typename WT, bool FIELD_ONLY, int UNROLL, bool SIGN>
 __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
                                                      const int32_t* __restrict__ col, const WT* __restrict__ w,
                                                      float wscale, const float* __restrict__ S_cur,
                                                      float* __restrict__ S_nxt, const float* Y_in, float* Y_out,
                                                      const float* __restrict__ bf, const float* __restrict__ a_table,
                                                      int k, float dt, float a0, float c0, float* __restrict__ F_out,
-                                                     int udeg) {
+                                                     int udeg, int method, float alpha) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t i = t / nvec;
     if (i >= n) return;
@@ -42,14 +43,20 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
         a_k = __ldg(a_table + k);
     }
     float acc[V];
-    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S_cur, R, off, i, acc, udeg);
+    vqd::csr_row_dot<V, WT, UNROLL, SIGN>(rp, col, w, S_cur, R, off, i, acc, udeg);
     float F[V];
 #pragma unroll
     for (int l = 0; l < V; ++l) F[l] = acc[l] * wscale;     // wscale is 1 or 1/2: exact
     if (F_out) vstore<V>(F_out + me, F);
     if constexpr (FIELD_ONLY) return;
+    if (method == vqd::METHOD_BSB) {
 #pragma unroll
-    for (int l = 0; l < V; ++l) vqd::bsb_update(F[l], b, a_k, dt, a0, c0, s[l], y[l]);
+        for (int l = 0; l < V; ++l) vqd::bsb_update(F[l], b, a_k, dt, a0, c0, s[l], y[l]);
+    } else {
+        const float lam = vqd::pa_lambda(a_k, a0);
+#pragma unroll
+        for (int l = 0; l < V; ++l) vqd::step_update(method, F[l], b, a_k, lam, dt, a0, c0, alpha, s[l], y[l]);
+    }
     vstore<V>(S_nxt + me, s);
     vstore<V>(Y_out + me, y);
 }
@@ -139,9 +146,9 @@ __global__ void __launch_bounds__(256) k_sparse_energy_x(int64_t n, int64_t B, c
     if (threadIdx.x == 0) parts[(int64_t)blockIdx.x * B + b] = sh[0];
 }
 
-template <bool FIELD_ONLY>
+template <bool FIELD_ONLY, bool SIGN>
 int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
-                const float* a_table, int k, float dt, float a0, float c0, float* F_out) {
+                const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
     const int V = vec_width(R);
     const int32_t nvec = R / V;
     const int64_t total = ctx->n * (int64_t)nvec;
@@ -150,9 +157,10 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
     const int32_t* cl = ctx->col.as<int32_t>();
     const float* bf = ctx->bf.as<float>();
     cudaStream_t st = ctx->stream;
-#define VQ_STEP_U(VV, WT, WPTR, SC, U)                                                                               \
-    k_stream_step<VV, WT, FIELD_ONLY, U><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, Y_in, Y_out, \
-                                                            bf, a_table, k, dt, a0, c0, F_out, ctx->uniform_deg)
+#define VQ_STEP_U(VV, WT, WPTR, SC, U)                                                                       \
+    k_stream_step<VV, WT, FIELD_ONLY, U, SIGN><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
+                                                                  Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out, \
+                                                                  ctx->uniform_deg, rule.method, rule.alpha)
 #define VQ_STEP(VV, WT, WPTR, SC)                                   \
     do {                                                            \
         if (unroll == 6) VQ_STEP_U(VV, WT, WPTR, SC, 6);            \
@@ -178,17 +186,21 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
 int vec_width(int32_t R) { return (R % 4 == 0) ? 4 : (R % 2 == 0) ? 2 : 1; }
 
 int stream_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
-                float dt, float a0, float c0, float* F_out) {
-    return launch_step<false>(ctx, R, S_cur, S_nxt, Y, Y, a_table, k, dt, a0, c0, F_out);
+                float dt, float a0, float c0, float* F_out, const Rule& rule) {
+    if (rule.method == VELOXQ_METHOD_PA)
+        return launch_step<false, true>(ctx, R, S_cur, S_nxt, Y, Y, a_table, k, dt, a0, c0, F_out, rule);
+    return launch_step<false, false>(ctx, R, S_cur, S_nxt, Y, Y, a_table, k, dt, a0, c0, F_out, rule);
 }
 
 int stream_step_y(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, const float* Y_in, float* Y_out,
-                  const float* a_table, int k, float dt, float a0, float c0, float* F_out) {
-    return launch_step<false>(ctx, R, S_cur, S_nxt, Y_in, Y_out, a_table, k, dt, a0, c0, F_out);
+                  const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
+    if (rule.method == VELOXQ_METHOD_PA)
+        return launch_step<false, true>(ctx, R, S_cur, S_nxt, Y_in, Y_out, a_table, k, dt, a0, c0, F_out, rule);
+    return launch_step<false, false>(ctx, R, S_cur, S_nxt, Y_in, Y_out, a_table, k, dt, a0, c0, F_out, rule);
 }
 
 int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
-    return launch_step<true>(ctx, R, S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F);
+    return launch_step<true, false>(ctx, R, S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F, Rule());
 }
 
 // Pick the gather variant of the streaming kernels for R replicas by timing
@@ -206,11 +218,11 @@ int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y
     for (int u : {1, 4, 6}) {
         if (u == 6 && ctx->uniform_deg != 6) continue;
         ctx->stream_unroll = u;
-        VQ_TRY(launch_step<false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr));   // warm
+        VQ_TRY((launch_step<false, false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr, Rule())));   // warm
         VQ_CUDA(cudaEventRecord(e0, ctx->stream));
         for (int k = 0; k < 3; ++k)
-            VQ_TRY(launch_step<false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f,
-                                      nullptr));
+            VQ_TRY((launch_step<false, false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f,
+                                              1.0f, 0.1f, nullptr, Rule())));
         VQ_CUDA(cudaEventRecord(e1, ctx->stream));
         VQ_CUDA(cudaEventSynchronize(e1));
         float ms = 0.f;

@@ -210,6 +210,7 @@ struct TcArgs {
     const float* a_table;
     float* F_out;            // [R][n] or null
     int* err;
+    float alpha;             // PA momentum
 };
 
 template <int PREC> __device__ __forceinline__ void store_op(void* base, int64_t idx, float s) {
@@ -221,7 +222,9 @@ template <int PREC> __device__ __forceinline__ void store_op(void* base, int64_t
     }
 }
 
-template <int PREC, bool FIELD_ONLY>
+// METHOD: the integrator (veloxq_method), a template parameter so that each
+// form keeps its own register allocation.
+template <int PREC, bool FIELD_ONLY, int METHOD>
 __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
                                                     const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
     extern __shared__ uint8_t smem_raw[];
@@ -315,6 +318,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
         const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
+        const float lam = (FIELD_ONLY || METHOD != vqd::METHOD_PA) ? 0.0f : vqd::pa_lambda(a_k, a.a0);
         const uint32_t acce_cl = mapa(smem_u32(&acce[0]), 0);
         uint32_t tt = 0;
         for (int tw = pair; tw < tiles; tw += pairs, ++tt) {
@@ -358,11 +362,14 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     if (ok && a.F_out) a.F_out[p] = F;
                     if constexpr (!FIELD_ONLY) {
                         float s = sv[j], y = yv[j];
-                        vqd::bsb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
+                        if constexpr (METHOD == vqd::METHOD_PA) vqd::pa_update(F, bi, lam, a.dt, a.alpha, a.c0, s, y);
+                        else if constexpr (METHOD == vqd::METHOD_ASB) vqd::asb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
+                        else vqd::bsb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
                         if (ok) {
                             a.S_nxt[p] = s;
                             a.Y[p] = y;
-                            store_op<PREC>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row, s);
+                            store_op<PREC>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row,
+                                           METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
                         }
                     }
                 }
@@ -421,11 +428,11 @@ __global__ void k_quant_q_fp8(int64_t n, int64_t n_pad, const float* __restrict_
 }
 
 template <int PREC>
-__global__ void k_quant_s(int64_t R, int64_t n, int64_t n_pad, const float* __restrict__ S, void* out) {
+__global__ void k_quant_s(int64_t R, int64_t n, int64_t n_pad, const float* __restrict__ S, void* out, int method) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= R * n_pad) return;
     const int64_t r = t / n_pad, j = t - r * n_pad;
-    store_op<PREC>(out, t, j < n ? S[r * n + j] : 0.0f);
+    store_op<PREC>(out, t, j < n ? vqd::field_operand(method, S[r * n + j]) : 0.0f);
 }
 
 // ---- tensor maps ------------------------------------------------------------
@@ -503,13 +510,13 @@ int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtens
     return VELOXQ_OK;
 }
 
-int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop) {
+int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule) {
     const int64_t n = ctx->n, np = tc_pad(n);
     const int64_t total = (int64_t)R * np;
     if (prec == VELOXQ_PREC_BF16)
-        k_quant_s<1><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop);
+        k_quant_s<1><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
     else
-        k_quant_s<2><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop);
+        k_quant_s<2><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
     VQ_LAUNCH_CHECK("tc quantize S");
     return VELOXQ_OK;
 }
@@ -522,7 +529,7 @@ size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R) {
 // mapS_cur, writes the next operand into sop_nxt.
 int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
             float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
-            float* F_out, int* err) {
+            float* F_out, int* err, const Rule& rule) {
     TcArgs a;
     a.n = (int32_t)ctx->n;
     a.R = R;
@@ -540,6 +547,7 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     a.a_table = a_table;
     a.F_out = F_out;
     a.err = err;
+    a.alpha = rule.alpha;
     // persistent: one CTA per SM in clusters of two (at most one pair per
     // pair tile), pair tiles strided over the pairs
     static int sms = 0;
@@ -551,8 +559,17 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     const int64_t tiles = div_up(ctx->n, 2 * BM) * div_up(R, BN);
     const bool field_only = S_nxt == nullptr;
     void (*fn)(const CUtensorMap, const CUtensorMap, const TcArgs);
-    if (prec == VELOXQ_PREC_BF16) fn = field_only ? k_tc_step<1, true> : k_tc_step<1, false>;
-    else fn = field_only ? k_tc_step<2, true> : k_tc_step<2, false>;
+    if (prec == VELOXQ_PREC_BF16) {
+        fn = field_only                                  ? k_tc_step<1, true, 0>
+             : rule.method == VELOXQ_METHOD_PA ? k_tc_step<1, false, vqd::METHOD_PA>
+             : rule.method == VELOXQ_METHOD_ASB ? k_tc_step<1, false, vqd::METHOD_ASB>
+                                                : k_tc_step<1, false, vqd::METHOD_BSB>;
+    } else {
+        fn = field_only                                  ? k_tc_step<2, true, 0>
+             : rule.method == VELOXQ_METHOD_PA ? k_tc_step<2, false, vqd::METHOD_PA>
+             : rule.method == VELOXQ_METHOD_ASB ? k_tc_step<2, false, vqd::METHOD_ASB>
+                                                : k_tc_step<2, false, vqd::METHOD_BSB>;
+    }
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(320);

@@ -41,9 +41,37 @@ def test_library_exports_every_declared_symbol(lib):
 
 def test_schedule_defaults(lib):
     s = lib.veloxq_schedule_default()
-    assert (s.dt, s.a0, s.kappa, s.c0, s.sigma0, s.n_knots, s.readout_every, s.prec, s.path) == \
-        (0.5, 1.0, 1.0, 0.0, pytest.approx(0.1), 0, 50, 0, 0)
-    assert ctypes.sizeof(lib.Schedule) == 48 and ctypes.sizeof(lib.Info) == 48
+    assert (s.dt, s.a0, s.kappa, s.c0, s.sigma0, s.n_knots, s.readout_every, s.prec, s.path, s.method) == \
+        (0.5, 1.0, 1.0, 0.0, pytest.approx(0.1), 0, 50, 0, 0, 0)
+    assert s.momentum == pytest.approx(0.9)
+
+
+def test_struct_layouts_match_the_header(lib, tmp_path):
+    """The ctypes mirrors have the sizes and field offsets the C header gives
+    (compiled here with the host C compiler)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    structs = {"veloxq_schedule": lib.Schedule, "veloxq_info": lib.Info, "veloxq_timing": lib.Timing}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "veloxq.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f, _ in py._fields_:
+            lines.append(f'printf("{cname}.{f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], capture_output=True, text=True,
+                                                       check=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f, _ in py._fields_:
+            assert int(got[f"{cname}.{f}"]) == getattr(py, f).offset, (cname, f)
 
 
 def test_argument_errors_before_device(lib):
