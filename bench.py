@@ -42,7 +42,7 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # the current kernel build (summaries and commands in profiles/); a kernel that
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
-    ("k_resident", "chimera_c16"): 285_952,
+    ("k_resident", "chimera_c16"): 291_072,
     ("k_tc_step", "sk_n8192_fp8"): 178_763_520,
     ("k_tc_step", "sk_n8192_bf16"): 286_354_432,
     ("k_stream_step", "lattice_l100"): 4_126_558_000,
@@ -339,12 +339,13 @@ def roofline(B, w, runner, path, main_ms, main_launches):
             "algorithmic_bytes_per_launch": hbm_bytes, "ms_per_launch": per}
 
 
-def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200):
+def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200, method=0):
     """Time-to-target of the mixed-precision forms against the plain FP32
-    form on the dense SK instance (n = 8192, 1024 replicas). The target E* is
-    the median over `seeds` of the FP32 form's best energy after K steps; a
-    form reaches it at the smallest K' of a grid where at least half of the
-    seeds end at or below E*. Times are CUDA-event times of whole solves."""
+    form on the dense SK instance (n = 8192, 1024 replicas), for one
+    integrator. The target E* is the median over `seeds` of the FP32 form's
+    best energy after K steps; a form reaches it at the smallest K' of a grid
+    where at least half of the seeds end at or below E*. Times are CUDA-event
+    times of whole solves."""
     import torch
     Q, c = I.sk_qubo(n, seed=0)
     ctx = B.veloxq_create_dense(Q, c)
@@ -353,13 +354,14 @@ def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200):
     def solve(prec, steps, seed):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        E = B.veloxq_solve(ctx, R, steps, B.make_schedule(prec=prec, readout_every=0), seed=seed, want_x=False,
-                           want_per_replica=False)["E"]
+        E = B.veloxq_solve(ctx, R, steps, B.make_schedule(prec=prec, readout_every=0, method=method), seed=seed,
+                           want_x=False, want_per_replica=False)["E"]
         e1.record(stream)
         torch.cuda.synchronize()
         return E, e0.elapsed_time(e1)
 
-    out = {"workload": f"sk n={n}, {R} replicas, final readout only", "seeds": seeds}
+    out = {"workload": f"sk n={n}, {R} replicas, final readout only", "seeds": seeds,
+           "method": {0: "bsb", 1: "asb", 2: "pa"}[method]}
     with torch.cuda.stream(stream):
         solve(0, 4, 0)
         fp32 = [solve(0, K, 100 + s) for s in range(seeds)]
@@ -379,6 +381,53 @@ def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200):
             out[name] = best
             out[f"speedup_{name}"] = (t32 / best["ms"]) if best else None
     ctx.destroy()
+    return out
+
+
+def time_to_target_batch(B, stream, seeds=4, K=1000, R=64):
+    """Time-to-target of the batched form (one persistent BF16 launch for the
+    512 Wishart instances) against the plain FP32 form (each instance solved
+    in turn on the CUDA-core path). Per instance, the target is the median
+    over `seeds` of the FP32 form's best energy after K steps; a form's
+    success is the fraction of (instance, seed) pairs at or below their
+    target, and it reaches the targets at the smallest K' of a grid with
+    success >= 0.5 (the FP32 form's own success is about 0.5 by
+    construction). Times are CUDA-event times of the whole batch."""
+    import torch
+    w = workload("wishart_b512")
+    ctxs = [B.veloxq_create_ising_dense(J, None) for J in batch_instances(w)]
+    for cx in ctxs:
+        B.veloxq_set_stream(cx, stream.cuda_stream)
+
+    def run(prec, steps, seed):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sched = B.make_schedule(prec=prec, readout_every=0, path=3)
+        e0.record(stream)
+        E = B.veloxq_solve_batch(ctxs, R, steps, sched, seed=seed, want_x=False)["E"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return np.asarray(E), e0.elapsed_time(e1)
+
+    out = {"workload": f"Wishart batch of {len(ctxs)} instances, {R} replicas, final readout only", "seeds": seeds}
+    with torch.cuda.stream(stream):
+        fp32 = [run(0, K, 300 + s) for s in range(seeds)]
+        E32 = np.stack([e for e, _ in fp32])                     # [seeds][instances]
+        E_star = np.median(E32, axis=0)
+        t32 = float(np.median([t for _, t in fp32]))
+        out["fp32"] = {"steps": K, "ms": t32, "success": float(np.mean(E32 <= E_star[None, :]))}
+        run(1, 4, 0)
+        best = None
+        for k2 in (100, 250, 500, K, 2 * K):
+            runs = [run(1, k2, 300 + s) for s in range(seeds)]
+            Eb = np.stack([e for e, _ in runs])
+            p = float(np.mean(Eb <= E_star[None, :]))
+            if p >= 0.5:
+                best = {"steps": k2, "ms": float(np.median([t for _, t in runs])), "success": p}
+                break
+        out["batched_bf16"] = best
+        out["speedup"] = (t32 / best["ms"]) if best else None
+    for cx in ctxs:
+        cx.destroy()
     return out
 
 
@@ -513,6 +562,12 @@ def run_ours(args, rank, world, local_rank):
     ttt = None
     if args.ttt and rank == 0:
         ttt = time_to_target(B, stream, seeds=args.ttt_seeds)
+        ttt_pa = time_to_target(B, stream, seeds=args.ttt_seeds, method=2)
+        ttt = {"bsb": ttt, "pa": ttt_pa}
+    if args.ttt_batch and rank == 0:
+        ttt_batch = time_to_target_batch(B, stream, seeds=4)
+    else:
+        ttt_batch = None
     tts = None
     if rank == 0 and w["name"] in ("dense_n20", "wishart_b512"):
         tts = tts_study(B, run, w, stream, seeds=32 if w["name"] == "dense_n20" else 4)
@@ -549,6 +604,7 @@ def run_ours(args, rank, world, local_rank):
                        "parallelism": f"replicas-only x{world}"},
             "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
             "time_to_target": ttt,
+            "time_to_target_batch": ttt_batch,
             "tts99": tts,
             "clocks": clk,
             "quality": {"best_energy_last_step": results[-1]},
@@ -621,6 +677,8 @@ def main():
                     help="measure time-to-target of BF16/FP8 against FP32 on the dense SK instance (default on)")
     ap.add_argument("--no-ttt", dest="ttt", action="store_false")
     ap.add_argument("--ttt-seeds", type=int, default=8)
+    ap.add_argument("--ttt-batch", action="store_true",
+                    help="time-to-target of the batched BF16 form against the plain FP32 form on the Wishart batch")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

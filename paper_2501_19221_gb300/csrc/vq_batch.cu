@@ -125,12 +125,13 @@ struct BatchArgs {
     uint64_t seed;
     const float* a_table;
     int* err;
-    int method;                 // veloxq_method (the operand is sign(s) for PA)
     float alpha;                // PA momentum
 };
 
-template <int STAGES>
-__global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchArgs a) {
+// METHOD: the integrator (veloxq_method), a template parameter so that the
+// ballistic form keeps its own register allocation.
+template <int STAGES, int METHOD>
+__global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     const int R = a.R;
@@ -246,14 +247,14 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                 in.S[e] = s0;
                 in.Y[e] = y0;
                 *reinterpret_cast<__nv_bfloat16*>(in.sop0 + (size_t)(i >> 6) * R * TILE_KB + swz(r, i & 63)) =
-                    __float2bfloat16_rn(vqd::field_operand(a.method, s0));
+                    __float2bfloat16_rn(METHOD == vqd::METHOD_PA ? vqd::pa_sign(s0) : s0);
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
             epi_bar();
             if (et == 0) mb_arrive(stepr);
             for (int k = 0; k < a.K && ok; ++k) {
                 const float a_k = __ldg(a.a_table + k);
-                const float lam = vqd::pa_lambda(a_k, a.a0);
+                const float lam = METHOD == vqd::METHOD_PA ? vqd::pa_lambda(a_k, a.a0) : 0.0f;
                 uint8_t* sop_n = (k & 1) ? in.sop0 : in.sop1;
                 for (int mt = 0; mt < in.MT; ++mt) {
                     const uint32_t b = tt & 1u;
@@ -275,8 +276,10 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             float s = sv[j], y = yv[j];
-                            vqd::step_update(a.method, __uint_as_float(v[j]), bi, a_k, lam, a.dt, a.a0, in.c0, a.alpha,
-                                             s, y);
+                            const float F = __uint_as_float(v[j]);
+                            if constexpr (METHOD == vqd::METHOD_PA) vqd::pa_update(F, bi, lam, a.dt, a.alpha, in.c0, s, y);
+                            else if constexpr (METHOD == vqd::METHOD_ASB) vqd::asb_update(F, bi, a_k, a.dt, a.a0, in.c0, s, y);
+                            else vqd::bsb_update(F, bi, a_k, a.dt, a.a0, in.c0, s, y);
                             if (row_ok) {
                                 const int r = c * 16 + j;
                                 const int64_t p = (int64_t)r * n + row;
@@ -284,7 +287,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                                 in.Y[p] = y;
                                 *reinterpret_cast<__nv_bfloat16*>(sop_n + (size_t)(row >> 6) * R * TILE_KB +
                                                                   swz(r, row & 63)) =
-                                    __float2bfloat16_rn(vqd::field_operand(a.method, s));
+                                    __float2bfloat16_rn(METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
                             }
                         }
                     }
@@ -415,19 +418,18 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
     a.seed = seed;
     a.a_table = ctxs[0]->a_table.as<float>();
     a.err = d_err;
-    a.method = p.method;
     a.alpha = p.alpha;
     cudaEvent_t e0, e1;
     VQ_CUDA(cudaEventCreate(&e0));
     VQ_CUDA(cudaEventCreate(&e1));
     VQ_CUDA(cudaEventRecord(e0, st));
-    if (stages == 4) {
-        VQ_CUDA(cudaFuncSetAttribute(k_batch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<4>(R)));
-        k_batch<4><<<ctas, 192, batch_smem<4>(R), st>>>(a);
-    } else {
-        VQ_CUDA(cudaFuncSetAttribute(k_batch<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem<6>(R)));
-        k_batch<6><<<ctas, 192, batch_smem<6>(R), st>>>(a);
-    }
+    void (*fn)(const BatchArgs);
+    const int m = p.method;
+    if (stages == 4) fn = m == VELOXQ_METHOD_PA ? k_batch<4, vqd::METHOD_PA> : m == VELOXQ_METHOD_ASB ? k_batch<4, vqd::METHOD_ASB> : k_batch<4, vqd::METHOD_BSB>;
+    else fn = m == VELOXQ_METHOD_PA ? k_batch<6, vqd::METHOD_PA> : m == VELOXQ_METHOD_ASB ? k_batch<6, vqd::METHOD_ASB> : k_batch<6, vqd::METHOD_BSB>;
+    const size_t smem = stages == 4 ? batch_smem<4>(R) : batch_smem<6>(R);
+    VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    fn<<<ctas, 192, smem, st>>>(a);
     VQ_LAUNCH_CHECK("batch kernel");
     VQ_CUDA(cudaEventRecord(e1, st));
     // exact final-readout energies and the best replica of every instance

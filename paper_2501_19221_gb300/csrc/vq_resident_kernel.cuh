@@ -243,70 +243,110 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     for (int k = a.k_begin; k < a.k_end; ++k) {
         const float a_k = __ldg(a.a_table + k);
         const bool last = (k == a.k_end - 1);
+        // field of row i into acc (slot order = CSR order)
+        auto row_field = [&](int i, float (&acc)[RC]) {
 #pragma unroll
-        for (int q = 0; q < RPT; ++q) {
+            for (int r = 0; r < RC; ++r) acc[r] = 0.0f;
+            if constexpr (ELL) {
+                // two slots per iteration: both neighbours' loads are in flight together
+                const uint32_t* e = packs + i;
+                for (int p = 0; p < a.ell_d; p += 2, e += 2 * n) {
+                    const uint32_t e0 = e[0], e1 = e[n];
+                    float s0[RC], s1[RC];
+                    ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
+                    ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
+                    if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); }
+                    acc_fma<RC>(acc, ent_w(e0), s0);
+                    acc_fma<RC>(acc, ent_w(e1), s1);
+                }
+            } else {
+                int p0, p1;
+                if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
+                else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
+                for (int p = p0; p < p1; ++p) {
+                    float w;
+                    float sj[RC];
+                    if constexpr (CSR_SMEM && PACKED) {
+                        const uint32_t e = packs[p];
+                        w = ent_w(e);
+                        ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
+                    } else {
+                        int j;
+                        if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
+                        else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
+                        ld_row<RC>(sc, j, sj);
+                    }
+                    if constexpr (SIGN) sign_row<RC>(sj);
+                    acc_fma<RC>(acc, w, sj);
+                }
+            }
+        };
+        // fields of rows i and i + T together (ELL): four neighbours' loads in flight
+        auto pair_field = [&](int i, float (&acc0)[RC], float (&acc1)[RC]) {
+#pragma unroll
+            for (int r = 0; r < RC; ++r) { acc0[r] = 0.0f; acc1[r] = 0.0f; }
+            const uint32_t* e = packs + i;
+            const uint32_t* f = packs + i + T;
+            for (int p = 0; p < a.ell_d; p += 2, e += 2 * n, f += 2 * n) {
+                const uint32_t e0 = e[0], e1 = e[n], f0 = f[0], f1 = f[n];
+                float s0[RC], s1[RC], t0[RC], t1[RC];
+                ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
+                ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
+                ld_row_at<RC>(sc, (int)(f0 & 0xFFFFu), t0);
+                ld_row_at<RC>(sc, (int)(f1 & 0xFFFFu), t1);
+                if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); sign_row<RC>(t0); sign_row<RC>(t1); }
+                acc_fma<RC>(acc0, ent_w(e0), s0);
+                acc_fma<RC>(acc0, ent_w(e1), s1);
+                acc_fma<RC>(acc1, ent_w(f0), t0);
+                acc_fma<RC>(acc1, ent_w(f1), t1);
+            }
+        };
+        // update of row i (the q-th of this thread) from its field, into the next buffer
+        auto finish = [&](int q, int i, const float (&acc)[RC]) {
+            float s[RC];
+            ld_row<RC>(sc, i, s);
+            const float b = bsh[i];
+            if constexpr (METHOD == vqd::METHOD_PA) {
+                const float lam = vqd::pa_lambda(a_k, a.a0);
+#pragma unroll
+                for (int r = 0; r < RC; ++r) vqd::pa_update(acc[r], b, lam, a.dt, a.alpha, a.c0, s[r], y[q][r]);
+            } else if constexpr (METHOD == vqd::METHOD_ASB) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r) vqd::asb_update(acc[r], b, a_k, a.dt, a.a0, a.c0, s[r], y[q][r]);
+            } else if constexpr (RC >= 2) {
+#pragma unroll
+                for (int r = 0; r < RC; r += 2)
+                    vqd::bsb_update2(acc[r], acc[r + 1], b, a_k, a.dt, a.a0, a.c0, s[r], s[r + 1], y[q][r],
+                                     y[q][r + 1]);
+            } else {
+                vqd::bsb_update(acc[0], b, a_k, a.dt, a.a0, a.c0, s[0], y[q][0]);
+            }
+            st_row<RC>(sn, i, s);
+            if (last && a.F_out) {
+#pragma unroll
+                for (int r = 0; r < RC; ++r)
+                    if (r0 + r < a.R) a.F_out[(int64_t)(r0 + r) * n + i] = acc[r];
+            }
+        };
+        constexpr bool PAIRS = ELL && RPT >= 2;
+#pragma unroll
+        for (int q = 0; q < RPT; q += PAIRS ? 2 : 1) {
             const int i = tid + q * T;
-            if (i < n) {
+            if constexpr (PAIRS) {
+                if (i + T < n) {
+                    float acc0[RC], acc1[RC];
+                    pair_field(i, acc0, acc1);
+                    finish(q, i, acc0);
+                    finish(q + 1, i + T, acc1);
+                } else if (i < n) {
+                    float acc[RC];
+                    row_field(i, acc);
+                    finish(q, i, acc);
+                }
+            } else if (i < n) {
                 float acc[RC];
-#pragma unroll
-                for (int r = 0; r < RC; ++r) acc[r] = 0.0f;
-                if constexpr (ELL) {
-                    // two slots per iteration: both neighbours' loads are in flight together
-                    const uint32_t* e = packs + i;
-                    for (int p = 0; p < a.ell_d; p += 2, e += 2 * n) {
-                        const uint32_t e0 = e[0], e1 = e[n];
-                        float s0[RC], s1[RC];
-                        ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
-                        ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
-                        if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); }
-                        acc_fma<RC>(acc, ent_w(e0), s0);
-                        acc_fma<RC>(acc, ent_w(e1), s1);
-                    }
-                } else {
-                    int p0, p1;
-                    if constexpr (CSR_SMEM) { p0 = rps[i]; p1 = rps[i + 1]; }
-                    else { p0 = (int)__ldg(a.rowptr + i); p1 = (int)__ldg(a.rowptr + i + 1); }
-                    for (int p = p0; p < p1; ++p) {
-                        float w;
-                        float sj[RC];
-                        if constexpr (CSR_SMEM && PACKED) {
-                            const uint32_t e = packs[p];
-                            w = ent_w(e);
-                            ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
-                        } else {
-                            int j;
-                            if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
-                            else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
-                            ld_row<RC>(sc, j, sj);
-                        }
-                        if constexpr (SIGN) sign_row<RC>(sj);
-                        acc_fma<RC>(acc, w, sj);
-                    }
-                }
-                float s[RC];
-                ld_row<RC>(sc, i, s);
-                const float b = bsh[i];
-                if constexpr (METHOD == vqd::METHOD_PA) {
-                    const float lam = vqd::pa_lambda(a_k, a.a0);
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) vqd::pa_update(acc[r], b, lam, a.dt, a.alpha, a.c0, s[r], y[q][r]);
-                } else if constexpr (METHOD == vqd::METHOD_ASB) {
-#pragma unroll
-                    for (int r = 0; r < RC; ++r) vqd::asb_update(acc[r], b, a_k, a.dt, a.a0, a.c0, s[r], y[q][r]);
-                } else if constexpr (RC >= 2) {
-#pragma unroll
-                    for (int r = 0; r < RC; r += 2)
-                        vqd::bsb_update2(acc[r], acc[r + 1], b, a_k, a.dt, a.a0, a.c0, s[r], s[r + 1], y[q][r],
-                                         y[q][r + 1]);
-                } else {
-                    vqd::bsb_update(acc[0], b, a_k, a.dt, a.a0, a.c0, s[0], y[q][0]);
-                }
-                st_row<RC>(sn, i, s);
-                if (last && a.F_out) {
-#pragma unroll
-                    for (int r = 0; r < RC; ++r)
-                        if (r0 + r < a.R) a.F_out[(int64_t)(r0 + r) * n + i] = acc[r];
-                }
+                row_field(i, acc);
+                finish(q, i, acc);
             }
         }
         __syncthreads();
