@@ -76,6 +76,13 @@ def workload(name: str) -> dict:
                 "readout_every": 0, "dt": 0.5, "knots": [0.0, 0.5, 1.0],
                 "desc": "gradient of the mean relaxed energy w.r.t. dt, kappa and 3 schedule knots, periodic "
                         "3-D +-J lattice L=100, int8 CSR, 400 unrolled steps, checkpoint every 20"}
+    if name == "hubo_chain_1e7":
+        inst = I.hubo_chain_3body(10 ** 7, seed=0)
+        n3 = inst.triples[0].shape[0]
+        return {"name": name, "kind": "hubo", "hubo": inst, "n": inst.n + n3, "R": 8, "K": 200,
+                "readout_every": 50,
+                "desc": "3-body +-Gaussian spin-glass chain (Sec. HUBO eq. nn), N = 1e7, reduced to second order "
+                        "by eq. reduction (one auxiliary spin per cubic term: n = 2e7 - 2), float CSR"}
     if name == "lattice_l464":
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
@@ -111,8 +118,20 @@ def batch_instances(w):
     return w["inst"]
 
 
+def reduce_hubo(B, w):
+    """The library's second-order form of a third-order workload, kept in w."""
+    if "sp" not in w:
+        inst = w["hubo"]
+        red = B.veloxq_hubo3_reduce(inst.n, inst.h, inst.pairs, inst.triples)
+        w["sp"] = I.SparseCoupling(red["n"], red["rowptr"], red["col"], red["val"], red["lin"])
+        w["hubo_offset"] = red["offset"]
+    return w["sp"]
+
+
 def create(B, w, stream=None):
-    if w["kind"] in ("ising_csr", "grad"):
+    if w["kind"] == "hubo":
+        reduce_hubo(B, w)
+    if w["kind"] in ("ising_csr", "grad", "hubo"):
         sp = w["sp"]
         return B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
     if w["kind"] == "batch":
@@ -121,7 +140,7 @@ def create(B, w, stream=None):
 
 
 def input_arrays(w) -> list:
-    if w["kind"] in ("ising_csr", "grad"):
+    if w["kind"] in ("ising_csr", "grad", "hubo"):
         sp = w["sp"]
         return [sp.rowptr, sp.col, sp.val, sp.lin]
     if w["kind"] == "batch":
@@ -131,6 +150,11 @@ def input_arrays(w) -> list:
 
 def oracle_problem(w):
     import oracle as O
+    if w["kind"] == "hubo":
+        inst = w["hubo"]
+        N, (qi, qj, qv), lin, _ = O.hubo3_reduce(inst.n, inst.h, inst.pairs, inst.triples)
+        p, _ = O.ising_pairs_to_qubo(N, qi, qj, qv, lin)
+        return p
     if w["kind"] in ("ising_csr", "grad"):
         sp = w["sp"]
         p, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
@@ -271,7 +295,10 @@ class Runner:
             out = self.B.veloxq_solve_batch(self.ctxs, self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)
             self.last_batch_E = out["E"]
             return float(np.min(out["E"]))
-        return self.B.veloxq_solve(self.ctxs[0], self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)["E"]
+        out = self.B.veloxq_solve(self.ctxs[0], self.w["R"], self.w["K"], self.sched, seed=seed, want_x=want_x)
+        if want_x:
+            self.last_x = out["x"]
+        return out["E"]
 
     def timing(self):
         return self.B.veloxq_last_timing(self.ctxs[0])
@@ -479,6 +506,7 @@ def run_ours(args, rank, world, local_rank):
     import __graft_entry__ as g
     g.build()
     from paper_2501_19221_gb300 import binding as B
+    from paper_2501_19221_gb300 import replicas as RP
 
     torch.cuda.set_device(local_rank)
     dist = None
@@ -493,7 +521,7 @@ def run_ours(args, rank, world, local_rank):
     run = Runner(B, w, stream, method)
     n = run.n_total
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
-    seed0 = 1000 * rank
+    seed0 = RP.rank_seed(0, rank)
     with torch.cuda.stream(stream):
         for i in range(args.warmup):
             run.solve(seed0 + i)
@@ -523,17 +551,18 @@ def run_ours(args, rank, world, local_rank):
         clk = clocks.stop(0) if rank == 0 else None
     step_ms = [a.elapsed_time(b) for a, b in ev]
     total_ms = sum(step_ms)
-    tmax = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-    if dist is not None:
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-    total_ms = float(tmax.item())
+    total_ms = RP.max_over_ranks(total_ms, dist, device="cuda")
+    best_ranks = None
+    if not run.batch and not run.grad:
+        E_all, _, r_all = RP.best_over_ranks(results[-1], run.last_x, dist, device="cuda")
+        best_ranks = {"E": E_all, "rank": r_all}
     value = world * n * R * K * args.steps / (total_ms / 1e3)
 
     # ---- end to end through the public API from pinned host buffers ----
     e2e_iters = max(1, min(args.steps, 3 if run.batch else 5))
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in input_arrays(w)]
     h2d = int(sum(a.nbytes for a in pinned))
-    if w["kind"] in ("ising_csr", "grad"):
+    if w["kind"] in ("ising_csr", "grad", "hubo"):
         pw = dict(w)
         pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
     elif w["kind"] == "batch":
@@ -576,12 +605,14 @@ def run_ours(args, rank, world, local_rank):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not run.batch:
         # calibrate on a short run, then time about 12 s of oracle work
-        R_s = min(R, 4 if run.grad else 64)
-        K_c = min(K, 4 if run.grad else 20)
-        rate0, _ = oracle_sample_rate(w, min(R, 4), K_c)
+        big = n > 2_000_000           # one replica, a few steps: the sample stays around 10 s
+        R_s = min(R, 1 if big else 4 if run.grad else 64)
+        K_c = min(K, 1 if big else 4 if run.grad else 20)
+        rate0, _ = oracle_sample_rate(w, min(R, R_s, 4), K_c)
         K_s2 = int(min(K, max(K_c, 12.0 * rate0 / (n * R_s))))
         rate1, dt1 = oracle_sample_rate(w, R_s, K_s2)
-        procs = os.cpu_count() or 1
+        # each process holds its own copy of the instance: fewer of them for the largest ones
+        procs = min(os.cpu_count() or 1, 4 if big else 64)
         rate, dt, used = oracle_parallel_rate(w, R_s, K_s2, procs)
         what = "reverse-mode gradient over" if run.grad else "solve of"
         cpu = {"value": rate, "unit": "spin-updates/s", "cores": used, "kind": "oracle",
@@ -620,6 +651,10 @@ def run_ours(args, rank, world, local_rank):
         elif not run.batch:
             off = run.ctxs[0].info.ising_offset
             line["quality"]["best_ising_energy_last_step"] = 2 * results[-1] + off
+            if w["kind"] == "hubo":
+                # the third-order cost of the original spins is at most the reduced cost
+                line["quality"]["hubo_energy_upper_bound"] = 2 * results[-1] + off + w["hubo_offset"]
+            line["quality"]["best_over_ranks"] = best_ranks
         else:
             gaps = [(2 * E + c.info.ising_offset - e0) / abs(e0)
                     for E, c, e0 in zip(run.last_batch_E, run.ctxs, w["E0"])]

@@ -173,6 +173,27 @@ int veloxq_create_ising_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, cons
 int veloxq_create_ising_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, const int32_t* col,
                             veloxq_vtype vt, const void* J, const double* h, void* stream);
 
+/* Third-order Ising cost function (HUBO, Sec. "HUBO" eqs. nn and mw3s)
+ *   H(s) = sum_i h_i s_i + sum_q J_q s_pi s_pj + sum_q K_q s_ti s_tj s_tk
+ * reduced to second order by the gadget of eq. reduction: one auxiliary
+ * spin a_q (index n + q) per cubic term, which adds
+ *   |K| [3 + sgn(K)(s_i + s_j + s_k + 2a) + 2a(s_i + s_j + s_k) + s_i s_j + s_j s_k + s_i s_k],
+ * so that min over the auxiliary spins of the result equals H(s). Host only
+ * (no device use). Inputs (host): h (n values, or NULL for 0), n2 pairs
+ * (pi, pj, J2; i != j, repeated pairs add), n3 triples (ti, tj, tk, K3;
+ * distinct indices). Outputs (host, caller-allocated): *n_out = n + n3;
+ * rowptr (n + n3 + 1), col and val (capacity 2 (n2 + 6 n3)): the reduced
+ * Ising couplings in the CSR form veloxq_create_ising_csr takes (each pair
+ * at both positions with the same summed value, columns sorted), *nnz_out
+ * the stored entries; lin (n + n3) the reduced fields; *offset the constant,
+ * so H_reduced(s, a) = sum_{i<j} J s s + sum lin s + *offset.
+ * Errors: EINVAL (bad sizes, indices out of range or repeated within a term,
+ * non-finite values, NULL arrays, n + n3 >= 2^31). */
+int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
+                        const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj, const int64_t* tk,
+                        const double* K3, int64_t* n_out, int64_t* nnz_out, int64_t* rowptr, int32_t* col,
+                        double* val, double* lin, double* offset);
+
 /* Release every device and host resource of ctx (NULL is a no-op). */
 void veloxq_destroy(veloxq_ctx* ctx);
 

@@ -75,6 +75,8 @@ def _load():
             "oracle_bsb_loss": (ctypes.c_int, [i64, i64, P, P, P, P, i32, i32, f64, f64, f64,
                                                i32, P, P, P, P]),
             "oracle_ising_pairs_to_qubo": (None, [i64, i64, P, P, P, P, P, P, P, P]),
+            "oracle_hubo3_energy": (f64, [i64, P, i64, P, P, P, i64, P, P, P, P, P]),
+            "oracle_hubo3_reduce": (None, [i64, P, i64, P, P, P, i64, P, P, P, P, P, P, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -212,6 +214,45 @@ def ising_energy(J: np.ndarray, h: np.ndarray, s: np.ndarray) -> float:
     h = np.ascontiguousarray(h, dtype=np.float64)
     s = np.ascontiguousarray(s, dtype=np.int8)
     return lib.oracle_ising_energy(J.shape[0], _p(J), _p(h), _p(s))
+
+
+def hubo3_energy(n: int, h, pairs, triples, S: np.ndarray) -> np.ndarray:
+    """H(s) = sum h s + sum J s s + sum K s s s per row of S (spins +-1), the
+    third-order cost function of Sec. "HUBO" (eqs. nn, mw3s). pairs = (pi, pj,
+    J), triples = (ti, tj, tk, K); either may be None."""
+    lib = _load()
+    z_i, z_f = np.zeros(0, dtype=np.int64), np.zeros(0)
+    pi, pj, J2 = (z_i, z_i, z_f) if pairs is None else pairs
+    ti, tj, tk, K3 = (z_i, z_i, z_i, z_f) if triples is None else triples
+    pi, pj, ti, tj, tk = (np.ascontiguousarray(a, dtype=np.int64) for a in (pi, pj, ti, tj, tk))
+    J2 = np.ascontiguousarray(J2, dtype=np.float64)
+    K3 = np.ascontiguousarray(K3, dtype=np.float64)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    S = np.ascontiguousarray(np.atleast_2d(S), dtype=np.int8)
+    return np.array([lib.oracle_hubo3_energy(n, _p(hh), pi.shape[0], _p(pi), _p(pj), _p(J2), ti.shape[0], _p(ti),
+                                             _p(tj), _p(tk), _p(K3), _p(np.ascontiguousarray(s))) for s in S])
+
+
+def hubo3_reduce(n: int, h, pairs, triples):
+    """Second-order form of a third-order cost function (Sec. "HUBO", eq.
+    reduction): one auxiliary spin per cubic term. Returns (n + n3, (pi, pj,
+    J) unmerged pairs, lin, offset)."""
+    lib = _load()
+    z_i, z_f = np.zeros(0, dtype=np.int64), np.zeros(0)
+    pi, pj, J2 = (z_i, z_i, z_f) if pairs is None else pairs
+    ti, tj, tk, K3 = (z_i, z_i, z_i, z_f) if triples is None else triples
+    pi, pj, ti, tj, tk = (np.ascontiguousarray(a, dtype=np.int64) for a in (pi, pj, ti, tj, tk))
+    J2 = np.ascontiguousarray(J2, dtype=np.float64)
+    K3 = np.ascontiguousarray(K3, dtype=np.float64)
+    hh = None if h is None else np.ascontiguousarray(h, dtype=np.float64)
+    n2, n3 = pi.shape[0], ti.shape[0]
+    m = n2 + 6 * n3
+    qi, qj, qv = np.zeros(m, dtype=np.int64), np.zeros(m, dtype=np.int64), np.zeros(m)
+    lin = np.zeros(n + n3)
+    off = ctypes.c_double()
+    lib.oracle_hubo3_reduce(n, _p(hh), n2, _p(pi), _p(pj), _p(J2), n3, _p(ti), _p(tj), _p(tk), _p(K3),
+                            _p(qi), _p(qj), _p(qv), _p(lin), ctypes.byref(off))
+    return n + n3, (qi, qj, qv), lin, off.value
 
 
 def ising_to_qubo(J: np.ndarray, h: np.ndarray):

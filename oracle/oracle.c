@@ -188,6 +188,53 @@ double oracle_ising_energy(int64_t n, const double* J, const double* h, const in
     return H;
 }
 
+/* Third-order Ising cost function (Sec. "HUBO", eqs. nn and mw3s):
+ *   H(s) = sum_i h_i s_i + sum_q J_q s_pi s_pj + sum_q K_q s_ti s_tj s_tk
+ * for one spin vector s in {-1, +1}^n (h may be NULL). */
+double oracle_hubo3_energy(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
+                           const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj, const int64_t* tk,
+                           const double* K3, const int8_t* s)
+{
+    double H = 0.0;
+    if (h)
+        for (int64_t i = 0; i < n; ++i) H += h[i] * (double)s[i];
+    for (int64_t q = 0; q < n2; ++q) H += J2[q] * (double)s[pi[q]] * (double)s[pj[q]];
+    for (int64_t q = 0; q < n3; ++q) H += K3[q] * (double)s[ti[q]] * (double)s[tj[q]] * (double)s[tk[q]];
+    return H;
+}
+
+/* Reduction to second order (Sec. "HUBO", eq. reduction): each cubic term
+ * K s_i s_j s_k gets an auxiliary spin a = s_{n+q} and is replaced by
+ *   |K| [3 + sgn(K)(s_i + s_j + s_k + 2a) + 2a(s_i + s_j + s_k)
+ *        + s_i s_j + s_j s_k + s_i s_k].
+ * Output: the pair list (input pairs first, then six per cubic term, not
+ * merged; capacity n2 + 6 n3), the fields lin (n + n3; h may be NULL) and
+ * the constant. */
+void oracle_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
+                         const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj, const int64_t* tk,
+                         const double* K3, int64_t* qi, int64_t* qj, double* qv, double* lin, double* offset)
+{
+    int64_t m = 0;
+    for (int64_t q = 0; q < n2; ++q) { qi[m] = pi[q]; qj[m] = pj[q]; qv[m] = J2[q]; ++m; }
+    for (int64_t i = 0; i < n + n3; ++i) lin[i] = (h && i < n) ? h[i] : 0.0;
+    double off = 0.0;
+    for (int64_t q = 0; q < n3; ++q) {
+        int64_t t[3] = {ti[q], tj[q], tk[q]};
+        int64_t a = n + q;
+        double K = K3[q], absK = fabs(K), sg = K > 0.0 ? 1.0 : (K < 0.0 ? -1.0 : 0.0);
+        off += 3.0 * absK;
+        for (int u = 0; u < 3; ++u) {
+            lin[t[u]] += sg * absK;                             /* sgn(K)|K| s_u */
+            qi[m] = a; qj[m] = t[u]; qv[m] = 2.0 * absK; ++m;   /* 2|K| a s_u */
+        }
+        lin[a] += 2.0 * sg * absK;                              /* 2 sgn(K)|K| a */
+        qi[m] = t[0]; qj[m] = t[1]; qv[m] = absK; ++m;
+        qi[m] = t[1]; qj[m] = t[2]; qv[m] = absK; ++m;
+        qi[m] = t[0]; qj[m] = t[2]; qv[m] = absK; ++m;
+    }
+    *offset = off;
+}
+
 /* ------------------------------------------------------------------------ */
 /* App. A conversions (dense)                                                */
 /* ------------------------------------------------------------------------ */

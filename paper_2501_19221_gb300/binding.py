@@ -33,7 +33,7 @@ EXPORTED = [
     "veloxq_create_ising_csr", "veloxq_destroy", "veloxq_last_error", "veloxq_get_info", "veloxq_set_stream",
     "veloxq_solve", "veloxq_solve_batch", "veloxq_energy", "veloxq_energy_dev", "veloxq_init_state_dev",
     "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad", "veloxq_last_timing",
-    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc",
+    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc", "veloxq_hubo3_reduce",
 ]
 
 
@@ -91,6 +91,7 @@ def _load():
         "veloxq_last_timing": (I, [P, ctypes.POINTER(Timing)]),
         "veloxq_batch_state_dev": (I, [P, I32, P, P]),
         "veloxq_energy_dev_noalloc": (I, [P, I64, P, P, P]),
+        "veloxq_hubo3_reduce": (I, [I64, P, I64, P, P, P, I64, P, P, P, P, P, P, P, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -230,6 +231,33 @@ def veloxq_create_ising_csr(n: int, rowptr, col, J, h=None, stream=None) -> Cont
     out = ctypes.c_void_p()
     _check(_lib.veloxq_create_ising_csr(ctypes.byref(out), n, _ptr(rp), _ptr(cl), _vt(jv), _ptr(jv), _ptr(hh), stream))
     return Context(out)
+
+
+def veloxq_hubo3_reduce(n: int, h=None, pairs=None, triples=None) -> dict:
+    """Third-order Ising cost function -> second order (one auxiliary spin
+    per cubic term). pairs = (pi, pj, J), triples = (ti, tj, tk, K). Returns
+    n (with the auxiliary spins), rowptr, col, val, lin and offset of the
+    reduced Ising instance, ready for veloxq_create_ising_csr."""
+    empty_i, empty_f = np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.float64)
+    pi, pj, J2 = (empty_i, empty_i, empty_f) if pairs is None else pairs
+    ti, tj, tk, K3 = (empty_i, empty_i, empty_i, empty_f) if triples is None else triples
+    pi, pj, ti, tj, tk = (_host(a, np.int64) for a in (pi, pj, ti, tj, tk))
+    J2, K3 = _host(J2, np.float64), _host(K3, np.float64)
+    hh = None if h is None else _host(h, np.float64)
+    n2, n3 = pi.shape[0], ti.shape[0]
+    N = n + n3
+    cap = max(1, 2 * (n2 + 6 * n3))
+    rowptr = np.zeros(N + 1, dtype=np.int64)
+    col = np.zeros(cap, dtype=np.int32)
+    val = np.zeros(cap, dtype=np.float64)
+    lin = np.zeros(N, dtype=np.float64)
+    n_out, nnz_out, off = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(_lib.veloxq_hubo3_reduce(n, _ptr(hh), n2, _ptr(pi), _ptr(pj), _ptr(J2), n3, _ptr(ti), _ptr(tj), _ptr(tk),
+                                    _ptr(K3), ctypes.byref(n_out), ctypes.byref(nnz_out), _ptr(rowptr), _ptr(col),
+                                    _ptr(val), _ptr(lin), ctypes.byref(off)))
+    m = nnz_out.value
+    return {"n": n_out.value, "rowptr": rowptr, "col": col[:m].copy(), "val": val[:m].copy(), "lin": lin,
+            "offset": off.value}
 
 
 def veloxq_destroy(ctx: Context):

@@ -272,3 +272,51 @@ def random_binary(B: int, n: int, seed: int = 0, p: float = 0.5) -> np.ndarray:
     """A uint8 batch [B][n] of binary vectors with P(x_i = 1) = p."""
     rng = np.random.default_rng(seed)
     return (rng.random((B, n)) < p).astype(np.uint8)
+
+
+# ---------------------------------------------------------------- third-order (HUBO) instances
+class Hubo3:
+    """A third-order Ising cost function
+    H(s) = const + sum h s + sum J s_pi s_pj + sum K s_ti s_tj s_tk."""
+
+    def __init__(self, n, h, pairs, triples, const=0.0):
+        self.n = int(n)
+        self.h = np.asarray(h, dtype=np.float64)
+        self.pairs = tuple(pairs)        # (pi, pj, J)
+        self.triples = tuple(triples)    # (ti, tj, tk, K)
+        self.const = float(const)
+
+
+def hubo_chain_3body(N: int, seed: int = 0) -> Hubo3:
+    """One-dimensional spin glass with nearest-neighbour two- and three-body
+    terms (Sec. "HUBO", eq. nn): h_i, J_i, K_i ~ N(0, 1)."""
+    rng = np.random.default_rng(seed)
+    h = rng.standard_normal(N)
+    J = rng.standard_normal(max(N - 1, 0))
+    K = rng.standard_normal(max(N - 2, 0))
+    i1 = np.arange(max(N - 1, 0), dtype=np.int64)
+    i2 = np.arange(max(N - 2, 0), dtype=np.int64)
+    return Hubo3(N, h, (i1, i1 + 1, J), (i2, i2 + 1, i2 + 2, K))
+
+
+def max3sat_weighted(N: int, seed: int = 0) -> Hubo3:
+    """Weighted MAX 3-SAT on consecutive triples (Sec. "HUBO", eq. mw3s):
+    clause i weighs w_i ~ U[0, 1] and contributes (w_i/8) prod_{m=0..2}
+    (1 + l_m s_{i+m}), l_m = (-1)^{c_m}, c_m ~ {0, 1}; the product is expanded
+    into its constant, field, pair and triple terms."""
+    rng = np.random.default_rng(seed)
+    M = max(N - 2, 0)
+    w = rng.uniform(0.0, 1.0, size=M)
+    c = rng.integers(0, 2, size=(M, 3))
+    l = 1.0 - 2.0 * c                     # (-1)^c
+    i = np.arange(M, dtype=np.int64)
+    idx = [i, i + 1, i + 2]
+    e = w / 8.0
+    h = np.zeros(N)
+    for m in range(3):
+        np.add.at(h, idx[m], e * l[:, m])
+    pi = np.concatenate([idx[0], idx[0], idx[1]])
+    pj = np.concatenate([idx[1], idx[2], idx[2]])
+    pv = np.concatenate([e * l[:, 0] * l[:, 1], e * l[:, 0] * l[:, 2], e * l[:, 1] * l[:, 2]])
+    K = e * l[:, 0] * l[:, 1] * l[:, 2]
+    return Hubo3(N, h, (pi, pj, pv), (idx[0], idx[1], idx[2], K), const=float(e.sum()))
