@@ -184,33 +184,37 @@ def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0, barrier=None) -> tu
     return p.n * R_s * K_s / dt, dt
 
 
-_BARRIER = None
-
-
-def _oracle_init(barrier):
-    global _BARRIER
-    _BARRIER = barrier
-
-
-def _oracle_worker(job):
+def _oracle_proc(job, barrier, results):
     name, method, R_s, K_s, seed = job
-    return oracle_sample_rate(dict(workload(name), method=method), R_s, K_s, seed, _BARRIER)
+    try:
+        results.put((seed, oracle_sample_rate(dict(workload(name), method=method), R_s, K_s, seed, barrier)))
+    except Exception as e:                                   # reported by the parent
+        results.put((seed, repr(e)))
 
 
 def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
     """The same oracle sample run as `procs` independent processes at once
-    (replica-parallel over the host cores, each process its own seed, the
-    timed runs released together): total spin-updates / the longest run."""
+    (replica-parallel over the host cores, one job per process, each with
+    its own seed, the timed runs released together by a barrier): total
+    spin-updates / the longest run."""
     import multiprocessing as mp
     if procs <= 1:
         rate, dt = oracle_sample_rate(w, R_s, K_s)
         return rate, dt, 1
     ctx = mp.get_context("spawn")          # never fork a process that has touched the GPU
-    barrier = ctx.Barrier(procs)
-    with ctx.Pool(procs, initializer=_oracle_init, initargs=(barrier,)) as pool:
-        res = pool.map(_oracle_worker, [(w["name"], w.get("method", "bsb"), R_s, K_s, s) for s in range(procs)],
-                       chunksize=1)
-    wall = max(dt for _, dt in res)
+    barrier = ctx.Barrier(procs, timeout=600)
+    results = ctx.Queue()
+    ps = [ctx.Process(target=_oracle_proc, args=((w["name"], w.get("method", "bsb"), R_s, K_s, s), barrier, results))
+          for s in range(procs)]
+    for p in ps:
+        p.start()
+    got = [results.get(timeout=1800) for _ in ps]
+    for p in ps:
+        p.join()
+    bad = [r for _, r in got if not isinstance(r, tuple)]
+    if bad:
+        raise RuntimeError(f"oracle sample failed: {bad[0]}")
+    wall = max(r[1] for _, r in got)
     return w["n"] * R_s * K_s * procs / wall, wall, procs
 
 
