@@ -162,14 +162,19 @@ def oracle_problem(w):
     return O.problem_from_dense(w["Q"], w["c"])
 
 
-def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0, barrier=None) -> tuple:
-    """Spin-updates/s of the FP64 oracle (single thread) on R_s replicas x the
-    first K_s steps of the workload's schedule. With a barrier, the timed run
-    starts when every process of the group has finished its set-up."""
+def oracle_setup(w):
+    """The oracle's problem and c0 = 2/rho for a workload (set-up, untimed)."""
     import oracle as O
     p = oracle_problem(w)
     rho = O.spectral_radius(p) if p.n <= 6000 else 6.0
-    c0 = 2.0 / rho
+    return p, 2.0 / rho
+
+
+def oracle_timed_run(w, p, c0, R_s: int, K_s: int, seed: int = 0, barrier=None) -> float:
+    """Seconds of the FP64 oracle (single thread) on R_s replicas x the first
+    K_s steps of the workload's schedule. With a barrier, the timed run starts
+    when every process of the group is ready."""
+    import oracle as O
     S0, Y0 = O.init_state(p.n, R_s, seed, 0.1)
     K = w["K"]
     knots = [0.0, (K_s - 1) / (K - 1) if K > 1 else 0.0]
@@ -180,42 +185,92 @@ def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0, barrier=None) -> tu
         O.bsb_grad(p, R_s, K_s, w["dt"], 1.0, c0, knots, S0, Y0)
     else:
         O.bsb_run(p, R_s, K_s, 0.5, 1.0, c0, knots, w["readout_every"], S0, Y0, method=w.get("method", "bsb"))
-    dt = time.perf_counter() - t0
+    return time.perf_counter() - t0
+
+
+def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0) -> tuple:
+    """(spin-updates/s, seconds) of one single-thread oracle sample."""
+    p, c0 = oracle_setup(w)
+    dt = oracle_timed_run(w, p, c0, R_s, K_s, seed)
     return p.n * R_s * K_s / dt, dt
 
 
-def _oracle_proc(job, barrier, results):
-    name, method, R_s, K_s, seed = job
+def _crew_member(name, method, c0, seed, barrier, jobs, results):
+    """A worker process of OracleCrew: builds the problem once, then runs the
+    rounds it is given, each released by the shared barrier."""
     try:
-        results.put((seed, oracle_sample_rate(dict(workload(name), method=method), R_s, K_s, seed, barrier)))
+        w = dict(workload(name), method=method)
+        p = oracle_problem(w)
+        while True:
+            job = jobs.get()
+            if job is None:
+                break
+            R_s, K_s = job
+            results.put((seed, oracle_timed_run(w, p, c0, R_s, K_s, seed, barrier)))
     except Exception as e:                                   # reported by the parent
         results.put((seed, repr(e)))
 
 
+class OracleCrew:
+    """`procs` persistent oracle processes, one per host core, each with its
+    own seed and its own copy of the problem (built once): a round runs the
+    same sample in all of them at once, released together by a barrier
+    (replica-parallel), and reports total spin-updates / the longest run.
+    Processes are spawned, never forked from a process that touched the GPU;
+    BLAS threads are pinned to one per process."""
+
+    def __init__(self, w, procs: int):
+        import multiprocessing as mp
+        self.w, self.procs = w, procs
+        _, self.c0 = oracle_setup(w)                      # rho once, in the parent
+        ctx = mp.get_context("spawn")
+        self.barrier = ctx.Barrier(procs, timeout=600)
+        self.results = ctx.Queue()
+        self.jobs = [ctx.Queue() for _ in range(procs)]
+        saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+        for k in saved:
+            os.environ[k] = "1"
+        try:
+            self.ps = [ctx.Process(target=_crew_member, args=(w["name"], w.get("method", "bsb"), self.c0, s,
+                                                               self.barrier, self.jobs[s], self.results))
+                       for s in range(procs)]
+            for p in self.ps:
+                p.start()
+        finally:
+            for k, v in saved.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
+
+    def run(self, R_s: int, K_s: int) -> tuple:
+        for q in self.jobs:
+            q.put((R_s, K_s))
+        got = [self.results.get(timeout=1800) for _ in self.ps]
+        bad = [r for _, r in got if not isinstance(r, float)]
+        if bad:
+            raise RuntimeError(f"oracle sample failed: {bad[0]}")
+        wall = max(r for _, r in got)
+        return self.w["n"] * R_s * K_s * self.procs / wall, wall
+
+    def close(self):
+        for q in self.jobs:
+            q.put(None)
+        for p in self.ps:
+            p.join(timeout=60)
+
+
 def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
-    """The same oracle sample run as `procs` independent processes at once
-    (replica-parallel over the host cores, one job per process, each with
-    its own seed, the timed runs released together by a barrier): total
-    spin-updates / the longest run."""
-    import multiprocessing as mp
+    """One replica-parallel round (see OracleCrew): (rate, seconds, processes)."""
     if procs <= 1:
         rate, dt = oracle_sample_rate(w, R_s, K_s)
         return rate, dt, 1
-    ctx = mp.get_context("spawn")          # never fork a process that has touched the GPU
-    barrier = ctx.Barrier(procs, timeout=600)
-    results = ctx.Queue()
-    ps = [ctx.Process(target=_oracle_proc, args=((w["name"], w.get("method", "bsb"), R_s, K_s, s), barrier, results))
-          for s in range(procs)]
-    for p in ps:
-        p.start()
-    got = [results.get(timeout=1800) for _ in ps]
-    for p in ps:
-        p.join()
-    bad = [r for _, r in got if not isinstance(r, tuple)]
-    if bad:
-        raise RuntimeError(f"oracle sample failed: {bad[0]}")
-    wall = max(r[1] for _, r in got)
-    return w["n"] * R_s * K_s * procs / wall, wall, procs
+    crew = OracleCrew(w, procs)
+    try:
+        rate, wall = crew.run(R_s, K_s)
+    finally:
+        crew.close()
+    return rate, wall, procs
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -286,9 +341,13 @@ class Runner:
         self.n_total = sum(c.info.n for c in self.ctxs)
         self.nnz_field = sum(c.info.nnz_field for c in self.ctxs)
         self.regular = False
+        self.int8_couplings = False
         if "sp" in w:
             deg = np.diff(np.asarray(w["sp"].rowptr))
             self.regular = bool(deg.size > 0 and np.all(deg == deg[0]))
+            v = np.asarray(w["sp"].val)
+            # integer Ising couplings J map to 2 Qs = J: kept as int8 when |J| <= 127
+            self.int8_couplings = bool(np.issubdtype(v.dtype, np.integer) and (v.size == 0 or np.abs(v).max() <= 127))
 
     def solve(self, seed, want_x=False):
         if self.grad:
@@ -360,9 +419,10 @@ def roofline(B, w, runner, path, main_ms, main_launches):
                 "frac": ach / fp32_peak, "traffic": None,
                 "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 (FMA) x max clock",
                 "algorithmic_flops_per_launch": flops, "ms_per_launch": per}
-    # state r/w + int8 couplings and columns, per step; the row pointers are
-    # read only when rows differ in length (rows of equal length start at i * degree)
-    hbm_bytes = 16 * n * R + 5 * runner.nnz_field + (0 if runner.regular else 8 * (n + 1))
+    # state r/w + couplings (int8 2Qs or float Qs) and int32 columns, per step; the row
+    # pointers are read only when rows differ in length (rows of equal length start at i * degree)
+    per_nnz = 5 if runner.int8_couplings else 8
+    hbm_bytes = 16 * n * R + per_nnz * runner.nnz_field + (0 if runner.regular else 8 * (n + 1))
     per = main_ms / max(1, main_launches)
     ach = hbm_bytes / (per / 1e3) / 1e9
     return {"kernel": "k_stream_step", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -418,7 +478,8 @@ def time_to_target(B, stream, seeds=8, n=8192, R=1024, K=200, method=0):
 def time_to_target_batch(B, stream, seeds=4, K=1000, R=64):
     """Time-to-target of the batched form (one persistent BF16 launch for the
     512 Wishart instances) against the plain FP32 form (each instance solved
-    in turn on the CUDA-core path). Per instance, the target is the median
+    in turn with the library's own path choice: the resident kernel up to
+    n = 512, the split-k SGEMM step above). Per instance, the target is the median
     over `seeds` of the FP32 form's best energy after K steps; a form's
     success is the fraction of (instance, seed) pairs at or below their
     target, and it reaches the targets at the smallest K' of a grid with
@@ -432,7 +493,7 @@ def time_to_target_batch(B, stream, seeds=4, K=1000, R=64):
 
     def run(prec, steps, seed):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sched = B.make_schedule(prec=prec, readout_every=0, path=3)
+        sched = B.make_schedule(prec=prec, readout_every=0)     # the library's own path choice
         e0.record(stream)
         E = B.veloxq_solve_batch(ctxs, R, steps, sched, seed=seed, want_x=False)["E"]
         e1.record(stream)
@@ -680,12 +741,17 @@ def run_reference(args, rank, world):
     rate0, _ = oracle_sample_rate(w, R_s, min(w["K"], 2))
     K_s = int(min(w["K"], 1000, max(1, 3.0 * rate0 / (w["n"] * R_s))))
     procs = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        oracle_sample_rate(w, R_s, min(K_s, 20))
-    times = []
-    for _ in range(args.steps):
-        _, dt, used = oracle_parallel_rate(w, R_s, K_s, procs)
-        times.append(dt)
+    crew = OracleCrew(w, procs)
+    try:
+        for _ in range(args.warmup):
+            crew.run(R_s, min(K_s, 20))
+        times = []
+        for _ in range(args.steps):
+            _, dt = crew.run(R_s, K_s)
+            times.append(dt)
+    finally:
+        crew.close()
+    used = procs
     total = sum(times)
     value = w["n"] * R_s * K_s * used * args.steps / total
     what = "reverse-mode gradient, " if w["kind"] == "grad" else ""

@@ -440,6 +440,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         TcRun tc;
         const bool use_tc = path == VELOXQ_PATH_DENSE && p.prec != VELOXQ_PREC_FP32;
         if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc));
+        if (path == VELOXQ_PATH_DENSE && !use_tc) VQ_TRY(dense_prepare(ctx, replicas));
         VQ_CUDA(cudaEventRecord(ex->t0, ctx->stream));
         VQ_TRY(launch_init_state(ctx, replicas, seed, p.sigma0, lay, ctx->s_a.as<float>(), ctx->y.as<float>()));
         if (use_tc) {

@@ -2,6 +2,8 @@
 // F = S Qoff as a register-tiled SGEMM (M = replicas, N = K = n; S replica-major
 // [R][n], Qoff symmetric row-major) with the ballistic-SB update fused into the
 // epilogue, and the exact readout energy in int64 fixed point.
+#include <algorithm>
+
 #include "vq_internal.cuh"
 
 namespace vq {
@@ -11,12 +13,16 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;   // 256 threads, 8x8 outputs each
 
 // C[r][i] = sum_j S[r][j] Qoff[j][i]. Tiles are zero-filled past the edges.
+// With gridDim.z = ksplit > 1 (small problems: too few output tiles to fill
+// the GPU) block z sums k-tiles [z per, (z+1) per) into part[z][r][i] and
+// k_dense_finish adds the splits in order and applies the update.
 template <bool FIELD_ONLY>
 __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const float* __restrict__ S_cur,
                                                     const float* __restrict__ Qoff, float* __restrict__ S_nxt,
                                                     float* __restrict__ Y, const float* __restrict__ bf,
                                                     const float* __restrict__ a_table, int k, float dt, float a0,
-                                                    float c0, float* __restrict__ F_out, int method, float alpha) {
+                                                    float c0, float* __restrict__ F_out, int method, float alpha,
+                                                    int ktile_per, float* __restrict__ part) {
     __shared__ __align__(16) float As[2][BK][BM];
     __shared__ __align__(16) float Bs[2][BK][BN];
     const int tid = threadIdx.x;
@@ -50,13 +56,16 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
     };
 
     const int ktiles = (int)div_up(n, BK);
+    const int kt0 = (int)blockIdx.z * ktile_per, kt1 = min(ktiles, kt0 + ktile_per);
     float ra[4], rb[4];
-    load_tiles(0, ra, rb);
-    store_tiles(0, ra, rb);
+    if (kt0 < kt1) {
+        load_tiles(kt0, ra, rb);
+        store_tiles(0, ra, rb);
+    }
     __syncthreads();
-    for (int kt = 0; kt < ktiles; ++kt) {
-        const int cur = kt & 1;
-        if (kt + 1 < ktiles) load_tiles(kt + 1, ra, rb);
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int cur = (kt - kt0) & 1;
+        if (kt + 1 < kt1) load_tiles(kt + 1, ra, rb);
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             float av[TM], bv[TN];
@@ -73,8 +82,22 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
-        if (kt + 1 < ktiles) store_tiles(cur ^ 1, ra, rb);
+        if (kt + 1 < kt1) store_tiles(cur ^ 1, ra, rb);
         __syncthreads();
+    }
+    if (gridDim.z > 1) {   // partial sums of this k-range; the update runs in k_dense_finish
+        float* P = part + (int64_t)blockIdx.z * R * n;
+#pragma unroll
+        for (int i = 0; i < TM; ++i) {
+            const int64_t r = m0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (r >= R) continue;
+#pragma unroll
+            for (int j = 0; j < TN; ++j) {
+                const int64_t c = n0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+                if (c < n) P[r * n + c] = acc[i][j];
+            }
+        }
+        return;
     }
     // ---- epilogue: field -> update (per output element) ----
     const float a_kv = FIELD_ONLY ? 0.0f : __ldg(a_table + k);
@@ -97,6 +120,29 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
                 Y[p] = yv;
             }
         }
+    }
+}
+
+// F = sum over the k splits (in order), then the update of the step.
+template <bool FIELD_ONLY>
+__global__ void __launch_bounds__(256) k_dense_finish(int32_t R, int32_t n, int ksplit, const float* __restrict__ part,
+                                                      const float* __restrict__ S_cur, float* __restrict__ S_nxt,
+                                                      float* __restrict__ Y, const float* __restrict__ bf,
+                                                      const float* __restrict__ a_table, int k, float dt, float a0,
+                                                      float c0, float* __restrict__ F_out, int method, float alpha) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t total = (int64_t)R * n;
+    if (p >= total) return;
+    float F = part[p];
+    for (int z = 1; z < ksplit; ++z) F = __fadd_rn(F, part[(int64_t)z * total + p]);
+    if (F_out) F_out[p] = F;
+    if constexpr (!FIELD_ONLY) {
+        const int64_t c = p % n;
+        const float a_kv = __ldg(a_table + k);
+        float s = S_cur[p], yv = Y[p];
+        vqd::step_update(method, F, __ldg(bf + c), a_kv, vqd::pa_lambda(a_kv, a0), dt, a0, c0, alpha, s, yv);
+        S_nxt[p] = s;
+        Y[p] = yv;
     }
 }
 
@@ -179,14 +225,44 @@ __global__ void __launch_bounds__(256) k_dense_energy(int64_t R, int32_t n, cons
     }
 }
 
+// k-splits of the FP32 dense step: enough CTAs to fill the GPU when the
+// output tiles alone cannot, with at least 16 k-tiles per split.
+void dense_split(int64_t n, int32_t R, int* ksplit, int* per) {
+    const int64_t ctas = div_up(n, BN) * div_up(R, BM);
+    const int ktiles = (int)div_up(n, BK);
+    int ks = 1;
+    if (ctas < 152) ks = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(2 * 152, ctas), ktiles / 16));
+    *per = (int)div_up(ktiles, ks);
+    *ksplit = (int)div_up(ktiles, *per);
+}
+
 template <bool FIELD_ONLY>
 int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table,
                       int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
     const int32_t n = (int32_t)ctx->n;
-    dim3 g((unsigned)div_up(n, BN), (unsigned)div_up(R, BM));
+    int ksplit, per;
+    dense_split(n, R, &ksplit, &per);
+    float* part = nullptr;
+    if (ksplit > 1) {
+        // the workspace is sized by dense_prepare before any capture; growing it here is only
+        // legal outside a stream capture
+        const size_t need = sizeof(float) * (size_t)ksplit * R * n;
+        if (ctx->dpart.bytes < need) {
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            VQ_CUDA(cudaStreamIsCapturing(ctx->stream, &cs));
+            if (cs != cudaStreamCaptureStatusNone) return fail(VELOXQ_ECUDA, "dense step workspace not prepared");
+            VQ_TRY(ctx->dpart.ensure(need));
+        }
+        part = ctx->dpart.as<float>();
+    }
+    dim3 g((unsigned)div_up(n, BN), (unsigned)div_up(R, BM), (unsigned)ksplit);
     k_dense_step<FIELD_ONLY><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
                                                          ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out,
-                                                         rule.method, rule.alpha);
+                                                         rule.method, rule.alpha, per, part);
+    if (ksplit > 1)
+        k_dense_finish<FIELD_ONLY><<<(unsigned)div_up((int64_t)R * n, 256), 256, 0, ctx->stream>>>(
+            R, n, ksplit, part, S_cur, S_nxt, Y, ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out, rule.method,
+            rule.alpha);
     VQ_LAUNCH_CHECK("dense_step");
     return VELOXQ_OK;
 }
@@ -222,6 +298,13 @@ int launch_dense_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_
 int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y, const float* a_table, int k,
                float dt, float a0, float c0, float* F_out, const Rule& rule) {
     return launch_dense_step<false>(ctx, R, S_cur, S_nxt, Y, a_table, k, dt, a0, c0, F_out, rule);
+}
+
+int dense_prepare(veloxq_ctx* ctx, int32_t R) {
+    int ksplit, per;
+    dense_split(ctx->n, R, &ksplit, &per);
+    if (ksplit > 1) VQ_TRY(ctx->dpart.ensure(sizeof(float) * (size_t)ksplit * R * ctx->n));
+    return VELOXQ_OK;
 }
 
 int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {

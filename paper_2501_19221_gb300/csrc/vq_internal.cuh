@@ -116,6 +116,7 @@ struct veloxq_ctx {
     // ---- scratch reused across calls ----
     vq::DevBuf s_a, s_b, y, f, ework, best_e, best_bits, flags, a_table, xout, misc;
     vq::DevBuf sop_a, sop_b;      // tensor-core operand copies of S (ping-pong)
+    vq::DevBuf dpart;             // float [ksplit][R][n] split-k partial fields of the FP32 dense step
     vq::DevBuf errw;              // device error word of bounded waits
     int stream_unroll = 0;        // gather variant of the streaming kernels: 1, 4, or 6 (rows of exactly
                                   // 6 couplings); 0: not tuned yet
@@ -172,6 +173,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, uint64_t seed, 
 int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, float* Y,
                const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule = Rule());
 int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
+int dense_prepare(veloxq_ctx* ctx, int32_t R);   // workspace of the split-k FP32 step (before capture)
 int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
 int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
 int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
