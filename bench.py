@@ -46,6 +46,7 @@ NCU_TRAFFIC = {
     ("k_tc_step", "sk_n8192_fp8"): 178_763_520,
     ("k_tc_step", "sk_n8192_bf16"): 286_354_432,
     ("k_stream_step", "lattice_l100"): 4_126_558_000,
+    ("k_stream_step", "hubo_chain_1e7"): 4_206_584_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152

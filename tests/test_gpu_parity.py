@@ -369,6 +369,9 @@ def test_malformed_inputs_rejected(B):
     with pytest.raises(B.VeloxqError) as e:
         B.veloxq_solve(ctx, 0, 10)
     assert e.value.status == B.VELOXQ_EINVAL
+    with pytest.raises(B.VeloxqError) as e:      # beyond the 2^20 replica limit: refused before any launch
+        B.veloxq_solve(ctx, (1 << 20) + 1, 10)
+    assert e.value.status == B.VELOXQ_EINVAL and "2^20" in e.value.message
     with pytest.raises(B.VeloxqError) as e:
         B.veloxq_solve(ctx, 4, 10, B.make_schedule(prec=B.VELOXQ_PREC_FP8))
     assert e.value.status == B.VELOXQ_EUNSUPPORTED
