@@ -194,6 +194,16 @@ int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* p
                         const double* K3, int64_t* n_out, int64_t* nnz_out, int64_t* rowptr, int32_t* col,
                         double* val, double* lin, double* offset);
 
+/* Failure-path self-test of the bounded device waits (the paper has no
+ * counterpart; this is a property of the library). Launches one small
+ * kernel that waits, with the same bounded wait every tensor-core kernel
+ * uses, on a barrier that nothing arrives on: the wait gives up after
+ * budget_cycles SM cycles, records its code and returns, and the device
+ * stays usable. Returns VELOXQ_ETIMEDOUT (with the code in the message) when
+ * that happened, ECUDA otherwise; EINVAL for a budget outside [1e3, 1e10].
+ * Runs on the current device and the default stream. */
+int veloxq_selftest_timeout(int64_t budget_cycles);
+
 /* Release every device and host resource of ctx (NULL is a no-op). */
 void veloxq_destroy(veloxq_ctx* ctx);
 

@@ -33,7 +33,7 @@ EXPORTED = [
     "veloxq_create_ising_csr", "veloxq_destroy", "veloxq_last_error", "veloxq_get_info", "veloxq_set_stream",
     "veloxq_solve", "veloxq_solve_batch", "veloxq_energy", "veloxq_energy_dev", "veloxq_init_state_dev",
     "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad", "veloxq_last_timing",
-    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc", "veloxq_hubo3_reduce",
+    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc", "veloxq_hubo3_reduce", "veloxq_selftest_timeout",
 ]
 
 
@@ -92,6 +92,7 @@ def _load():
         "veloxq_batch_state_dev": (I, [P, I32, P, P]),
         "veloxq_energy_dev_noalloc": (I, [P, I64, P, P, P]),
         "veloxq_hubo3_reduce": (I, [I64, P, I64, P, P, P, I64, P, P, P, P, P, P, P, P, P, P, P]),
+        "veloxq_selftest_timeout": (I, [I64]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -258,6 +259,12 @@ def veloxq_hubo3_reduce(n: int, h=None, pairs=None, triples=None) -> dict:
     m = nnz_out.value
     return {"n": n_out.value, "rowptr": rowptr, "col": col[:m].copy(), "val": val[:m].copy(), "lin": lin,
             "offset": off.value}
+
+
+def veloxq_selftest_timeout(budget_cycles: int) -> None:
+    """Run the bounded-wait self-test (raises VeloxqError: ETIMEDOUT is the
+    expected outcome)."""
+    _check(_lib.veloxq_selftest_timeout(int(budget_cycles)))
 
 
 def veloxq_destroy(ctx: Context):

@@ -746,6 +746,15 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
     return VELOXQ_OK;
 }
 
+int veloxq_selftest_timeout(int64_t budget_cycles) {
+    if (budget_cycles < 1000 || budget_cycles > 10000000000LL)
+        return fail(VELOXQ_EINVAL, "budget_cycles must be in [1e3, 1e10]");
+    int code = 0;
+    VQ_TRY(tc_wait_selftest((long long)budget_cycles, &code));
+    if (code == 0) return fail(VELOXQ_ECUDA, "the self-test wait completed although nothing arrived");
+    return fail(VELOXQ_ETIMEDOUT, "bounded device wait gave up as intended (code " + std::to_string(code) + ")");
+}
+
 int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                 int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa, double* d_knots) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");

@@ -77,12 +77,10 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
             av[4] = a1v.x; av[5] = a1v.y; av[6] = a1v.z; av[7] = a1v.w;
             bv[0] = b0v.x; bv[1] = b0v.y; bv[2] = b0v.z; bv[3] = b0v.w;
             bv[4] = b1v.x; bv[5] = b1v.y; bv[6] = b1v.z; bv[7] = b1v.w;
-            // two-lane FMAs (the same bits as scalar fmaf, half the issue slots)
 #pragma unroll
             for (int i = 0; i < TM; ++i)
 #pragma unroll
-                for (int j = 0; j < TN; j += 2)
-                    vqd::fma2(acc[i][j], acc[i][j + 1], av[i], av[i], bv[j], bv[j + 1], acc[i][j], acc[i][j + 1]);
+                for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
         if (kt + 1 < kt1) store_tiles(cur ^ 1, ra, rb);
         __syncthreads();

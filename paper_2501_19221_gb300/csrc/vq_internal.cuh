@@ -199,6 +199,7 @@ int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtens
             CUtensorMap* ms1);
 int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule = Rule());
 size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R);
+int tc_wait_selftest(long long budget, int* code_out);   // the bounded wait run out on purpose
 int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
             float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
             float* F_out, int* err, const Rule& rule = Rule());

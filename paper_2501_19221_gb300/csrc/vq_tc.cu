@@ -42,7 +42,7 @@ constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BNH * BKB, STAGE_BYTES = A_BYTE
 constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
-enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4 };
+enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4, TC_ERR_SELFTEST = 8 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -78,13 +78,14 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity)
 // Bounded wait: false (and the error word set) if the phase does not complete
 // within the budget or another thread already gave up.
 template <bool CLUSTER = false>
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code,
+                                          long long budget = kWaitCycles) {
     const long long t0 = clock64();
     uint32_t spins = 0;
     while (!(CLUSTER ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity))) {
         if ((++spins & 1023u) == 0) {
             if (*(volatile int*)err) return false;
-            if (clock64() - t0 > kWaitCycles) {
+            if (clock64() - t0 > budget) {
                 atomicOr(err, code);
                 return false;
             }
@@ -399,6 +400,20 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     if (warp == 1) tmem_dealloc(tmem, 2 * BN);
 }
 
+// The bounded wait of the kernels above on a barrier that nothing arrives on:
+// it runs out after `budget` cycles, records its code in the error word and
+// returns (the path every kernel takes when a wait gives up).
+__global__ void k_wait_selftest(int* err, long long budget) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait(&bar, 0, err, TC_ERR_SELFTEST, budget);
+    __syncthreads();
+}
+
 // ---- operand preparation --------------------------------------------------
 __global__ void k_quant_q_bf16(int64_t n, int64_t n_pad, const float* __restrict__ q, __nv_bfloat16* out) {
     const int64_t i = blockIdx.x;
@@ -518,6 +533,22 @@ int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, 
     else
         k_quant_s<2><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
     VQ_LAUNCH_CHECK("tc quantize S");
+    return VELOXQ_OK;
+}
+
+int tc_wait_selftest(long long budget, int* code_out) {
+    int* err = nullptr;
+    VQ_CUDA(cudaMalloc(&err, sizeof(int)));
+    int h = 0;
+    cudaError_t e = cudaMemset(err, 0, sizeof(int));
+    if (e == cudaSuccess) {
+        k_wait_selftest<<<1, 32>>>(err, budget);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(err);
+    if (e != cudaSuccess) return cuda_fail(e, "wait self-test");
+    *code_out = h;
     return VELOXQ_OK;
 }
 
