@@ -349,6 +349,38 @@ __device__ __forceinline__ void pa_update(float F, float b, float lam, float dt,
     x = fminf(fmaxf(__fadd_rn(x, m), -1.0f), 1.0f);
 }
 
+// The same two updates for two replicas of one variable, in the two-lane
+// forms: the same operations in the same order, hence the same bits.
+__device__ __forceinline__ void asb_update2(float F0, float F1, float b, float a_k, float dt, float a0, float c0,
+                                            float& s0, float& s1, float& y0, float& y1) {
+    float t0, t1, q0, q1, c0v, c1v, m0, m1, d0, d1, yh0, yh1, sn0, sn1;
+    add2(t0, t1, F0, F1, b, b);
+    mul2(q0, q1, s0, s1, s0, s1);
+    const float am = __fsub_rn(a0, a_k);
+    add2(c0v, c1v, q0, q1, am, am);
+    mul2(m0, m1, c0v, c1v, s0, s1);
+    const float hc = __fmul_rn(-0.5f, c0);
+    fma2(d0, d1, hc, hc, t0, t1, -m0, -m1);
+    fma2(yh0, yh1, dt, dt, d0, d1, y0, y1);
+    const float da = __fmul_rn(dt, a0);
+    fma2(sn0, sn1, da, da, yh0, yh1, s0, s1);
+    s0 = sn0; s1 = sn1; y0 = yh0; y1 = yh1;
+}
+__device__ __forceinline__ void pa_update2(float F0, float F1, float b, float lam, float dt, float alpha, float c0,
+                                           float& x0, float& x1, float& m0, float& m1) {
+    float t0, t1, h0, h1, g0, g1, e0, e1, n0, n1, u0, u1;
+    add2(t0, t1, F0, F1, b, b);
+    const float hc = __fmul_rn(0.5f, c0);
+    mul2(h0, h1, hc, hc, t0, t1);
+    fma2(g0, g1, lam, lam, x0, x1, h0, h1);
+    mul2(e0, e1, dt, dt, g0, g1);
+    fma2(n0, n1, alpha, alpha, m0, m1, -e0, -e1);
+    add2(u0, u1, x0, x1, n0, n1);
+    m0 = n0; m1 = n1;
+    x0 = fminf(fmaxf(u0, -1.0f), 1.0f);
+    x1 = fminf(fmaxf(u1, -1.0f), 1.0f);
+}
+
 // One update of the given method; lam is pa_lambda(a_k, a0) (PA only).
 __device__ __forceinline__ void step_update(int method, float F, float b, float a_k, float lam, float dt, float a0,
                                             float c0, float alpha, float& s, float& y) {

@@ -264,6 +264,22 @@ def test_resident_and_stream_paths_identical(B):
     assert np.array_equal(a["x"], b["x"]) and a["E_int"] == b["E_int"]
 
 
+@pytest.mark.parametrize("method", [0, 1, 2])
+@pytest.mark.parametrize("m,R", [(4, 40), (4, 304), (4, 600), (4, 640), (16, 600), (16, 1024)])
+def test_resident_variants_match_stream(B, method, m, R):
+    """Every replicas-per-CTA and rows-per-thread variant the plan picks
+    (Chimera C4: 1, 2, 4 and 8 replicas per CTA, one row per thread; C16: 4
+    and 8 replicas per CTA with rows in pairs) does the streaming kernel's
+    FP32 operations in the same order: bitwise the same per-replica energies,
+    for each integrator."""
+    ctx, _ = inst_chimera(B, m)
+    kw = dict(readout_every=25, method=method, dt=0.3)
+    a = B.veloxq_solve(ctx, R, 120, B.make_schedule(path=1, **kw), seed=3)
+    b = B.veloxq_solve(ctx, R, 120, B.make_schedule(path=2, **kw), seed=3)
+    assert np.array_equal(a["E_per_replica"], b["E_per_replica"])
+    assert np.array_equal(a["x"], b["x"])
+
+
 # ----------------------------------------------------------------- solve
 def test_solve_dense_int20_reaches_ground_state(B):
     ctx, p = inst_dense_int20(B)
