@@ -320,42 +320,146 @@ __global__ void k_fix(int64_t n, const double* __restrict__ d, int shift, int64_
 }
 
 // ---------------------------- power iteration -----------------------------
-__global__ void k_pi_init(int64_t n, double* v) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+// FP32 vectors and products (FP64 runs at a small fraction of the FP32 rate
+// on this part, and the estimate only scales c0); block partial norms are
+// summed in FP64 by one block, which also forms 1/|w| once per iteration.
+__device__ __forceinline__ float pi_start(int64_t i) {
     uint32_t h = (uint32_t)i * 2654435761u;
     h ^= h >> 15;
     h *= 2246822519u;
     h ^= h >> 13;
-    const double mag = 1.0 + (double)((h >> 1) & 1023u) / 4096.0;
-    v[i] = (h & 1u) ? mag : -mag;
+    const float mag = 1.0f + (float)((h >> 1) & 1023u) / 4096.0f;
+    return (h & 1u) ? mag : -mag;
 }
-
+__global__ void k_pi_init(int64_t n, float* v) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = pi_start(i);
+}
 __global__ void k_pi_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const float* __restrict__ w, const double* __restrict__ v, const double* __restrict__ nrm2,
-                          double* out) {
+                          const float* __restrict__ w, const float* __restrict__ v, const float* __restrict__ inv,
+                          float* out) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double inv = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
-    double a = 0.0;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a += (double)w[p] * v[col[p]];
-    out[i] = a * inv;
+    float a = 0.0f;
+    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(w[p], v[col[p]], a);
+    out[i] = a * *inv;
 }
-
-__global__ void k_pi_gemv(int64_t n, const float* __restrict__ q, const double* __restrict__ v,
-                          const double* __restrict__ nrm2, double* out) {
-    __shared__ double sh[256];
+__global__ void k_pi_gemv(int64_t n, const float* __restrict__ q, const float* __restrict__ v,
+                          const float* __restrict__ inv, float* out) {
+    __shared__ float sh[256];
     const int64_t i = blockIdx.x;
     const float* row = q + i * n;
-    double a = 0.0;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a += (double)row[j] * v[j];
+    float a = 0.0f;
+    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a = fmaf(row[j], v[j], a);
     sh[threadIdx.x] = a;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
         __syncthreads();
     }
-    if (threadIdx.x == 0) out[i] = *nrm2 > 0.0 ? sh[0] / sqrt(*nrm2) : 0.0;
+    if (threadIdx.x == 0) out[i] = sh[0] * *inv;
+}
+// |x|^2: per-block FP32 partials (fixed partition and tree order) ...
+__global__ void k_pi_norm1(const float* __restrict__ x, int64_t n, double* __restrict__ part) {
+    __shared__ float sh[kRedThreads];
+    float acc = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc = fmaf(x[i], x[i], acc);
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = (double)sh[0];
+}
+// ... summed in FP64 by one block: |x|^2 and 1/|x| for the next product
+__global__ void k_pi_norm2(const double* __restrict__ part, int nparts, double* __restrict__ nrm2, float* inv) {
+    __shared__ double sh[kRedThreads];
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
+    sh[threadIdx.x] = acc;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        *nrm2 = sh[0];
+        *inv = sh[0] > 0.0 ? (float)(1.0 / sqrt(sh[0])) : 0.0f;
+    }
+}
+
+// The same power iteration for a small sparse instance in ONE CTA (no launch
+// per iteration): v, w and the CSR rows in shared memory, FP32 arithmetic.
+// Each thread sums the squares of the rows it writes; one barrier per
+// iteration publishes both w and the per-warp partials, which every warp then
+// reduces in the same fixed order, so all threads hold the same 1/|w|. The
+// partials alternate between two arrays: the next write to one of them comes
+// after the following barrier, when every warp has read it.
+constexpr int kPiThreads = 1024;
+constexpr int kPiWarps = kPiThreads / 32;
+constexpr int64_t kPiSingleMaxN = 8192;
+constexpr size_t kPiSmemMax = 200 * 1024;
+__host__ __device__ inline size_t pi_smem(int64_t n, int64_t nnz) {
+    return sizeof(float) * 2 * (size_t)n + sizeof(int32_t) * (size_t)(n + 1) +
+           (sizeof(int32_t) + sizeof(float)) * (size_t)nnz;
+}
+__device__ __forceinline__ float warp_sum_to_lane0(float a) {
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
+}
+__global__ void __launch_bounds__(kPiThreads) k_pi_single(int32_t n, int32_t nnz, int iters,
+                                                          const int64_t* __restrict__ rp_g,
+                                                          const int32_t* __restrict__ col_g,
+                                                          const float* __restrict__ wq_g, double* out) {
+    extern __shared__ __align__(16) unsigned char pis_raw[];
+    float* v = reinterpret_cast<float*>(pis_raw);
+    float* w = v + n;
+    int32_t* rp = reinterpret_cast<int32_t*>(w + n);
+    int32_t* col = rp + (n + 1);
+    float* wq = reinterpret_cast<float*>(col + nnz);
+    __shared__ float red[2][kPiWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // |x|^2 from the per-warp partials of one array, identical in every thread
+    auto all_norm2 = [&](const float* part) {
+        return __shfl_sync(0xffffffffu, warp_sum_to_lane0(part[lane]), 0);
+    };
+    for (int i = threadIdx.x; i <= n; i += kPiThreads) rp[i] = (int32_t)rp_g[i];
+    for (int p = threadIdx.x; p < nnz; p += kPiThreads) {
+        col[p] = col_g[p];
+        wq[p] = wq_g[p];
+    }
+    float sq = 0.0f;
+    for (int i = threadIdx.x; i < n; i += kPiThreads) {
+        const float x = pi_start(i);
+        v[i] = x;
+        sq = fmaf(x, x, sq);
+    }
+    sq = warp_sum_to_lane0(sq);
+    if (lane == 0) red[0][warp] = sq;
+    __syncthreads();
+    float nrm2 = all_norm2(red[0]);
+    for (int t = 0; t < iters; ++t) {
+        const float inv = nrm2 > 0.0f ? 1.0f / sqrtf(nrm2) : 0.0f;
+        float* part = red[(t + 1) & 1];
+        sq = 0.0f;
+        for (int i = threadIdx.x; i < n; i += kPiThreads) {
+            float a = 0.0f;
+            for (int p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(wq[p], v[col[p]], a);
+            a *= inv;
+            w[i] = a;
+            sq = fmaf(a, a, sq);
+        }
+        sq = warp_sum_to_lane0(sq);
+        if (lane == 0) part[warp] = sq;
+        __syncthreads();
+        nrm2 = all_norm2(part);
+        float* tmp = v;
+        v = w;
+        w = tmp;
+    }
+    if (threadIdx.x == 0) *out = (double)nrm2;
 }
 
 template <typename T>
@@ -640,26 +744,43 @@ int ingest_csr(veloxq_ctx* ctx, const int64_t* rowptr, const int32_t* col, velox
 int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
     const int64_t n = ctx->n;
     cudaStream_t st = ctx->stream;
+    double h = 0.0;
+    if (!ctx->dense && ctx->has_csr && n <= kPiSingleMaxN && pi_smem(n, ctx->nnz) <= kPiSmemMax) {
+        DevBuf one;
+        VQ_TRY(one.ensure(sizeof(double)));
+        const size_t sm = pi_smem(n, ctx->nnz);
+        VQ_CUDA(cudaFuncSetAttribute(k_pi_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        k_pi_single<<<1, kPiThreads, sm, st>>>((int32_t)n, (int32_t)ctx->nnz, iters, ctx->rowptr.as<int64_t>(),
+                                                ctx->col.as<int32_t>(), ctx->wf.as<float>(), one.as<double>());
+        VQ_LAUNCH_CHECK("power iteration");
+        VQ_CUDA(cudaMemcpyAsync(&h, one.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+        VQ_CUDA(cudaStreamSynchronize(st));
+        *rho = std::sqrt(h);
+        return VELOXQ_OK;
+    }
     DevBuf buf;
-    VQ_TRY(buf.ensure(sizeof(double) * (size_t)(2 * n + kRedBlocks + 4)));
-    double* v = buf.as<double>();
-    double* w = v + n;
-    double* part = w + n;
+    const size_t vbytes = (sizeof(float) * (size_t)(2 * n) + 15) & ~size_t(15);
+    VQ_TRY(buf.ensure(vbytes + sizeof(double) * (size_t)(kRedBlocks + 2)));
+    float* v = buf.as<float>();
+    float* w = v + n;
+    double* part = reinterpret_cast<double*>(buf.as<uint8_t>() + vbytes);
     double* nrm = part + kRedBlocks;
+    float* inv = reinterpret_cast<float*>(nrm + 1);
     const unsigned gr = (unsigned)div_up(n, 256);
     k_pi_init<<<gr, 256, 0, st>>>(n, v);
-    VQ_TRY(reduce_sum(st, v, n, 1, nrm, part));
+    k_pi_norm1<<<kRedBlocks, kRedThreads, 0, st>>>(v, n, part);
+    k_pi_norm2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, nrm, inv);
     for (int t = 0; t < iters; ++t) {
         if (ctx->dense)
-            k_pi_gemv<<<(unsigned)n, 256, 0, st>>>(n, ctx->qoff32.as<float>(), v, nrm, w);
+            k_pi_gemv<<<(unsigned)n, 256, 0, st>>>(n, ctx->qoff32.as<float>(), v, inv, w);
         else
             k_pi_spmv<<<gr, 256, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(), ctx->wf.as<float>(),
-                                          v, nrm, w);
-        VQ_TRY(reduce_sum(st, w, n, 1, nrm, part));
+                                          v, inv, w);
+        k_pi_norm1<<<kRedBlocks, kRedThreads, 0, st>>>(w, n, part);
+        k_pi_norm2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, nrm, inv);
         std::swap(v, w);
     }
     VQ_LAUNCH_CHECK("power iteration");
-    double h = 0.0;
     VQ_CUDA(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
     VQ_CUDA(cudaStreamSynchronize(st));
     *rho = std::sqrt(h);

@@ -94,7 +94,7 @@ def test_grad_default_kappa_chain_rule(B):
     ctx, _ = _lattice(B, 5)
     rho = ctx.info.rho
     kappa = 0.8
-    c0 = float(np.float32(2.0 * kappa / rho))
+    c0 = float(np.float32(2.0 * float(np.float32(kappa)) / rho))   # as the library forms it from the float kappa
     ga = B.veloxq_grad(ctx, 8, 30, B.make_schedule(kappa=kappa, readout_every=0), 2, 10)
     gb = B.veloxq_grad(ctx, 8, 30, B.make_schedule(c0=c0, readout_every=0), 2, 10)
     assert ga["loss"] == gb["loss"]
