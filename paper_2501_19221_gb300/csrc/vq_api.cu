@@ -198,9 +198,10 @@ bool is_readout(const RunParams& p, int k) {
 }
 
 // Enqueue the step loop (steps, readouts, argmin) on ctx->stream; ev_steps
-// (if not null) is recorded right after the last integration step.
+// (if not null) is recorded right after the last integration step; tc_energy:
+// readout energies in the tensor-core form (sized before the capture).
 int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& p, int nparts, const TcRun* tc,
-                 cudaEvent_t ev_steps) {
+                 bool tc_energy, cudaEvent_t ev_steps) {
     const Layout lay = path == VELOXQ_PATH_DENSE ? LAYOUT_RN : LAYOUT_NR;
     float* cur = ctx->s_a.as<float>();
     float* nxt = ctx->s_b.as<float>();
@@ -222,7 +223,7 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
         if (ev_steps && k == p.K - 1) VQ_CUDA(cudaEventRecordWithFlags(ev_steps, ctx->stream, cudaEventRecordExternal));
         if (!is_readout(p, k)) continue;
         int64_t* parts = ctx->ework.as<int64_t>();
-        if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_energy(ctx, R, cur, parts, &np));
+        if (path == VELOXQ_PATH_DENSE) VQ_TRY(dense_energy(ctx, R, cur, parts, &np, tc_energy));
         else VQ_TRY(stream_energy(ctx, R, cur, parts, &np));
         VQ_TRY(launch_best_update(ctx, R, np, parts, ctx->best_e.as<int64_t>(), ctx->flags.as<uint8_t>()));
         VQ_TRY(launch_best_bits(ctx, R, lay, cur, ctx->flags.as<uint8_t>(), ctx->best_bits.as<uint32_t>()));
@@ -441,12 +442,12 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         const bool use_tc = path == VELOXQ_PATH_DENSE && p.prec != VELOXQ_PREC_FP32;
         if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc));
         if (path == VELOXQ_PATH_DENSE && !use_tc) VQ_TRY(dense_prepare(ctx, replicas));
+        if (path == VELOXQ_PATH_DENSE) VQ_TRY(tc_energy_prepare(ctx, replicas));
+        const bool tc_e = path == VELOXQ_PATH_DENSE && tc_energy_ready(ctx, replicas);
         VQ_CUDA(cudaEventRecord(ex->t0, ctx->stream));
         VQ_TRY(launch_init_state(ctx, replicas, seed, p.sigma0, lay, ctx->s_a.as<float>(), ctx->y.as<float>()));
-        if (use_tc) {
-            VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
-            VQ_TRY(tc_quant_s(ctx, p.prec, replicas, ctx->s_a.as<float>(), tc.sop[0], rule_of(p)));
-        }
+        if (use_tc || tc_e) VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
+        if (use_tc) VQ_TRY(tc_quant_s(ctx, p.prec, replicas, ctx->s_a.as<float>(), tc.sop[0], rule_of(p)));
         VQ_CUDA(cudaMemsetAsync(ctx->best_e.p, 0x7f, sizeof(int64_t) * R, ctx->stream));
         VQ_CUDA(cudaMemsetAsync(ctx->best_bits.p, 0, sizeof(uint32_t) * R * nw, ctx->stream));
         // the captured loop depends on every pointer and parameter below
@@ -459,6 +460,9 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
                                      (uint64_t)(uintptr_t)ctx->flags.p, (uint64_t)(uintptr_t)ctx->misc.p,
                                      (uint64_t)(uintptr_t)ctx->xout.p, (uint64_t)(uintptr_t)ctx->a_table.p};
         key.push_back((uint64_t)p.method);
+        for (uint64_t v : {(uint64_t)tc_e, (uint64_t)ctx->eplanes, (uint64_t)(uintptr_t)ctx->eplane.p,
+                           (uint64_t)(uintptr_t)ctx->exop.p, (uint64_t)(uintptr_t)ctx->efield.p})
+            key.push_back(v);
         float fp[4] = {p.dt, p.a0, p.c0, p.alpha};
         for (float f : fp) {
             uint32_t u;
@@ -472,7 +476,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
             }
             cudaGraph_t g = nullptr;
             VQ_CUDA(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-            int st = enqueue_loop(ctx, path, replicas, p, nparts, use_tc ? &tc : nullptr, ex->t2);
+            int st = enqueue_loop(ctx, path, replicas, p, nparts, use_tc ? &tc : nullptr, tc_e, ex->t2);
             cudaError_t ce = cudaStreamEndCapture(ctx->stream, &g);
             if (st != VELOXQ_OK) {
                 if (g) cudaGraphDestroy(g);
@@ -495,7 +499,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         VQ_CUDA(cudaEventRecord(ex->t3, ctx->stream));
         launches = 1 + (use_tc ? 1 : 0) + ex->graph_launches;   // init (+ operand) kernels + graph nodes
         main_launches = steps;
-        if (use_tc) VQ_TRY(check_err_word(ctx));
+        if (use_tc || tc_e) VQ_TRY(check_err_word(ctx));
     }
     std::vector<int64_t> be((size_t)R);
     int64_t misc[2] = {0, 0};
@@ -604,19 +608,28 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
     return VELOXQ_OK;
 }
 
-static int energy_impl(veloxq_ctx* ctx, int64_t B, const uint8_t* Xd, double* Ed, int64_t* Eid) {
+// allow_tc: a dense context may take the tensor-core form, whose bounded
+// waits are checked here (this synchronises the stream)
+static int energy_impl(veloxq_ctx* ctx, int64_t B, const uint8_t* Xd, double* Ed, int64_t* Eid, bool allow_tc) {
     int64_t* parts;
     int np = 0;
     const int64_t chunk = 65535;
+    bool tc_e = false;
+    if (allow_tc && ctx->dense && B > 0) {
+        VQ_TRY(tc_energy_prepare(ctx, std::min(chunk, B)));
+        tc_e = tc_energy_ready(ctx, std::min(chunk, B));
+        if (tc_e) VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
+    }
     for (int64_t b0 = 0; b0 < B; b0 += chunk) {
         const int64_t nb = std::min(chunk, B - b0);
         const int npmax = ctx->dense ? (int)div_up(ctx->n, 64) : 64;
         VQ_TRY(ctx->ework.ensure(sizeof(int64_t) * (size_t)npmax * nb));
         parts = ctx->ework.as<int64_t>();
-        if (ctx->dense) VQ_TRY(dense_energy_x(ctx, nb, Xd + b0 * ctx->n, parts, &np));
+        if (ctx->dense) VQ_TRY(dense_energy_x(ctx, nb, Xd + b0 * ctx->n, parts, &np, tc_e));
         else VQ_TRY(sparse_energy_x(ctx, nb, Xd + b0 * ctx->n, parts, &np));
         VQ_TRY(launch_sum_parts(ctx, nb, np, parts, Ed ? Ed + b0 : nullptr, Eid ? Eid + b0 : nullptr));
     }
+    if (tc_e) VQ_TRY(check_err_word(ctx));
     return VELOXQ_OK;
 }
 
@@ -625,7 +638,7 @@ int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* 
     if (batch < 0) return fail(VELOXQ_EINVAL, "batch must be >= 0");
     if (batch > 0 && !X) return fail(VELOXQ_EINVAL, "X must not be NULL");
     if (E_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_int requires an integer-valued context");
-    return energy_impl(ctx, batch, X, E, E_int);
+    return energy_impl(ctx, batch, X, E, E_int, false);
 }
 
 int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int) {
@@ -639,7 +652,7 @@ int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, i
     VQ_TRY(ed.ensure(sizeof(double) * batch));
     if (E_int) VQ_TRY(eid.ensure(sizeof(int64_t) * batch));
     VQ_CUDA(cudaMemcpyAsync(xd.p, X, (size_t)(batch * ctx->n), cudaMemcpyHostToDevice, ctx->stream));
-    VQ_TRY(energy_impl(ctx, batch, xd.as<uint8_t>(), ed.as<double>(), E_int ? eid.as<int64_t>() : nullptr));
+    VQ_TRY(energy_impl(ctx, batch, xd.as<uint8_t>(), ed.as<double>(), E_int ? eid.as<int64_t>() : nullptr, true));
     if (E) VQ_CUDA(cudaMemcpyAsync(E, ed.p, sizeof(double) * batch, cudaMemcpyDeviceToHost, ctx->stream));
     if (E_int) VQ_CUDA(cudaMemcpyAsync(E_int, eid.p, sizeof(int64_t) * batch, cudaMemcpyDeviceToHost, ctx->stream));
     VQ_CUDA(cudaStreamSynchronize(ctx->stream));

@@ -445,7 +445,7 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
         cudaStream_t keep = c->stream;
         c->stream = st;
         int np2 = 0;
-        int rc = dense_energy(c, R, c->s_a.as<float>(), c->ework.as<int64_t>(), &np2);
+        int rc = dense_energy(c, R, c->s_a.as<float>(), c->ework.as<int64_t>(), &np2, false);
         if (rc == VELOXQ_OK) rc = (cudaMemsetAsync(c->best_e.p, 0x7f, sizeof(int64_t) * R, st) == cudaSuccess)
                                       ? VELOXQ_OK : VELOXQ_ECUDA;
         if (rc == VELOXQ_OK) rc = launch_best_update(c, R, np2, c->ework.as<int64_t>(), c->best_e.as<int64_t>(),

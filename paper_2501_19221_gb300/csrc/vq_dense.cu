@@ -146,19 +146,6 @@ __global__ void __launch_bounds__(256) k_dense_finish(int32_t R, int32_t n, int 
     }
 }
 
-template <typename QT> __device__ __forceinline__ int64_t qfix(QT q, int shift);
-template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int shift) { return (int64_t)q * (1ll << shift); }
-template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int shift) { return (int64_t)q * (1ll << shift); }
-// q 2^S is exact in float (a power-of-two scaling that stays below 2^62), so
-// the rounding to an integer is the same as in double, without FP64 arithmetic
-template <> __device__ __forceinline__ int64_t qfix<float>(float q, int shift) {
-    if (shift <= 100) return __float2ll_rn(q * ldexpf(1.0f, shift));
-    return __double2ll_rn((double)q * ldexp(1.0, shift));
-}
-template <> __device__ __forceinline__ int64_t qfix<double>(double q, int shift) {
-    return __double2ll_rn(q * ldexp(1.0, shift));
-}
-
 // Exact energy of x_r = [S_r > 0] (or of a caller batch of bytes), fixed
 // point: parts[g][r] = sum over the 64 rows of tile g of
 // x_ri (dfix_i + sum_{j != i} qfix(Q_ij) x_rj), Q as given.
@@ -182,7 +169,7 @@ __global__ void __launch_bounds__(256) k_dense_energy(int64_t R, int32_t n, cons
         for (int e = threadIdx.x; e < 64 * 32; e += 256) {
             const int ii = e / 32, jj = e % 32;
             const int64_t gi = i0 + ii, gj = j0 + jj;
-            qt[ii][jj] = (gi < n && gj < n && gi != gj) ? qfix<QT>(Q[gi * n + gj], shift) : 0;
+            qt[ii][jj] = (gi < n && gj < n && gi != gj) ? vqd::qfix<QT>(Q[gi * n + gj], shift) : 0;
         }
         if (g == 0) {
             // bit jj of xw[lane] = x[r][j0 + jj]
@@ -268,10 +255,12 @@ int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_n
 }
 
 template <bool FROM_BYTES>
-int launch_dense_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_t* X, int64_t* parts, int* nparts) {
+int launch_dense_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_t* X, int64_t* parts, int* nparts,
+                        bool allow_tc) {
     const int32_t n = (int32_t)ctx->n;
     *nparts = (int)div_up(n, 64);
     if (R == 0) return VELOXQ_OK;
+    if (allow_tc && tc_energy_ready(ctx, R)) return tc_energy(ctx, R, S, X, parts, nparts);
     dim3 g((unsigned)div_up(n, 64), (unsigned)div_up(R, 32));
     const int sh = ctx->energy_shift;
     const int64_t* df = ctx->dfix.as<int64_t>();
@@ -311,12 +300,14 @@ int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
     return launch_dense_step<true>(ctx, R, S, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F, Rule());
 }
 
-int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts) {
-    return launch_dense_energy<false>(ctx, R, S, nullptr, parts, nparts);
+// allow_tc: the tensor-core form when tc_energy_prepare has sized it for R
+// replicas (the caller then checks ctx->errw)
+int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts, bool allow_tc) {
+    return launch_dense_energy<false>(ctx, R, S, nullptr, parts, nparts, allow_tc);
 }
 
-int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts) {
-    return launch_dense_energy<true>(ctx, B, nullptr, X, parts, nparts);
+int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts, bool allow_tc) {
+    return launch_dense_energy<true>(ctx, B, nullptr, X, parts, nparts, allow_tc);
 }
 
 }  // namespace vq

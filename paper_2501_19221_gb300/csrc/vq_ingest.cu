@@ -321,8 +321,11 @@ __global__ void k_fix(int64_t n, const double* __restrict__ d, int shift, int64_
 
 // ---------------------------- power iteration -----------------------------
 // FP32 vectors and products (FP64 runs at a small fraction of the FP32 rate
-// on this part, and the estimate only scales c0); block partial norms are
-// summed in FP64 by one block, which also forms 1/|w| once per iteration.
+// on this part, and the estimate only scales c0). One launch per iteration:
+// each block adds the squares of the entries it wrote, and the last block to
+// finish sums the block partials in FP64, in block order, and forms |w|^2 and
+// 1/|w| for the next launch. |w|^2 and 1/|w| alternate between two slots, so
+// the slot a launch reads is never the one its last block writes.
 __device__ __forceinline__ float pi_start(int64_t i) {
     uint32_t h = (uint32_t)i * 2654435761u;
     h ^= h >> 15;
@@ -331,63 +334,110 @@ __device__ __forceinline__ float pi_start(int64_t i) {
     const float mag = 1.0f + (float)((h >> 1) & 1023u) / 4096.0f;
     return (h & 1u) ? mag : -mag;
 }
-__global__ void k_pi_init(int64_t n, float* v) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) v[i] = pi_start(i);
+__device__ __forceinline__ float warp_sum_to_lane0(float a) {
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
+    return a;
 }
-__global__ void k_pi_spmv(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
-                          const float* __restrict__ w, const float* __restrict__ v, const float* __restrict__ inv,
-                          float* out) {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    float a = 0.0f;
-    for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(w[p], v[col[p]], a);
-    out[i] = a * *inv;
-}
-__global__ void k_pi_gemv(int64_t n, const float* __restrict__ q, const float* __restrict__ v,
-                          const float* __restrict__ inv, float* out) {
-    __shared__ float sh[256];
-    const int64_t i = blockIdx.x;
-    const float* row = q + i * n;
-    float a = 0.0f;
-    for (int64_t j = threadIdx.x; j < n; j += blockDim.x) a = fmaf(row[j], v[j], a);
-    sh[threadIdx.x] = a;
+constexpr int kPiBlock = 256;
+struct PiNorm {
+    double* part;      // one partial per block
+    unsigned* count;   // blocks finished in this launch (reset by the last one)
+    double* nrm2;      // [2] |w|^2, alternating
+    float* inv;        // [2] 1/|w|, alternating
+};
+// Called by every thread of the block with its own sum of squares.
+__device__ __forceinline__ void pi_block_finish(float sq, PiNorm nm, int slot) {
+    __shared__ float wsum[kPiBlock / 32];
+    __shared__ double dsum[kPiBlock];
+    __shared__ bool last;
+    sq = warp_sum_to_lane0(sq);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sq;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        float b = 0.0f;
+        for (int q = 0; q < kPiBlock / 32; ++q) b += wsum[q];
+        nm.part[blockIdx.x] = (double)b;
+        __threadfence();
+        last = atomicAdd(nm.count, 1u) == gridDim.x - 1;
     }
-    if (threadIdx.x == 0) out[i] = sh[0] * *inv;
-}
-// |x|^2: per-block FP32 partials (fixed partition and tree order) ...
-__global__ void k_pi_norm1(const float* __restrict__ x, int64_t n, double* __restrict__ part) {
-    __shared__ float sh[kRedThreads];
-    float acc = 0.0f;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        acc = fmaf(x[i], x[i], acc);
-    sh[threadIdx.x] = acc;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) part[blockIdx.x] = (double)sh[0];
-}
-// ... summed in FP64 by one block: |x|^2 and 1/|x| for the next product
-__global__ void k_pi_norm2(const double* __restrict__ part, int nparts, double* __restrict__ nrm2, float* inv) {
-    __shared__ double sh[kRedThreads];
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nparts; i += blockDim.x) acc += part[i];
-    sh[threadIdx.x] = acc;
+    if (!last) return;
+    double a = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += kPiBlock) a += __ldcg(nm.part + i);
+    dsum[threadIdx.x] = a;
     __syncthreads();
-    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    for (int s = kPiBlock / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) dsum[threadIdx.x] += dsum[threadIdx.x + s];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        *nrm2 = sh[0];
-        *inv = sh[0] > 0.0 ? (float)(1.0 / sqrt(sh[0])) : 0.0f;
+        nm.nrm2[slot] = dsum[0];
+        nm.inv[slot] = dsum[0] > 0.0 ? (float)(1.0 / sqrt(dsum[0])) : 0.0f;
+        *nm.count = 0u;
     }
+}
+__global__ void __launch_bounds__(kPiBlock) k_pi_init(int64_t n, float* __restrict__ v, PiNorm nm) {
+    float sq = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kPiBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPiBlock) {
+        const float x = pi_start(i);
+        v[i] = x;
+        sq = fmaf(x, x, sq);
+    }
+    pi_block_finish(sq, nm, 0);
+}
+// w = Qoff (v / |v|) for CSR rows; odd launches walk the rows backwards so
+// that the ones the previous launch read last (still in L2) come first.
+__global__ void __launch_bounds__(kPiBlock) k_pi_spmv(int64_t n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const float* __restrict__ w8,
+                                                     const float* __restrict__ v, float* __restrict__ out, PiNorm nm,
+                                                     int t) {
+    const float inv = nm.inv[t & 1];
+    const bool rev = t & 1;
+    float sq = 0.0f;
+    for (int64_t k = (int64_t)blockIdx.x * kPiBlock + threadIdx.x; k < n; k += (int64_t)gridDim.x * kPiBlock) {
+        const int64_t i = rev ? n - 1 - k : k;
+        float a = 0.0f;
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(w8[p], v[col[p]], a);
+        a *= inv;
+        out[i] = a;
+        sq = fmaf(a, a, sq);
+    }
+    pi_block_finish(sq, nm, (t + 1) & 1);
+}
+// The same for a dense Qoff: one warp per row, 16-byte loads when n % 4 == 0.
+__global__ void __launch_bounds__(kPiBlock) k_pi_gemv(int64_t n, const float* __restrict__ q,
+                                                     const float* __restrict__ v, float* __restrict__ out, PiNorm nm,
+                                                     int t) {
+    const float inv = nm.inv[t & 1];
+    const bool rev = t & 1;
+    const int lane = threadIdx.x & 31;
+    const int64_t nwarps = (int64_t)gridDim.x * (kPiBlock / 32);
+    float sq = 0.0f;
+    for (int64_t k = (int64_t)blockIdx.x * (kPiBlock / 32) + (threadIdx.x >> 5); k < n; k += nwarps) {
+        const int64_t i = rev ? n - 1 - k : k;
+        const float* row = q + i * n;
+        float a = 0.0f;
+        if ((n & 3) == 0) {
+            const float4* r4 = reinterpret_cast<const float4*>(row);
+            const float4* v4 = reinterpret_cast<const float4*>(v);
+            for (int64_t j = lane; j < n / 4; j += 32) {
+                const float4 x = r4[j], y = v4[j];
+                a = fmaf(x.x, y.x, a);
+                a = fmaf(x.y, y.y, a);
+                a = fmaf(x.z, y.z, a);
+                a = fmaf(x.w, y.w, a);
+            }
+        } else {
+            for (int64_t j = lane; j < n; j += 32) a = fmaf(row[j], v[j], a);
+        }
+        a = warp_sum_to_lane0(a);
+        if (lane == 0) {
+            a *= inv;
+            out[i] = a;
+            sq = fmaf(a, a, sq);
+        }
+    }
+    pi_block_finish(sq, nm, (t + 1) & 1);
 }
 
 // The same power iteration for a small sparse instance in ONE CTA (no launch
@@ -404,10 +454,6 @@ constexpr size_t kPiSmemMax = 200 * 1024;
 __host__ __device__ inline size_t pi_smem(int64_t n, int64_t nnz) {
     return sizeof(float) * 2 * (size_t)n + sizeof(int32_t) * (size_t)(n + 1) +
            (sizeof(int32_t) + sizeof(float)) * (size_t)nnz;
-}
-__device__ __forceinline__ float warp_sum_to_lane0(float a) {
-    for (int o = 16; o > 0; o >>= 1) a += __shfl_down_sync(0xffffffffu, a, o);
-    return a;
 }
 __global__ void __launch_bounds__(kPiThreads) k_pi_single(int32_t n, int32_t nnz, int iters,
                                                           const int64_t* __restrict__ rp_g,
@@ -758,30 +804,31 @@ int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
         *rho = std::sqrt(h);
         return VELOXQ_OK;
     }
+    const int64_t grid_cap = 152 * (2048 / kPiBlock);
+    const unsigned grid = (unsigned)std::max<int64_t>(
+        1, std::min<int64_t>(ctx->dense ? div_up(n, kPiBlock / 32) : div_up(n, kPiBlock), grid_cap));
     DevBuf buf;
     const size_t vbytes = (sizeof(float) * (size_t)(2 * n) + 15) & ~size_t(15);
-    VQ_TRY(buf.ensure(vbytes + sizeof(double) * (size_t)(kRedBlocks + 2)));
+    VQ_TRY(buf.ensure(vbytes + sizeof(double) * ((size_t)grid + 4) + 16));
     float* v = buf.as<float>();
     float* w = v + n;
-    double* part = reinterpret_cast<double*>(buf.as<uint8_t>() + vbytes);
-    double* nrm = part + kRedBlocks;
-    float* inv = reinterpret_cast<float*>(nrm + 1);
-    const unsigned gr = (unsigned)div_up(n, 256);
-    k_pi_init<<<gr, 256, 0, st>>>(n, v);
-    k_pi_norm1<<<kRedBlocks, kRedThreads, 0, st>>>(v, n, part);
-    k_pi_norm2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, nrm, inv);
+    PiNorm nm;
+    nm.part = reinterpret_cast<double*>(buf.as<uint8_t>() + vbytes);
+    nm.nrm2 = nm.part + grid;
+    nm.inv = reinterpret_cast<float*>(nm.nrm2 + 2);
+    nm.count = reinterpret_cast<unsigned*>(nm.inv + 2);
+    VQ_CUDA(cudaMemsetAsync(nm.count, 0, sizeof(unsigned), st));
+    k_pi_init<<<grid, kPiBlock, 0, st>>>(n, v, nm);
     for (int t = 0; t < iters; ++t) {
         if (ctx->dense)
-            k_pi_gemv<<<(unsigned)n, 256, 0, st>>>(n, ctx->qoff32.as<float>(), v, inv, w);
+            k_pi_gemv<<<grid, kPiBlock, 0, st>>>(n, ctx->qoff32.as<float>(), v, w, nm, t);
         else
-            k_pi_spmv<<<gr, 256, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(), ctx->wf.as<float>(),
-                                          v, inv, w);
-        k_pi_norm1<<<kRedBlocks, kRedThreads, 0, st>>>(w, n, part);
-        k_pi_norm2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, nrm, inv);
+            k_pi_spmv<<<grid, kPiBlock, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                 ctx->wf.as<float>(), v, w, nm, t);
         std::swap(v, w);
     }
     VQ_LAUNCH_CHECK("power iteration");
-    VQ_CUDA(cudaMemcpyAsync(&h, nrm, sizeof(double), cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(&h, nm.nrm2 + (iters & 1), sizeof(double), cudaMemcpyDeviceToHost, st));
     VQ_CUDA(cudaStreamSynchronize(st));
     *rho = std::sqrt(h);
     return VELOXQ_OK;

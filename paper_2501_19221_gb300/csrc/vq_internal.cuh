@@ -108,6 +108,11 @@ struct veloxq_ctx {
     vq::DevBuf qtile;             // pre-tiled swizzled BF16 Qoff for the batched kernel
     size_t qtile_bytes = 0;
     int32_t batch_R = 0;          // replicas of the state left by the last batched run (0: none)
+    // exact readout energies on the tensor cores (vq_energy_tc.cu)
+    int eplanes = 0;              // digit planes of round(Q 2^S): 0 not built yet, -1 not used
+    vq::DevBuf eplane;            // bf16 [eplanes][n][n_pad] balanced base-256 digits
+    vq::DevBuf exop;              // bf16 [R][n_pad] x = [S > 0] (operand)
+    vq::DevBuf efield;            // float [R][n] one plane's integer row sums
 
     // ---- common ----
     vq::DevBuf bf;                // float  [n] b = Qs 1 + c
@@ -174,8 +179,8 @@ int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, flo
                const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule = Rule());
 int dense_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F);
 int dense_prepare(veloxq_ctx* ctx, int32_t R);   // workspace of the split-k FP32 step (before capture)
-int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts);
-int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
+int dense_energy(veloxq_ctx* ctx, int32_t R, const float* S, int64_t* parts, int* nparts, bool allow_tc);
+int dense_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts, bool allow_tc);
 int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts, int* nparts);
 
 // persistent batched kernel (vq_batch.cu)
@@ -203,7 +208,13 @@ int tc_wait_selftest(long long budget, int* code_out);   // the bounded wait run
 int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
             float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
             float* F_out, int* err, const Rule& rule = Rule());
+int tc_operand_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, bool a_operand);
 int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
+
+// exact readout energies of a dense instance on the tensor cores (vq_energy_tc.cu)
+int tc_energy_prepare(veloxq_ctx* ctx, int64_t R);   // digit planes and workspaces (before capture)
+bool tc_energy_ready(const veloxq_ctx* ctx, int64_t R);
+int tc_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_t* X, int64_t* parts, int* nparts);
 
 }  // namespace vq
 
@@ -487,6 +498,20 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
     }
     }
+}
+
+// Fixed-point form of a coupling: round(q 2^shift) as int64 (energies).
+template <typename QT> __device__ __forceinline__ int64_t qfix(QT q, int shift);
+template <> __device__ __forceinline__ int64_t qfix<int8_t>(int8_t q, int shift) { return (int64_t)q * (1ll << shift); }
+template <> __device__ __forceinline__ int64_t qfix<int32_t>(int32_t q, int shift) { return (int64_t)q * (1ll << shift); }
+// q 2^S is exact in float (a power-of-two scaling that stays below 2^62), so
+// the rounding to an integer is the same as in double, without FP64 arithmetic
+template <> __device__ __forceinline__ int64_t qfix<float>(float q, int shift) {
+    if (shift <= 100) return __float2ll_rn(q * ldexpf(1.0f, shift));
+    return __double2ll_rn((double)q * ldexp(1.0, shift));
+}
+template <> __device__ __forceinline__ int64_t qfix<double>(double q, int shift) {
+    return __double2ll_rn(q * ldexp(1.0, shift));
 }
 
 }  // namespace vqd

@@ -62,7 +62,7 @@ extern "C" int veloxq_energy_dev_noalloc(veloxq_ctx* ctx, int64_t batch, const u
     VQ_TRY(scratch_on_current_device(&parts));
     int np = 0;
     // every partial sum is written before it is read: nothing in the scratch needs clearing
-    if (ctx->dense) VQ_TRY(dense_energy_x(ctx, batch, X, parts, &np));
+    if (ctx->dense) VQ_TRY(dense_energy_x(ctx, batch, X, parts, &np, false));
     else VQ_TRY(sparse_energy_x(ctx, batch, X, parts, &np));
     return launch_sum_parts(ctx, batch, np, parts, E, E_int);
 }

@@ -536,6 +536,12 @@ int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, 
     return VELOXQ_OK;
 }
 
+// A K-major operand map of the field kernel: A (rows of the coupling
+// matrix, box of BM rows) or B (replicas, box of BN/2 rows).
+int tc_operand_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, bool a_operand) {
+    return make_map(m, base, prec, rows, n_pad, a_operand ? BM : BNH);
+}
+
 int tc_wait_selftest(long long budget, int* code_out) {
     int* err = nullptr;
     VQ_CUDA(cudaMalloc(&err, sizeof(int)));

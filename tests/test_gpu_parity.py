@@ -337,6 +337,24 @@ def test_rho_and_K0(B, name):
     assert info.K0 == pytest.approx(K0, rel=1e-12, abs=1e-12)
 
 
+def test_rho_multi_launch_sparse(B):
+    """A sparse problem too large for the one-CTA power iteration (n = 13824)
+    runs one launch per iteration with the rows walked backwards on odd
+    launches. Ferromagnetic periodic cubic lattice: rho = 6 exactly."""
+    L = I.cubic_lattice_ising(24, seed=0)
+    ctx = B.veloxq_create_csr(L.n, L.rowptr, L.col, np.abs(L.val).astype(np.int32))
+    assert 6.0 * (1 - 2e-2) <= ctx.info.rho <= 6.0 * (1 + 1e-6)
+
+
+def test_rho_multi_launch_dense_unaligned(B):
+    """Dense, n % 4 != 0 and above the CSR size: the GEMV's scalar loop."""
+    n = 517
+    Q, c = I.sk_qubo(n, seed=3)
+    ctx = B.veloxq_create_dense(Q, c)
+    rho = O.spectral_radius(O.problem_from_dense(Q.astype(np.float64), c))
+    assert rho * (1 - 2e-2) <= ctx.info.rho <= rho * (1 + 1e-6)
+
+
 def test_ising_offset_matches_oracle(B):
     sp = I.chimera_ising(3, 3, 4, seed=2)
     h = np.random.default_rng(1).integers(-2, 3, size=sp.n).astype(np.float64)
