@@ -84,6 +84,12 @@ def workload(name: str) -> dict:
                 "readout_every": 50,
                 "desc": "3-body +-Gaussian spin-glass chain (Sec. HUBO eq. nn), N = 1e7, reduced to second order "
                         "by eq. reduction (one auxiliary spin per cubic term: n = 2e7 - 2), float CSR"}
+    if name == "xorsat_3r3x_1e5":
+        x = I.xorsat_3r3x(10 ** 5, seed=0)
+        return {"name": name, "kind": "hubo", "hubo": x.hubo, "E0_hubo": x.E0, "n": 2 * 10 ** 5, "R": 256,
+                "K": 2000, "readout_every": 100,
+                "desc": "planted 3-regular 3-XORSAT (Sec. 3R3X), 1e5 equations and variables, reduced to second "
+                        "order by eq. reduction (n = 2e5), ground energy -1e5 by construction, float CSR"}
     if name == "lattice_l464":
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
@@ -720,6 +726,10 @@ def run_ours(args, rank, world, local_rank):
             if w["kind"] == "hubo":
                 # the third-order cost of the original spins is at most the reduced cost
                 line["quality"]["hubo_energy_upper_bound"] = 2 * results[-1] + off + w["hubo_offset"]
+                if "E0_hubo" in w:
+                    e0 = w["E0_hubo"]
+                    line["quality"]["planted_energy"] = e0
+                    line["quality"]["gap_to_planted"] = (line["quality"]["hubo_energy_upper_bound"] - e0) / abs(e0)
             line["quality"]["best_over_ranks"] = best_ranks
         else:
             gaps = [(2 * E + c.info.ising_offset - e0) / abs(e0)

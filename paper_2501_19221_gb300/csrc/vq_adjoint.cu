@@ -55,8 +55,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_loss(int64_t n, int32_t R, 
     const int64_t total = n * (int64_t)nvec;
     const float invR = 1.0f / (float)R;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / nvec;
-        const int64_t off = (int64_t)(t - i * nvec) * V;
+        int64_t i;
+        int32_t vi;
+        vqd::split_index(t, n, nvec, i, vi);
+        const int64_t off = (int64_t)vi * V;
         const int64_t me = i * R + off;
         float acc[V], s[V], ls[V], ly[V];
         vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, S, R, off, i, acc, udeg);
@@ -92,8 +94,10 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
     double acc3[3] = {0.0, 0.0, 0.0};
     const int64_t total = n * (int64_t)nvec;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = t / nvec;
-        const int64_t off = (int64_t)(t - i * nvec) * V;
+        int64_t i;
+        int32_t vi;
+        vqd::split_index(t, n, nvec, i, vi);
+        const int64_t off = (int64_t)vi * V;
         const int64_t me = i * R + off;
         float acc[V], s[V], y[V], ls[V], ly[V], gp[V], gs[V], gy[V];
         vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, Sk, R, off, i, acc, udeg);
@@ -142,9 +146,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_b(int64_t n, int32_t R, int
                                                        float wscale, const float* __restrict__ gphi,
                                                        const float* __restrict__ gsl, float* lam_s, int udeg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t / nvec;
-    if (i >= n) return;
-    const int64_t off = (int64_t)(t - i * nvec) * V;
+    if (t >= n * nvec) return;
+    int64_t i;
+    int32_t vi;
+    vqd::split_index(t, n, nvec, i, vi);
+    const int64_t off = (int64_t)vi * V;
     const int64_t me = i * R + off;
     float acc[V], g[V];
     vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, gphi, R, off, i, acc, udeg);

@@ -517,6 +517,9 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         ex->timing.launches = launches;
         ex->timing.path = (int32_t)path;
         ex->timing.main_launches = main_launches;
+        const bool streamed = path == VELOXQ_PATH_STREAM;
+        ex->timing.stream_gather = streamed ? ctx->stream_unroll : 0;
+        ex->timing.stream_chunk = streamed ? ctx->stream_cvec * vec_width(replicas) : 0;
         ex->timed = true;
     }
     const int sh = ctx->energy_shift;
@@ -604,6 +607,8 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
     ex->timing.launches = 1 + 5 * (int64_t)count;
     ex->timing.path = VELOXQ_PATH_DENSE;
     ex->timing.main_launches = 1;
+    ex->timing.stream_gather = 0;
+    ex->timing.stream_chunk = 0;
     ex->timed = true;
     return VELOXQ_OK;
 }
@@ -810,6 +815,8 @@ int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_s
     ex->timing.launches = tm.launches;
     ex->timing.path = VELOXQ_PATH_STREAM;
     ex->timing.main_launches = tm.reverse_launches;
+    ex->timing.stream_gather = 0;
+    ex->timing.stream_chunk = 0;
     ex->timed = true;
     if (d_kappa) {
         // c0 = kappa / rho(J) = 2 kappa / rho(Qoff) unless c0 was given

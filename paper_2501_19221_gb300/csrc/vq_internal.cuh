@@ -126,6 +126,7 @@ struct veloxq_ctx {
     int stream_unroll = 0;        // gather variant of the streaming kernels: 1, 4, or 6 (rows of exactly
                                   // 6 couplings); 0: not tuned yet
     int32_t stream_tuned_R = -1;  // replica count the variant was tuned for
+    int32_t stream_cvec = 0;      // replica vectors per chunk of the streaming step's thread order (0: all)
 };
 
 namespace vq {
@@ -497,6 +498,23 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
 #pragma unroll
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv[u], sj[u][l], acc[l]);
     }
+    }
+}
+
+// Row i and replica vector v of the linear thread index t < n * nvec over n
+// rows of nvec vectors; 32-bit divisions when every index fits (a 64-bit
+// division costs several times as many instructions).
+__device__ __forceinline__ void split_index(int64_t t, int64_t n, int32_t nvec, int64_t& i, int32_t& v) {
+    if (nvec == 1) {
+        i = t;
+        v = 0;
+    } else if (n * nvec < (int64_t(1) << 32)) {
+        const uint32_t tt = (uint32_t)t, r = tt / (uint32_t)nvec;
+        i = r;
+        v = (int32_t)(tt - r * (uint32_t)nvec);
+    } else {
+        i = t / nvec;
+        v = (int32_t)(t - i * nvec);
     }
 }
 

@@ -6,6 +6,8 @@
 // Step (App. B, ballistic form):  F_i = sum_{j != i} Qs_ij s_j  over the CSR
 // row of i, then phi, y, s, walls. Couplings come as FP32 Qs or, for integer
 // instances with |2 Qs| <= 127, as int8 2Qs (F = acc / 2, exact scaling).
+#include <vector>
+
 #include "vq_internal.cuh"
 
 namespace vq {
@@ -27,11 +29,31 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
                                                      float* __restrict__ S_nxt, const float* Y_in, float* Y_out,
                                                      const float* __restrict__ bf, const float* __restrict__ a_table,
                                                      int k, float dt, float a0, float c0, float* __restrict__ F_out,
-                                                     int udeg, int method, float alpha) {
+                                                     int udeg, int method, float alpha, int32_t cvec) {
+    // threads in chunk-major order: all rows of replica vectors [c cvec,
+    // (c+1) cvec) before the next chunk (cvec = nvec: one chunk), so that
+    // the neighbours' states a wave gathers span one chunk of every row
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i = t / nvec;
-    if (i >= n) return;
-    const int32_t v = (int32_t)(t - i * nvec);
+    if (t >= n * nvec) return;
+    int64_t i;
+    int32_t v;
+    if (cvec == nvec) {
+        vqd::split_index(t, n, nvec, i, v);
+    } else {
+        // chunk c = t / (n cvec), then row and vector within the chunk
+        int64_t c, rem;
+        if (n * nvec < (int64_t(1) << 32)) {
+            const uint32_t per_chunk = (uint32_t)n * (uint32_t)cvec;
+            c = (uint32_t)t / per_chunk;
+            rem = t - c * per_chunk;
+        } else {
+            c = t / (n * cvec);
+            rem = t - c * n * cvec;
+        }
+        int32_t w;
+        vqd::split_index(rem, n, cvec, i, w);
+        v = (int32_t)(c * cvec) + w;
+    }
     const int64_t off = (int64_t)v * V;
     const int64_t me = i * R + off;
     // the variable's own state first: independent of the couplings, in flight during the gathers
@@ -151,6 +173,7 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
                 const float* a_table, int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
     const int V = vec_width(R);
     const int32_t nvec = R / V;
+    const int32_t cvec = (ctx->stream_cvec > 0 && nvec % ctx->stream_cvec == 0) ? ctx->stream_cvec : nvec;
     const int64_t total = ctx->n * (int64_t)nvec;
     const unsigned g = (unsigned)div_up(total, 256);
     const int64_t* rp = ctx->rowptr.as<int64_t>();
@@ -160,7 +183,7 @@ int launch_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, co
 #define VQ_STEP_U(VV, WT, WPTR, SC, U)                                                                       \
     k_stream_step<VV, WT, FIELD_ONLY, U, SIGN><<<g, 256, 0, st>>>(ctx->n, R, nvec, rp, cl, WPTR, SC, S_cur, S_nxt, \
                                                                   Y_in, Y_out, bf, a_table, k, dt, a0, c0, F_out, \
-                                                                  ctx->uniform_deg, rule.method, rule.alpha)
+                                                                  ctx->uniform_deg, rule.method, rule.alpha, cvec)
 #define VQ_STEP(VV, WT, WPTR, SC)                                   \
     do {                                                            \
         if (unroll == 6) VQ_STEP_U(VV, WT, WPTR, SC, 6);            \
@@ -203,8 +226,36 @@ int stream_field(veloxq_ctx* ctx, int32_t R, const float* S, float* F) {
     return launch_step<true, false>(ctx, R, S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F, Rule());
 }
 
-// Pick the gather variant of the streaming kernels for R replicas by timing
-// three steps of each on the caller's buffers (contents are overwritten).
+// Chunk widths (replica vectors) worth trying for R replicas: when one state
+// array is larger than about half of L2, the widths whose chunk of every row
+// (n x width x V floats) fits in 64 MB, at least 32 replicas (one 128-byte
+// line per row) and dividing the vectors of a row; 0 (no chunking) always.
+static std::vector<int32_t> chunk_candidates(int64_t n, int32_t R) {
+    const int V = vec_width(R);
+    const int32_t nvec = R / V;
+    const int64_t budget = int64_t(64) << 20;
+    std::vector<int32_t> out = {0};
+    if (n * (int64_t)R * 4 <= budget) return out;
+    int32_t widest = 0;
+    for (int32_t cv = nvec / 2; cv * V >= 32; --cv)
+        if (nvec % cv == 0 && n * (int64_t)cv * V * 4 <= budget) {
+            widest = cv;
+            break;
+        }
+    if (widest) {
+        out.push_back(widest);
+        for (int32_t cv = widest / 2; cv * V >= 32; --cv)
+            if (nvec % cv == 0) {
+                out.push_back(cv);
+                break;
+            }
+    }
+    return out;
+}
+
+// Pick the gather variant (one, four or six couplings at a time) and the
+// replica chunk width of the streaming kernels for R replicas by timing three
+// steps of each pair on the caller's buffers (contents are overwritten).
 // Runs eagerly on ctx->stream; must not be called during stream capture.
 int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y) {
     if (ctx->stream_unroll != 0 && ctx->stream_tuned_R == R) return VELOXQ_OK;
@@ -213,25 +264,33 @@ int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y
     VQ_CUDA(cudaEventCreate(&e1));
     float best = 1e30f;
     int pick = 1;
+    int32_t pick_cv = 0;
     VQ_TRY(launch_init_state(ctx, R, 1, 0.1f, LAYOUT_NR, S_a, Y));
     const float* at = ctx->a_table.as<float>();
-    for (int u : {1, 4, 6}) {
-        if (u == 6 && ctx->uniform_deg != 6) continue;
-        ctx->stream_unroll = u;
-        VQ_TRY((launch_step<false, false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr, Rule())));   // warm
-        VQ_CUDA(cudaEventRecord(e0, ctx->stream));
-        for (int k = 0; k < 3; ++k)
-            VQ_TRY((launch_step<false, false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f,
-                                              1.0f, 0.1f, nullptr, Rule())));
-        VQ_CUDA(cudaEventRecord(e1, ctx->stream));
-        VQ_CUDA(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        VQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) { best = ms; pick = u; }
-    }
+    for (int32_t cv : chunk_candidates(ctx->n, R))
+        for (int u : {1, 4, 6}) {
+            if (u == 6 && ctx->uniform_deg != 6) continue;
+            ctx->stream_unroll = u;
+            ctx->stream_cvec = cv;
+            VQ_TRY((launch_step<false, false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr, Rule())));   // warm
+            VQ_CUDA(cudaEventRecord(e0, ctx->stream));
+            for (int k = 0; k < 3; ++k)
+                VQ_TRY((launch_step<false, false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f,
+                                                  1.0f, 0.1f, nullptr, Rule())));
+            VQ_CUDA(cudaEventRecord(e1, ctx->stream));
+            VQ_CUDA(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            VQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                pick = u;
+                pick_cv = cv;
+            }
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->stream_unroll = pick;
+    ctx->stream_cvec = pick_cv;
     ctx->stream_tuned_R = R;
     return VELOXQ_OK;
 }

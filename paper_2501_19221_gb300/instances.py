@@ -320,3 +320,62 @@ def max3sat_weighted(N: int, seed: int = 0) -> Hubo3:
     pv = np.concatenate([e * l[:, 0] * l[:, 1], e * l[:, 0] * l[:, 2], e * l[:, 1] * l[:, 2]])
     K = e * l[:, 0] * l[:, 1] * l[:, 2]
     return Hubo3(N, h, (pi, pj, pv), (idx[0], idx[1], idx[2], K), const=float(e.sum()))
+
+
+class Xorsat3R3X:
+    """A planted 3-regular 3-XORSAT instance: the equations (T, b), the
+    planted assignment and the third-order Ising cost built from them."""
+
+    def __init__(self, T, b, x_planted, hubo, E0):
+        self.T = T                    # [m][3] int64, the variables of equation i (distinct, sorted)
+        self.b = b                    # [m] uint8, right-hand sides
+        self.x_planted = x_planted    # [n] uint8
+        self.s_planted = (2 * x_planted.astype(np.int8) - 1).astype(np.int8)
+        self.hubo = hubo              # Hubo3: sum_i K_i s_i1 s_i2 s_i3, K_i = (-1)^b_i
+        self.E0 = E0                  # ground energy, -m
+
+
+def _three_regular_triples(n: int, rng, max_rounds: int = 100000) -> np.ndarray:
+    """m = n triples of distinct variables, every variable in exactly three of
+    them and no triple twice: three copies of every variable dealt at random
+    into rows of three, then rows that repeat a variable or an earlier row
+    swap one entry with a random entry elsewhere (which keeps every
+    variable's count at three) until none is left."""
+    if n < 4:
+        raise ValueError("a 3-regular 3-XORSAT instance needs n >= 4")
+    T = rng.permutation(np.repeat(np.arange(n, dtype=np.int64), 3)).reshape(n, 3)
+    for _ in range(max_rounds):
+        S = np.sort(T, axis=1)
+        bad = (S[:, 0] == S[:, 1]) | (S[:, 1] == S[:, 2])
+        _, first = np.unique(S, axis=0, return_index=True)
+        again = np.ones(n, dtype=bool)
+        again[first] = False
+        rows = np.flatnonzero(bad | again)
+        if rows.size == 0:
+            return S
+        for r in rows:
+            q, a, c = int(rng.integers(n)), int(rng.integers(3)), int(rng.integers(3))
+            T[r, a], T[q, c] = T[q, c], T[r, a]
+    raise RuntimeError("no simple 3-regular triple system found")
+
+
+def xorsat_3r3x(n: int, seed: int = 0) -> Xorsat3R3X:
+    """Planted 3-regular 3-XORSAT (Sec. "3-regular 3-XORSAT equation
+    planting"): m = n equations sum_{j in T_i} x_j = b_i (mod 2) over three
+    distinct variables each, every variable in exactly three equations. A
+    uniformly random x* fixes b = A x* (mod 2), so the system has a solution.
+
+    With sigma_j = (-1)^{x_j} the equations read prod sigma = (-1)^{b_i} and
+    the cost is -sum_i (-1)^{b_i} prod sigma. The library's spins are
+    s = 2x - 1 = -sigma, and a product of three flips sign, so the cost is
+    sum_i K_i s_i1 s_i2 s_i3 with K_i = (-1)^{b_i}. Each term is at least -1
+    and equals -1 exactly when equation i holds: the ground energy is -m,
+    reached at s* = 2x* - 1 and at every other solution of the system."""
+    rng = np.random.default_rng(seed)
+    T = _three_regular_triples(n, rng)
+    x = rng.integers(0, 2, size=n).astype(np.uint8)
+    b = (x[T[:, 0]] ^ x[T[:, 1]] ^ x[T[:, 2]]).astype(np.uint8)
+    K = 1.0 - 2.0 * b.astype(np.float64)
+    empty = np.zeros(0, dtype=np.int64)
+    hubo = Hubo3(n, np.zeros(n), (empty, empty, np.zeros(0)), (T[:, 0], T[:, 1], T[:, 2], K))
+    return Xorsat3R3X(T, b, x, hubo, -float(n))

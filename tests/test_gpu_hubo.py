@@ -41,3 +41,49 @@ def test_reduced_solve_reaches_hubo_minimum(B, kind, path):
     Hs = O.hubo3_energy(N, inst.h, inst.pairs, inst.triples, s[None, :N])[0]
     assert Hs <= Hred + 1e-9
     assert Hs == pytest.approx(H.min(), abs=1e-9)
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_3r3x_reduced_solve_reaches_planted_energy(B, path):
+    """Planted 3-regular 3-XORSAT, n = 24 equations and variables, reduced to
+    48 spins: the solve returns a configuration whose original spins satisfy
+    every equation (third-order cost -m). The FP64 oracle's dynamics from
+    the same initial states put 207 of 256 replicas there."""
+    inst = I.xorsat_3r3x(24, seed=1)
+    h = inst.hubo
+    red = B.veloxq_hubo3_reduce(h.n, h.h, h.pairs, h.triples)
+    ctx = B.veloxq_create_ising_csr(red["n"], red["rowptr"], red["col"], red["val"], red["lin"])
+    rho = ctx.info.rho
+    out = B.veloxq_solve(ctx, 256, 2000, B.make_schedule(path=path, c0=float(np.float32(2.0 / rho))), seed=1)
+    s = 2 * out["x"].astype(np.int8) - 1
+    Hs = O.hubo3_energy(h.n, h.h, h.pairs, h.triples, s[None, :h.n].astype(np.float64))[0]
+    assert 2 * out["E"] + ctx.info.ising_offset + red["offset"] >= Hs - 1e-9
+    assert Hs == inst.E0
+
+
+def test_stream_chunked_thread_order(B):
+    """A random sparse graph whose state outgrows L2 (3R3X, 1e5 equations,
+    2e5 spins, 256 replicas: 205 MB per state array): the timed choice of the
+    streaming step takes a chunked thread order (every row of a replica chunk
+    before the next chunk, so the neighbours' states gathered stay in L2), and
+    its field matches the oracle on replicas from several chunks."""
+    inst = I.xorsat_3r3x(10 ** 5, seed=0)
+    h = inst.hubo
+    red = B.veloxq_hubo3_reduce(h.n, h.h, h.pairs, h.triples)
+    ctx = B.veloxq_create_ising_csr(red["n"], red["rowptr"], red["col"], red["val"], red["lin"])
+    R, n = 256, red["n"]
+    B.veloxq_solve(ctx, R, 4, B.make_schedule(path=2, readout_every=0), seed=2)
+    t = B.veloxq_last_timing(ctx)
+    assert t.path == 2 and t.stream_gather in (1, 4)
+    assert t.stream_chunk > 0 and R % t.stream_chunk == 0
+    S = I.uniform_state(R, n, seed=3)
+    F = torch.empty(R, n, device="cuda")
+    B.veloxq_field_dev(ctx, R, B.VELOXQ_PREC_FP32, torch.as_tensor(S, device="cuda"), F)
+    torch.cuda.synchronize()
+    rows = np.r_[0:3, t.stream_chunk - 1:t.stream_chunk + 2, R - 3:R]
+    N, (qi, qj, qv), lin, _ = O.hubo3_reduce(h.n, h.h, h.pairs, h.triples)
+    p, _ = O.ising_pairs_to_qubo(N, qi, qj, qv, lin)
+    Ss = S[rows].astype(np.float64)
+    ref = O.field(p, Ss)
+    scale = O.abs_field(p, Ss)
+    assert np.all(np.abs(F.cpu().numpy()[rows].astype(np.float64) - ref) <= 1e-5 * scale + 1e-30)
