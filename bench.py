@@ -45,8 +45,9 @@ NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 291_072,
     ("k_tc_step", "sk_n8192_fp8"): 178_763_520,
     ("k_tc_step", "sk_n8192_bf16"): 286_354_432,
-    ("k_stream_step", "lattice_l100"): 4_126_558_000,
-    ("k_stream_step", "hubo_chain_1e7"): 4_206_584_000,
+    ("k_stream_step", "lattice_l100"): 4_129_237_000,
+    ("k_stream_step", "hubo_chain_1e7"): 4_204_906_000,
+    ("k_stream_step", "xorsat_3r3x_1e5"): 878_414_848,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 NUM_SMS = 152
