@@ -441,20 +441,25 @@ __global__ void __launch_bounds__(kPiBlock) k_pi_gemv(int64_t n, const float* __
 }
 
 // The same power iteration for a small sparse instance in ONE CTA (no launch
-// per iteration): v, w and the CSR rows in shared memory, FP32 arithmetic.
-// Each thread sums the squares of the rows it writes; one barrier per
-// iteration publishes both w and the per-warp partials, which every warp then
-// reduces in the same fixed order, so all threads hold the same 1/|w|. The
-// partials alternate between two arrays: the next write to one of them comes
-// after the following barrier, when every warp has read it.
+// per iteration): v, w and the rows in shared memory, FP32 arithmetic. With
+// W > 0 the rows are stored as W slots each, slot-major (slot k of row i at
+// k n + i), short rows padded with zero weights on their own column, and the
+// slot loop is unrolled; W = 0 keeps the CSR rows. Either way a row is summed
+// in CSR order. Each thread sums the squares of the rows it writes; one
+// barrier per iteration publishes both w and the per-warp partials, which
+// every warp then reduces in the same fixed order, so all threads hold the
+// same 1/|w|. The partials alternate between two arrays: the next write to
+// one of them comes after the following barrier, when every warp has read it.
 constexpr int kPiThreads = 1024;
 constexpr int kPiWarps = kPiThreads / 32;
 constexpr int64_t kPiSingleMaxN = 8192;
 constexpr size_t kPiSmemMax = 200 * 1024;
-__host__ __device__ inline size_t pi_smem(int64_t n, int64_t nnz) {
+__host__ __device__ inline size_t pi_smem(int64_t n, int64_t nnz, int W) {
+    if (W > 0) return sizeof(float) * 2 * (size_t)n + (sizeof(int32_t) + sizeof(float)) * (size_t)n * (size_t)W;
     return sizeof(float) * 2 * (size_t)n + sizeof(int32_t) * (size_t)(n + 1) +
            (sizeof(int32_t) + sizeof(float)) * (size_t)nnz;
 }
+template <int W>
 __global__ void __launch_bounds__(kPiThreads) k_pi_single(int32_t n, int32_t nnz, int iters,
                                                           const int64_t* __restrict__ rp_g,
                                                           const int32_t* __restrict__ col_g,
@@ -462,20 +467,42 @@ __global__ void __launch_bounds__(kPiThreads) k_pi_single(int32_t n, int32_t nnz
     extern __shared__ __align__(16) unsigned char pis_raw[];
     float* v = reinterpret_cast<float*>(pis_raw);
     float* w = v + n;
-    int32_t* rp = reinterpret_cast<int32_t*>(w + n);
-    int32_t* col = rp + (n + 1);
-    float* wq = reinterpret_cast<float*>(col + nnz);
+    int32_t* rp = reinterpret_cast<int32_t*>(w + n);                       // W = 0
+    int32_t* col = W > 0 ? reinterpret_cast<int32_t*>(w + n) : rp + (n + 1);
+    float* wq = reinterpret_cast<float*>(col + (W > 0 ? W * n : nnz));
     __shared__ float red[2][kPiWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     // |x|^2 from the per-warp partials of one array, identical in every thread
     auto all_norm2 = [&](const float* part) {
         return __shfl_sync(0xffffffffu, warp_sum_to_lane0(part[lane]), 0);
     };
-    for (int i = threadIdx.x; i <= n; i += kPiThreads) rp[i] = (int32_t)rp_g[i];
-    for (int p = threadIdx.x; p < nnz; p += kPiThreads) {
-        col[p] = col_g[p];
-        wq[p] = wq_g[p];
+    if constexpr (W > 0) {
+        for (int i = threadIdx.x; i < n; i += kPiThreads) {
+            const int p0 = (int)rp_g[i], deg = (int)(rp_g[i + 1] - rp_g[i]);
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                col[k * n + i] = k < deg ? col_g[p0 + k] : i;
+                wq[k * n + i] = k < deg ? wq_g[p0 + k] : 0.0f;
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i <= n; i += kPiThreads) rp[i] = (int32_t)rp_g[i];
+        for (int p = threadIdx.x; p < nnz; p += kPiThreads) {
+            col[p] = col_g[p];
+            wq[p] = wq_g[p];
+        }
     }
+    // (Qoff v)_i in CSR order
+    auto row_dot = [&](const float* x, int i) {
+        float a = 0.0f;
+        if constexpr (W > 0) {
+#pragma unroll
+            for (int k = 0; k < W; ++k) a = fmaf(wq[k * n + i], x[col[k * n + i]], a);
+        } else {
+            for (int p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(wq[p], x[col[p]], a);
+        }
+        return a;
+    };
     float sq = 0.0f;
     for (int i = threadIdx.x; i < n; i += kPiThreads) {
         const float x = pi_start(i);
@@ -490,12 +517,18 @@ __global__ void __launch_bounds__(kPiThreads) k_pi_single(int32_t n, int32_t nnz
         const float inv = nrm2 > 0.0f ? 1.0f / sqrtf(nrm2) : 0.0f;
         float* part = red[(t + 1) & 1];
         sq = 0.0f;
-        for (int i = threadIdx.x; i < n; i += kPiThreads) {
-            float a = 0.0f;
-            for (int p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(wq[p], v[col[p]], a);
-            a *= inv;
-            w[i] = a;
-            sq = fmaf(a, a, sq);
+        // two rows at a time (the second clamped into range, kept only when
+        // it exists) so that both rows' loads are in flight together
+        for (int i0 = threadIdx.x; i0 < n; i0 += 2 * kPiThreads) {
+            const int i1 = i0 + kPiThreads;
+            const float a0 = row_dot(v, i0) * inv;
+            const float a1 = row_dot(v, i1 < n ? i1 : i0) * inv;
+            w[i0] = a0;
+            sq = fmaf(a0, a0, sq);
+            if (i1 < n) {
+                w[i1] = a1;
+                sq = fmaf(a1, a1, sq);
+            }
         }
         sq = warp_sum_to_lane0(sq);
         if (lane == 0) part[warp] = sq;
@@ -791,13 +824,25 @@ int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
     const int64_t n = ctx->n;
     cudaStream_t st = ctx->stream;
     double h = 0.0;
-    if (!ctx->dense && ctx->has_csr && n <= kPiSingleMaxN && pi_smem(n, ctx->nnz) <= kPiSmemMax) {
+    // slots per row of the one-CTA form: the longest row rounded up to 6, 8,
+    // 12 or 16 (0: CSR rows)
+    int W = 0;
+    for (int c : {6, 8, 12, 16})
+        if (ctx->max_row <= c) {
+            W = c;
+            break;
+        }
+    if (W && pi_smem(n, ctx->nnz, W) > kPiSmemMax) W = 0;
+    if (!ctx->dense && ctx->has_csr && n <= kPiSingleMaxN && pi_smem(n, ctx->nnz, W) <= kPiSmemMax) {
         DevBuf one;
         VQ_TRY(one.ensure(sizeof(double)));
-        const size_t sm = pi_smem(n, ctx->nnz);
-        VQ_CUDA(cudaFuncSetAttribute(k_pi_single, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        k_pi_single<<<1, kPiThreads, sm, st>>>((int32_t)n, (int32_t)ctx->nnz, iters, ctx->rowptr.as<int64_t>(),
-                                                ctx->col.as<int32_t>(), ctx->wf.as<float>(), one.as<double>());
+        const size_t sm = pi_smem(n, ctx->nnz, W);
+        void (*fn)(int32_t, int32_t, int, const int64_t*, const int32_t*, const float*, double*) =
+            W == 6 ? k_pi_single<6> : W == 8 ? k_pi_single<8> : W == 12 ? k_pi_single<12>
+                                    : W == 16 ? k_pi_single<16> : k_pi_single<0>;
+        VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        fn<<<1, kPiThreads, sm, st>>>((int32_t)n, (int32_t)ctx->nnz, iters, ctx->rowptr.as<int64_t>(),
+                                      ctx->col.as<int32_t>(), ctx->wf.as<float>(), one.as<double>());
         VQ_LAUNCH_CHECK("power iteration");
         VQ_CUDA(cudaMemcpyAsync(&h, one.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         VQ_CUDA(cudaStreamSynchronize(st));
