@@ -29,13 +29,11 @@ constexpr int kRedThreads = 512;
 template <typename T> __device__ __forceinline__ double to_d(T v) { return (double)v; }
 
 // deterministic two-stage sum (fixed partition and tree order)
-__global__ void k_sum_stage1(const double* __restrict__ x, int64_t n, int square, double* __restrict__ part) {
+__global__ void k_sum_stage1(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
     __shared__ double sh[kRedThreads];
     double acc = 0.0;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-        const double v = x[i];
-        acc += square ? v * v : v;
-    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        acc += x[i];
     sh[threadIdx.x] = acc;
     __syncthreads();
     for (int s = blockDim.x / 2; s > 0; s >>= 1) {
@@ -58,8 +56,8 @@ __global__ void k_sum_stage2(const double* __restrict__ part, int nparts, double
     if (threadIdx.x == 0) *out = sh[0];
 }
 
-int reduce_sum(cudaStream_t st, const double* x, int64_t n, int square, double* out, double* part) {
-    k_sum_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(x, n, square, part);
+int reduce_sum(cudaStream_t st, const double* x, int64_t n, double* out, double* part) {
+    k_sum_stage1<<<kRedBlocks, kRedThreads, 0, st>>>(x, n, part);
     k_sum_stage2<<<1, kRedThreads, 0, st>>>(part, kRedBlocks, out);
     VQ_LAUNCH_CHECK("reduce_sum");
     return VELOXQ_OK;
@@ -578,11 +576,11 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     k_dense_bias<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, ising ? 1 : 0, rowsum, colsum, diag,
                                                             lin, d, ctx->bf.as<float>(), absd);
     VQ_LAUNCH_CHECK("dense ingest");
-    VQ_TRY(reduce_sum(st, rowsum, n, 0, scal + 0, part));
-    VQ_TRY(reduce_sum(st, d, n, 0, scal + 1, part));
-    VQ_TRY(reduce_sum(st, absrow, n, 0, scal + 2, part));
-    VQ_TRY(reduce_sum(st, absd, n, 0, scal + 3, part));
-    VQ_TRY(reduce_sum(st, lin, n, 0, scal + 4, part));
+    VQ_TRY(reduce_sum(st, rowsum, n, scal + 0, part));
+    VQ_TRY(reduce_sum(st, d, n, scal + 1, part));
+    VQ_TRY(reduce_sum(st, absrow, n, scal + 2, part));
+    VQ_TRY(reduce_sum(st, absd, n, scal + 3, part));
+    VQ_TRY(reduce_sum(st, lin, n, scal + 4, part));
     double hs[5];
     int herr = 0;
     VQ_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
@@ -711,11 +709,11 @@ int ingest_csr_t(veloxq_ctx* ctx, const int64_t* rph, const int32_t* colh, const
     VQ_TRY(ctx->bf.ensure(sizeof(float) * n));
     k_csr_bias<<<gr, 256, 0, st>>>(n, ising ? 1 : 0, rowsum, diag, lin, d, ctx->bf.as<float>(), absd);
     VQ_LAUNCH_CHECK("csr bias");
-    VQ_TRY(reduce_sum(st, rowsum, n, 0, scal + 0, part));
-    VQ_TRY(reduce_sum(st, d, n, 0, scal + 1, part));
-    VQ_TRY(reduce_sum(st, absrow, n, 0, scal + 2, part));
-    VQ_TRY(reduce_sum(st, absd, n, 0, scal + 3, part));
-    VQ_TRY(reduce_sum(st, lin, n, 0, scal + 4, part));
+    VQ_TRY(reduce_sum(st, rowsum, n, scal + 0, part));
+    VQ_TRY(reduce_sum(st, d, n, scal + 1, part));
+    VQ_TRY(reduce_sum(st, absrow, n, scal + 2, part));
+    VQ_TRY(reduce_sum(st, absd, n, scal + 3, part));
+    VQ_TRY(reduce_sum(st, lin, n, scal + 4, part));
     double hs[5];
     VQ_CUDA(cudaMemcpyAsync(hs, scal, sizeof(hs), cudaMemcpyDeviceToHost, st));
     VQ_CUDA(cudaStreamSynchronize(st));

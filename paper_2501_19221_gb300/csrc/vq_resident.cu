@@ -10,7 +10,7 @@ namespace {
 
 using namespace resident;
 
-KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, bool ell, int method) {
+KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, int ell, int method) {
 #define VQ_PICK_RC(M)                                                           \
     switch (rc) {                                                               \
         case 1: return resident_pick_rc1_m##M(rpt, csr_smem, packed, ell);    \
@@ -127,7 +127,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed,
     a.F_out = F_out;
     a.best_e = best_e;
     a.best_bits = best_bits;
-    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d > 0, rp.method);
+    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d, rp.method);
     if (!fn) return fail(VELOXQ_EUNSUPPORTED, "no resident kernel variant for this plan");
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     fn<<<(unsigned)div_up(R, p.rc), p.threads, p.smem, ctx->stream>>>(a);

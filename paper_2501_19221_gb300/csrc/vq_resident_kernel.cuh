@@ -165,12 +165,15 @@ template <int RC> __device__ __forceinline__ void sign_row(float (&v)[RC]) {
 }
 
 // METHOD: the integrator (veloxq_method). For PA the state buffers hold the
-// analog spins x and the field is of their binarised spins.
-template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, bool ELL, int METHOD>
+// analog spins x and the field is of their binarised spins. ELL: 0, rows in
+// CSR form; 6, six slots per row (Chimera graphs, cubic lattices), a count
+// known here, so the slot loops unroll completely; 1, a.ell_d slots.
+template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, int ELL, int METHOD>
 __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     constexpr bool SIGN = METHOD == vqd::METHOD_PA;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n;
+    const int ELLD = ELL == 6 ? 6 : a.ell_d;   // slots per row (ELL != 0)
     const int T = blockDim.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -190,8 +193,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
 
     // ---- stage constants ----
     for (int i = tid; i < n; i += T) bsh[i] = a.bf[i];
-    if constexpr (ELL) {
-        const int64_t tot = (int64_t)a.ell_d * n;
+    if constexpr (ELL != 0) {
+        const int64_t tot = (int64_t)ELLD * n;
         for (int64_t idx = tid; idx < tot; idx += T) {
             const int p = (int)(idx / n), i = (int)(idx - (int64_t)p * n);
             const int64_t q0 = a.rowptr[i];
@@ -248,10 +251,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
         auto row_field = [&](int i, float (&acc)[RC]) {
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = 0.0f;
-            if constexpr (ELL) {
+            if constexpr (ELL != 0) {
                 // two slots per iteration: both neighbours' loads are in flight together
                 const uint32_t* e = packs + i;
-                for (int p = 0; p < a.ell_d; p += 2, e += 2 * n) {
+#pragma unroll
+                for (int p = 0; p < ELLD; p += 2, e += 2 * n) {
                     const uint32_t e0 = e[0], e1 = e[n];
                     float s0[RC], s1[RC];
                     ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
@@ -288,7 +292,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             for (int r = 0; r < RC; ++r) { acc0[r] = 0.0f; acc1[r] = 0.0f; }
             const uint32_t* e = packs + i;
             const uint32_t* f = packs + i + T;
-            for (int p = 0; p < a.ell_d; p += 2, e += 2 * n, f += 2 * n) {
+#pragma unroll
+            for (int p = 0; p < ELLD; p += 2, e += 2 * n, f += 2 * n) {
                 const uint32_t e0 = e[0], e1 = e[n], f0 = f[0], f1 = f[n];
                 float s0[RC], s1[RC], t0[RC], t1[RC];
                 ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
@@ -343,7 +348,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     if (r0 + r < a.R) a.F_out[(int64_t)(r0 + r) * n + i] = acc[r];
             }
         };
-        constexpr bool PAIRS = ELL && RPT >= 2;
+        constexpr bool PAIRS = ELL != 0 && RPT >= 2;
 #pragma unroll
         for (int q = 0; q < RPT; q += PAIRS ? 2 : 1) {
             const int i = tid + q * T;
@@ -387,10 +392,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     int64_t row[RC];
 #pragma unroll
                     for (int r = 0; r < RC; ++r) row[r] = 0;
-                    if constexpr (ELL) {
+                    if constexpr (ELL != 0) {
                         // integer instances only: 2 Qs is exact from the half value
                         const uint32_t* e = packs + i;
-                        for (int p = 0; p < a.ell_d; ++p, e += n) {
+#pragma unroll
+                        for (int p = 0; p < ELLD; ++p, e += n) {
                             const uint32_t ev = e[0];
                             float sj[RC];
                             ld_row_at<RC>(sc, (int)(ev & 0xFFFFu), sj);
@@ -488,20 +494,21 @@ using KFn = void (*)(const ResArgs);
 
 // 1024-thread CTAs keep at most 8 momenta per thread in registers (64-register
 // cap); 512-thread CTAs up to 32.
-template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, bool ell) {
+template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, int ell_d) {
     constexpr int MAXT = (RC * RPT <= 8) ? 1024 : 512;
     if constexpr (RC * RPT > 32) {
         return nullptr;   // never planned (the momenta do not fit in registers)
     } else {
-        if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, false, METHOD>;
-        if (ell) return k_resident<RC, RPT, true, true, MAXT, true, METHOD>;
-        return packed ? k_resident<RC, RPT, true, true, MAXT, false, METHOD>
-                      : k_resident<RC, RPT, true, false, MAXT, false, METHOD>;
+        if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, 0, METHOD>;
+        if (ell_d == 6) return k_resident<RC, RPT, true, true, MAXT, 6, METHOD>;
+        if (ell_d > 0) return k_resident<RC, RPT, true, true, MAXT, 1, METHOD>;
+        return packed ? k_resident<RC, RPT, true, true, MAXT, 0, METHOD>
+                      : k_resident<RC, RPT, true, false, MAXT, 0, METHOD>;
     }
 }
 
 // the variants of one replica count per CTA and one integrator
-template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, bool ell) {
+template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, int ell) {
     switch (rpt) {
         case 1: return pick_csr<RC, 1, METHOD>(csr_smem, packed, ell);
         case 2: return pick_csr<RC, 2, METHOD>(csr_smem, packed, ell);
@@ -515,7 +522,7 @@ template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, 
 
 // one per replica count per CTA and integrator (vq_resident_*.cu, compiled in parallel)
 #define VQ_RESIDENT_PICK(RC, M) \
-    resident::KFn resident_pick_rc##RC##_m##M(int rpt, bool csr_smem, bool packed, bool ell)
+    resident::KFn resident_pick_rc##RC##_m##M(int rpt, bool csr_smem, bool packed, int ell)
 VQ_RESIDENT_PICK(1, 0); VQ_RESIDENT_PICK(2, 0); VQ_RESIDENT_PICK(4, 0); VQ_RESIDENT_PICK(8, 0);
 VQ_RESIDENT_PICK(1, 1); VQ_RESIDENT_PICK(2, 1); VQ_RESIDENT_PICK(4, 1); VQ_RESIDENT_PICK(8, 1);
 VQ_RESIDENT_PICK(1, 2); VQ_RESIDENT_PICK(2, 2); VQ_RESIDENT_PICK(4, 2); VQ_RESIDENT_PICK(8, 2);

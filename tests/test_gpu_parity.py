@@ -280,6 +280,22 @@ def test_resident_variants_match_stream(B, method, m, R):
     assert np.array_equal(a["x"], b["x"])
 
 
+@pytest.mark.parametrize("method", [0, 2])
+@pytest.mark.parametrize("R", [8, 64])
+def test_resident_runtime_slot_count_matches_stream(B, method, R):
+    """Chimera C_{4,4} with shores of 6 (degree 8: eight slots per row, a
+    count the kernel reads at run time, unlike the six of C_{m,m,4} and the
+    lattices): bitwise the streaming kernel's energies."""
+    sp = I.chimera_ising(4, 4, 6, seed=1)
+    assert np.max(np.diff(sp.rowptr)) == 8
+    ctx = B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+    kw = dict(readout_every=25, method=method, dt=0.3)
+    a = B.veloxq_solve(ctx, R, 120, B.make_schedule(path=1, **kw), seed=5)
+    b = B.veloxq_solve(ctx, R, 120, B.make_schedule(path=2, **kw), seed=5)
+    assert np.array_equal(a["E_per_replica"], b["E_per_replica"])
+    assert np.array_equal(a["x"], b["x"])
+
+
 # ----------------------------------------------------------------- solve
 def test_solve_dense_int20_reaches_ground_state(B):
     ctx, p = inst_dense_int20(B)
