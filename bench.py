@@ -617,6 +617,7 @@ def run_ours(args, rank, world, local_rank):
             mains.append(t.ms_main)
             launches += t.launches
             main_launches, path = t.main_launches, t.path
+            gather = (t.stream_gather, t.stream_chunk) if hasattr(t, "stream_gather") else (0, 0)
         torch.cuda.synchronize()
         wall = time.perf_counter() - wall0
         if dist is not None:
@@ -703,6 +704,7 @@ def run_ours(args, rank, world, local_rank):
             "config": {"workload": w["name"], "instance": w["desc"], "n": n, "nnz_field": run.nnz_field,
                        "replicas": R, "integration_steps": K, "readout_every": w["readout_every"],
                        "path": {1: "resident", 2: "stream", 3: "dense"}.get(path, str(path)),
+                       **({"stream_gather": gather[0], "stream_chunk_replicas": gather[1]} if path == 2 else {}),
                        "method": args.method,
                        "state": "f32", "l2": "flushed by a 256 MiB write before each timed step",
                        "parallelism": f"replicas-only x{world}"},
