@@ -267,6 +267,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     cluster_sync();                              // both CTAs' barriers exist before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // Programmatic dependent launch: everything above (barriers, tensor
+    // memory, the cluster handshake) may overlap the previous kernel on the
+    // stream; nothing it wrote is read before this wait returns. The next
+    // step may then be scheduled, onto SMs this grid frees as it exits (every
+    // CTA of this grid is resident by now, one per SM).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
@@ -612,11 +619,13 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     cfg.blockDim = dim3(320);
     cfg.dynamicSmemBytes = TC_SMEM;
     cfg.stream = ctx->stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 2;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     // as many pairs as can be resident at once (one CTA per SM)
@@ -632,6 +641,7 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     }
     const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles, max_pairs));
     cfg.gridDim = dim3((unsigned)(2 * pairs));
+    cfg.numAttrs = 2;   // with programmatic dependent launch (the occupancy query above used the cluster only)
     VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms_cur, a));
     VQ_LAUNCH_CHECK("tc step");
     return VELOXQ_OK;
