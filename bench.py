@@ -43,6 +43,8 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 282_624,
+    ("k_tc_step", "sk_n8192_fp8"): 179_263_488,
+    ("k_tc_step", "sk_n8192_bf16"): 286_730_752,
     ("k_stream_step", "lattice_l100"): 4_129_237_000,
     ("k_stream_step", "hubo_chain_1e7"): 4_204_906_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 878_414_848,
