@@ -125,6 +125,9 @@ __global__ void k_dense_cols(const T* __restrict__ q, int64_t n, double* colsum)
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double a = 0.0;
+    // one column in row order; unrolled so that many rows' loads are in
+    // flight ahead of the (sequential) additions
+#pragma unroll 16
     for (int64_t i = 0; i < n; ++i)
         if (i != j) a += to_d(q[i * n + j]);
     colsum[j] = a;
@@ -568,7 +571,7 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     k_dense_check<T><<<gb, 256, 0, st>>>(q, total, err);
     if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
     k_dense_rows<T><<<(unsigned)n, 256, 0, st>>>(q, n, rowsum, absrow, diag);
-    k_dense_cols<T><<<(unsigned)div_up(n, 128), 128, 0, st>>>(q, n, colsum);
+    k_dense_cols<T><<<(unsigned)div_up(n, 64), 64, 0, st>>>(q, n, colsum);
     VQ_TRY(ctx->qoff32.ensure(sizeof(float) * (size_t)total));
     dim3 tb(32, 8), tg((unsigned)div_up(n, 32), (unsigned)div_up(n, 32));
     k_dense_qoff<T><<<tg, tb, 0, st>>>(q, n, ctx->qoff32.as<float>());
