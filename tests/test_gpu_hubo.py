@@ -87,3 +87,20 @@ def test_stream_chunked_thread_order(B):
     ref = O.field(p, Ss)
     scale = O.abs_field(p, Ss)
     assert np.all(np.abs(F.cpu().numpy()[rows].astype(np.float64) - ref) <= 1e-5 * scale + 1e-30)
+
+
+def test_stream_chunked_order_bitwise_equal_to_unchunked(B):
+    """Replicas are independent and seeded by index, so the first 64
+    replicas of a 256-replica solve (chunked thread order: 205 MB per state
+    array) and a 64-replica solve (51 MB, never chunked) do the same FP32
+    operations: bitwise the same per-replica energies."""
+    inst = I.xorsat_3r3x(10 ** 5, seed=2)
+    h = inst.hubo
+    red = B.veloxq_hubo3_reduce(h.n, h.h, h.pairs, h.triples)
+    ctx = B.veloxq_create_ising_csr(red["n"], red["rowptr"], red["col"], red["val"], red["lin"])
+    sched = B.make_schedule(path=2, readout_every=10)
+    big = B.veloxq_solve(ctx, 256, 30, sched, seed=7)
+    assert B.veloxq_last_timing(ctx).stream_chunk > 0
+    small = B.veloxq_solve(ctx, 64, 30, sched, seed=7)
+    assert B.veloxq_last_timing(ctx).stream_chunk == 0
+    assert np.array_equal(big["E_per_replica"][:64], small["E_per_replica"])
