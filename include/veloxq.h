@@ -188,7 +188,8 @@ int veloxq_create_ising_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, 
  * distinct indices). Outputs (host, caller-allocated): *n_out = n + n3;
  * rowptr (n + n3 + 1), col and val (capacity 2 (n2 + 6 n3)): the reduced
  * Ising couplings in the CSR form veloxq_create_ising_csr takes (each pair
- * at both positions with the same summed value, columns sorted), *nnz_out
+ * at both positions with the same value, summed in the order of the terms;
+ * columns sorted), *nnz_out
  * the stored entries; lin (n + n3) the reduced fields; *offset the constant,
  * so H_reduced(s, a) = sum_{i<j} J s s + sum lin s + *offset.
  * Errors: EINVAL (bad sizes, indices out of range or repeated within a term,
@@ -197,6 +198,21 @@ int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* p
                         const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj, const int64_t* tk,
                         const double* K3, int64_t* n_out, int64_t* nnz_out, int64_t* rowptr, int32_t* col,
                         double* val, double* lin, double* offset);
+
+/* The same reduction, numbered for locality: the original spins keep their
+ * order, and each is followed by the auxiliary spins of the cubic terms whose
+ * largest index it is (in term order), so that a term's auxiliary spin sits
+ * next to its variables (for the chain of eq. nn: spin i at 2i - 2 from i = 2
+ * on, term q's auxiliary right after spin q + 2). index (host,
+ * caller-allocated, n + n3 entries) receives the reduced index of every spin:
+ * original v at index[v], auxiliary q at index[n + q]; every other output is
+ * veloxq_hubo3_reduce's relabeled by index, bit for bit. Errors: those of
+ * veloxq_hubo3_reduce, and EINVAL for a NULL index. */
+int veloxq_hubo3_reduce_local(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
+                              const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj,
+                              const int64_t* tk, const double* K3, int64_t* n_out, int64_t* nnz_out,
+                              int64_t* rowptr, int32_t* col, double* val, double* lin, double* offset,
+                              int64_t* index);
 
 /* Failure-path self-test of the bounded device waits (the paper has no
  * counterpart; this is a property of the library). Launches one small

@@ -33,7 +33,8 @@ EXPORTED = [
     "veloxq_create_ising_csr", "veloxq_destroy", "veloxq_last_error", "veloxq_get_info", "veloxq_set_stream",
     "veloxq_solve", "veloxq_solve_batch", "veloxq_energy", "veloxq_energy_dev", "veloxq_init_state_dev",
     "veloxq_field_dev", "veloxq_steps_dev", "veloxq_spectral_radius", "veloxq_grad", "veloxq_last_timing",
-    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc", "veloxq_hubo3_reduce", "veloxq_selftest_timeout",
+    "veloxq_batch_state_dev", "veloxq_energy_dev_noalloc", "veloxq_hubo3_reduce", "veloxq_hubo3_reduce_local",
+    "veloxq_selftest_timeout",
 ]
 
 
@@ -93,6 +94,7 @@ def _load():
         "veloxq_batch_state_dev": (I, [P, I32, P, P]),
         "veloxq_energy_dev_noalloc": (I, [P, I64, P, P, P]),
         "veloxq_hubo3_reduce": (I, [I64, P, I64, P, P, P, I64, P, P, P, P, P, P, P, P, P, P, P]),
+        "veloxq_hubo3_reduce_local": (I, [I64, P, I64, P, P, P, I64, P, P, P, P, P, P, P, P, P, P, P, P]),
         "veloxq_selftest_timeout": (I, [I64]),
     }
     for name, (res, args) in sig.items():
@@ -235,11 +237,13 @@ def veloxq_create_ising_csr(n: int, rowptr, col, J, h=None, stream=None) -> Cont
     return Context(out)
 
 
-def veloxq_hubo3_reduce(n: int, h=None, pairs=None, triples=None) -> dict:
+def veloxq_hubo3_reduce(n: int, h=None, pairs=None, triples=None, local: bool = False) -> dict:
     """Third-order Ising cost function -> second order (one auxiliary spin
     per cubic term). pairs = (pi, pj, J), triples = (ti, tj, tk, K). Returns
     n (with the auxiliary spins), rowptr, col, val, lin and offset of the
-    reduced Ising instance, ready for veloxq_create_ising_csr."""
+    reduced Ising instance, ready for veloxq_create_ising_csr. local=True
+    numbers the spins for locality (veloxq_hubo3_reduce_local) and adds
+    "index", the reduced index of every original and auxiliary spin."""
     empty_i, empty_f = np.zeros(0, dtype=np.int64), np.zeros(0, dtype=np.float64)
     pi, pj, J2 = (empty_i, empty_i, empty_f) if pairs is None else pairs
     ti, tj, tk, K3 = (empty_i, empty_i, empty_i, empty_f) if triples is None else triples
@@ -254,12 +258,20 @@ def veloxq_hubo3_reduce(n: int, h=None, pairs=None, triples=None) -> dict:
     val = np.zeros(cap, dtype=np.float64)
     lin = np.zeros(N, dtype=np.float64)
     n_out, nnz_out, off = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
-    _check(_lib.veloxq_hubo3_reduce(n, _ptr(hh), n2, _ptr(pi), _ptr(pj), _ptr(J2), n3, _ptr(ti), _ptr(tj), _ptr(tk),
-                                    _ptr(K3), ctypes.byref(n_out), ctypes.byref(nnz_out), _ptr(rowptr), _ptr(col),
-                                    _ptr(val), _ptr(lin), ctypes.byref(off)))
+    args = (n, _ptr(hh), n2, _ptr(pi), _ptr(pj), _ptr(J2), n3, _ptr(ti), _ptr(tj), _ptr(tk), _ptr(K3),
+            ctypes.byref(n_out), ctypes.byref(nnz_out), _ptr(rowptr), _ptr(col), _ptr(val), _ptr(lin),
+            ctypes.byref(off))
+    index = np.zeros(N, dtype=np.int64) if local else None
+    if local:
+        _check(_lib.veloxq_hubo3_reduce_local(*args, _ptr(index)))
+    else:
+        _check(_lib.veloxq_hubo3_reduce(*args))
     m = nnz_out.value
-    return {"n": n_out.value, "rowptr": rowptr, "col": col[:m].copy(), "val": val[:m].copy(), "lin": lin,
-            "offset": off.value}
+    out = {"n": n_out.value, "rowptr": rowptr, "col": col[:m].copy(), "val": val[:m].copy(), "lin": lin,
+           "offset": off.value}
+    if local:
+        out["index"] = index
+    return out
 
 
 def veloxq_selftest_timeout(budget_cycles: int) -> None:

@@ -15,10 +15,12 @@
 
 using namespace vq;
 
-extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
-                                   const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj,
-                                   const int64_t* tk, const double* K3, int64_t* n_out, int64_t* nnz_out,
-                                   int64_t* rowptr, int32_t* col, double* val, double* lin, double* offset) {
+// The reduction with every spin v (original v < n, auxiliary n + q) stored at
+// index index[v] (a permutation of [0, n + n3)), or at v when index is NULL.
+static int reduce3(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj, const double* J2,
+                   int64_t n3, const int64_t* ti, const int64_t* tj, const int64_t* tk, const double* K3,
+                   int64_t* n_out, int64_t* nnz_out, int64_t* rowptr, int32_t* col, double* val, double* lin,
+                   double* offset, const int64_t* index) {
     if (n < 1 || n2 < 0 || n3 < 0) return fail(VELOXQ_EINVAL, "n >= 1, n2 >= 0 and n3 >= 0 required");
     if ((n2 > 0 && (!pi || !pj || !J2)) || (n3 > 0 && (!ti || !tj || !tk || !K3)))
         return fail(VELOXQ_EINVAL, "term arrays must not be NULL");
@@ -32,7 +34,10 @@ extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const
     };
     std::vector<Pair> pairs;
     pairs.reserve((size_t)(n2 + 6 * n3));
+    auto at = [&](int64_t v) { return index ? index[v] : v; };
     auto add = [&](int64_t a, int64_t b, double v) {
+        a = at(a);
+        b = at(b);
         if (a > b) std::swap(a, b);
         pairs.push_back(Pair{a, b, v});
     };
@@ -42,7 +47,7 @@ extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const
         if (!std::isfinite(J2[q])) return fail(VELOXQ_EINVAL, "pair coupling is not finite");
         add(pi[q], pj[q], J2[q]);
     }
-    for (int64_t i = 0; i < N; ++i) lin[i] = (h && i < n) ? h[i] : 0.0;
+    for (int64_t i = 0; i < N; ++i) lin[at(i)] = (h && i < n) ? h[i] : 0.0;
     for (int64_t i = 0; i < n && h; ++i)
         if (!std::isfinite(h[i])) return fail(VELOXQ_EINVAL, "field h is not finite");
     double off = 0.0;
@@ -55,10 +60,10 @@ extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const
         const double m = std::fabs(K);
         const int64_t a = n + q;   // the auxiliary spin of this term
         off += 3.0 * m;
-        lin[i] += K;               // sgn(K)|K|
-        lin[j] += K;
-        lin[k] += K;
-        lin[a] += 2.0 * K;
+        lin[at(i)] += K;           // sgn(K)|K|
+        lin[at(j)] += K;
+        lin[at(k)] += K;
+        lin[at(a)] += 2.0 * K;
         add(a, i, 2.0 * m);
         add(a, j, 2.0 * m);
         add(a, k, 2.0 * m);
@@ -66,9 +71,11 @@ extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const
         add(j, k, m);
         add(i, k, m);
     }
-    std::sort(pairs.begin(), pairs.end(),
-              [](const Pair& x, const Pair& y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
-    // merge repeated pairs (values summed in the sorted order)
+    // stable: repeated pairs keep the order of the terms that made them, so
+    // their values are summed in that order under any numbering
+    std::stable_sort(pairs.begin(), pairs.end(),
+                     [](const Pair& x, const Pair& y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
+    // merge repeated pairs
     size_t m = 0;
     for (size_t q = 0; q < pairs.size(); ++q) {
         if (m > 0 && pairs[m - 1].a == pairs[q].a && pairs[m - 1].b == pairs[q].b) pairs[m - 1].v += pairs[q].v;
@@ -96,4 +103,42 @@ extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const
     *nnz_out = cnt[(size_t)N];
     *offset = off;
     return VELOXQ_OK;
+}
+
+extern "C" int veloxq_hubo3_reduce(int64_t n, const double* h, int64_t n2, const int64_t* pi, const int64_t* pj,
+                                   const double* J2, int64_t n3, const int64_t* ti, const int64_t* tj,
+                                   const int64_t* tk, const double* K3, int64_t* n_out, int64_t* nnz_out,
+                                   int64_t* rowptr, int32_t* col, double* val, double* lin, double* offset) {
+    return reduce3(n, h, n2, pi, pj, J2, n3, ti, tj, tk, K3, n_out, nnz_out, rowptr, col, val, lin, offset, nullptr);
+}
+
+// The same reduction numbered for locality: the original spins in order,
+// each followed by the auxiliary spins of the cubic terms whose largest index
+// it is (in term order). index[v] is where spin v went.
+extern "C" int veloxq_hubo3_reduce_local(int64_t n, const double* h, int64_t n2, const int64_t* pi,
+                                         const int64_t* pj, const double* J2, int64_t n3, const int64_t* ti,
+                                         const int64_t* tj, const int64_t* tk, const double* K3, int64_t* n_out,
+                                         int64_t* nnz_out, int64_t* rowptr, int32_t* col, double* val, double* lin,
+                                         double* offset, int64_t* index) {
+    if (!index) return fail(VELOXQ_EINVAL, "index must not be NULL");
+    if (n < 1 || n3 < 0) return fail(VELOXQ_EINVAL, "n >= 1 and n3 >= 0 required");
+    if (n3 > 0 && (!ti || !tj || !tk)) return fail(VELOXQ_EINVAL, "term arrays must not be NULL");
+    if (n + n3 > INT32_MAX) return fail(VELOXQ_EINVAL, "n + n3 must fit 32-bit column indices");
+    std::vector<int64_t> anchor((size_t)n3), cnt((size_t)n + 1, 0);
+    for (int64_t q = 0; q < n3; ++q) {
+        const int64_t i = ti[q], j = tj[q], k = tk[q];
+        if (i < 0 || i >= n || j < 0 || j >= n || k < 0 || k >= n)
+            return fail(VELOXQ_EINVAL, "cubic term " + std::to_string(q) + ": indices out of range or repeated");
+        anchor[(size_t)q] = std::max(i, std::max(j, k));
+        ++cnt[(size_t)anchor[(size_t)q] + 1];
+    }
+    // spin v sits after v original spins and the auxiliary spins anchored below v
+    for (int64_t v = 0; v < n; ++v) cnt[(size_t)v + 1] += cnt[(size_t)v];
+    std::vector<int64_t> next((size_t)n);
+    for (int64_t v = 0; v < n; ++v) {
+        index[v] = v + cnt[(size_t)v];
+        next[(size_t)v] = index[v] + 1;
+    }
+    for (int64_t q = 0; q < n3; ++q) index[n + q] = next[(size_t)anchor[(size_t)q]]++;
+    return reduce3(n, h, n2, pi, pj, J2, n3, ti, tj, tk, K3, n_out, nnz_out, rowptr, col, val, lin, offset, index);
 }

@@ -137,3 +137,43 @@ def test_oracle_reduction_pinned_and_equal_to_library(B, kind):
     Jl[rows[up], red["col"][up]] = red["val"][up]
     assert np.allclose(Jl, Jo, rtol=0, atol=1e-12)
     assert np.allclose(red["lin"], lin, rtol=0, atol=1e-12) and red["offset"] == pytest.approx(off, abs=1e-12)
+
+
+@pytest.mark.parametrize("kind", ["chain", "max3sat", "random"])
+def test_local_numbering_is_a_relabeling(B, kind):
+    """veloxq_hubo3_reduce_local is the default reduction with its spins
+    renumbered: index is a permutation, and couplings, fields and offset
+    agree under it; every auxiliary spin comes right after the largest
+    original spin of its term (or after the auxiliaries anchored there)."""
+    if kind == "chain":
+        inst = I.hubo_chain_3body(40, seed=1)
+    elif kind == "max3sat":
+        inst = I.max3sat_weighted(40, seed=2)
+    else:
+        inst = I.xorsat_3r3x(40, seed=3).hubo
+    n = inst.n
+    a = B.veloxq_hubo3_reduce(n, inst.h, inst.pairs, inst.triples)
+    b = B.veloxq_hubo3_reduce(n, inst.h, inst.pairs, inst.triples, local=True)
+    P = b["index"]
+    N = a["n"]
+    assert b["n"] == N and np.array_equal(np.sort(P), np.arange(N))
+    assert b["offset"] == a["offset"]
+    assert np.array_equal(b["lin"][P], a["lin"])
+
+    def dense(r):
+        M = np.zeros((N, N))
+        rows = np.repeat(np.arange(N), np.diff(r["rowptr"]))
+        M[rows, r["col"]] = r["val"]
+        return M
+
+    assert np.array_equal(dense(b)[np.ix_(P, P)], dense(a))
+    ti, tj, tk, _ = inst.triples
+    anchor = np.maximum(np.maximum(ti, tj), tk)
+    orig = P[:n]
+    assert np.all(np.diff(orig) >= 1)                       # originals keep their order
+    assert np.all(P[n:] > orig[anchor])
+    nxt = np.append(orig[1:], N)
+    assert np.all(P[n:] < nxt[anchor])                      # before the next original spin
+    if kind == "chain":
+        q = np.arange(n - 2)
+        assert np.array_equal(P[n:], 2 * q + 3)
