@@ -8,7 +8,7 @@
 // and, for the exact energy of a binary x,
 //   E(x) = sum_i x_i (d_i + sum_{j != i} Qs_ij x_j).
 // Energies are accumulated as int64 multiples of 2^-S (S = energy_shift):
-// exact for integer Q (S = 0 dense, S = 1 sparse, where 2 Qs is an integer)
+// exact for integer Q (S = 1, dense and sparse alike: 2 Qs is an integer)
 // and, for real Q, exact sums of values rounded to 2^-S with S chosen so that
 // no sum can overflow -- order-independent, unlike FP64 summation.
 #include <cub/cub.cuh>
