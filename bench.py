@@ -48,7 +48,7 @@ NCU_TRAFFIC = {
     ("k_stream_step", "lattice_l100"): 4_129_237_000,
     ("k_stream_step", "hubo_chain_1e7"): 3_561_701_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 878_414_848,
-    ("k_batch", "wishart_b512"): 2_757_086_000,
+    ("k_batch", "wishart_b512"): 2_259_262_096,
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes

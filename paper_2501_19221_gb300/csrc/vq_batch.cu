@@ -72,6 +72,20 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
                  ::"r"(su32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
                  : "memory");
 }
+// The same copy marked evict-first in L2: the coupling tiles stream through
+// once per step, and should not push out the replica operand, which every row
+// tile of the instance reads again.
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
+                                                uint64_t pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(su32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(su32(bar)), "l"(pol)
+                 : "memory");
+}
 __device__ __forceinline__ void tcf_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tcf_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ uint64_t sdesc(const void* p) {
@@ -173,6 +187,7 @@ __global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
 
     if (warp == 0) {
         if (lane == 0) {
+            const uint64_t qpol = l2_evict_first_policy();
             uint32_t it = 0, sp = 0;
             bool ok = true;
             for (int w = first; w < last && ok; ++w) {
@@ -191,7 +206,7 @@ __global__ void __launch_bounds__(192, 1) k_batch(const BatchArgs a) {
                             }
                             uint8_t* dst = smem + s * STAGE;
                             mb_expect(&full[s], STAGE);
-                            bulk_g2s(dst, in.qt + (((size_t)mt * in.KT + kt) << 14), A_TILE, &full[s]);
+                            bulk_g2s_stream(dst, in.qt + (((size_t)mt * in.KT + kt) << 14), A_TILE, &full[s], qpol);
                             bulk_g2s(dst + A_TILE, sop + (size_t)kt * B_TILE, B_TILE, &full[s]);
                             ++it;
                         }
