@@ -45,9 +45,6 @@ NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 282_624,
     ("k_tc_step", "sk_n8192_fp8"): 179_263_488,
     ("k_tc_step", "sk_n8192_bf16"): 286_730_752,
-    ("k_stream_step", "lattice_l100"): 4_129_237_000,
-    ("k_stream_step", "hubo_chain_1e7"): 3_561_701_000,
-    ("k_stream_step", "xorsat_3r3x_1e5"): 878_414_848,
     ("k_batch", "wishart_b512"): 2_259_262_096,
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }

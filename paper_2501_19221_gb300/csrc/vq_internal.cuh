@@ -417,6 +417,18 @@ template <int V> __device__ __forceinline__ void vstore(float* p, const float (&
     else if constexpr (V == 2) *reinterpret_cast<float2*>(p) = make_float2(v[0], v[1]);
     else *p = v[0];
 }
+// Streaming forms (evict-first in the caches) for data a step touches once,
+// so that the state the neighbours gather keeps its place in L2.
+template <int V> __device__ __forceinline__ void vload_stream(const float* p, float (&v)[V]) {
+    if constexpr (V == 4) { const float4 t = __ldcs(reinterpret_cast<const float4*>(p)); v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w; }
+    else if constexpr (V == 2) { const float2 t = __ldcs(reinterpret_cast<const float2*>(p)); v[0] = t.x; v[1] = t.y; }
+    else { v[0] = __ldcs(p); }
+}
+template <int V> __device__ __forceinline__ void vstore_stream(float* p, const float (&v)[V]) {
+    if constexpr (V == 4) __stcs(reinterpret_cast<float4*>(p), make_float4(v[0], v[1], v[2], v[3]));
+    else if constexpr (V == 2) __stcs(reinterpret_cast<float2*>(p), make_float2(v[0], v[1]));
+    else __stcs(p, v[0]);
+}
 
 __device__ __forceinline__ float wval(float w) { return w; }
 __device__ __forceinline__ float wval(int8_t w) { return (float)w; }

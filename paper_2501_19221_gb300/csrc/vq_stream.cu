@@ -16,6 +16,8 @@ namespace {
 
 using vqd::vload;
 using vqd::vload_plain;
+using vqd::vload_stream;
+using vqd::vstore_stream;
 using vqd::vstore;
 using vqd::wval;
 
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
     float s[V], y[V], b = 0.0f, a_k = 0.0f;
     if constexpr (!FIELD_ONLY) {
         vload<V>(S_cur + me, s);
-        vload_plain<V>(Y_in + me, y);
+        vload_stream<V>(Y_in + me, y);
         b = __ldg(bf + i);
         a_k = __ldg(a_table + k);
     }
@@ -79,8 +81,8 @@ __global__ void __launch_bounds__(256) k_stream_step(int64_t n, int32_t R, int32
 #pragma unroll
         for (int l = 0; l < V; ++l) vqd::step_update(method, F[l], b, a_k, lam, dt, a0, c0, alpha, s[l], y[l]);
     }
-    vstore<V>(S_nxt + me, s);
-    vstore<V>(Y_out + me, y);
+    vstore_stream<V>(S_nxt + me, s);
+    vstore_stream<V>(Y_out + me, y);
 }
 
 __device__ __forceinline__ int64_t ewval(int8_t w) { return (int64_t)w; }
