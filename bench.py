@@ -43,6 +43,9 @@ L2_FLUSH_BYTES = 256 << 20          # > 129 MB of L2
 # changes after its capture must be removed from this table.
 NCU_TRAFFIC = {
     ("k_resident", "chimera_c16"): 282_624,
+    ("k_stream_step", "lattice_l100"): 4_104_791_000,
+    ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
+    ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_tc_step", "sk_n8192_fp8"): 179_263_488,
     ("k_tc_step", "sk_n8192_bf16"): 286_730_752,
     ("k_batch", "wishart_b512"): 2_259_262_096,
