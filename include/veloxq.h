@@ -59,11 +59,25 @@ typedef enum {
 typedef enum { VELOXQ_I8 = 0, VELOXQ_I32 = 1, VELOXQ_F32 = 2, VELOXQ_F64 = 3 } veloxq_vtype;
 
 /* Operand precision of the dense local-field product F = Qoff S. FP32 runs on
- * the CUDA cores; BF16 and FP8 (E4M3 with one FP32 scale per row of Qoff and
- * the fixed scale 448 for S, whose entries the walls keep in [-1, 1]) run on
- * the tcgen05 tensor cores; all accumulate in FP32. Sparse contexts always
- * use FP32 (or exact int8 couplings). */
-typedef enum { VELOXQ_PREC_FP32 = 0, VELOXQ_PREC_BF16 = 1, VELOXQ_PREC_FP8 = 2 } veloxq_prec;
+ * the CUDA cores; the others run on the tcgen05 tensor cores; all accumulate
+ * in FP32. Sparse contexts always use FP32 (or exact int8 couplings).
+ *   BF16:          bf16(Qoff) x bf16(s).
+ *   FP8:           Qoff as E4M3 with one FP32 scale per row (amax_i / 448);
+ *                  S (whose entries the walls keep in [-1, 1]) with the fixed
+ *                  scale 448 as two E4M3 terms, v = 448 s, hi = e4m3(v),
+ *                  lo = e4m3(v - hi), both multiplied by the same Qoff operand
+ *                  into one FP32 accumulator. The field's error is then that of
+ *                  Qoff's rounding (about 2.7% normwise on Gaussian couplings).
+ *   FP8_ONE_TERM:  the same with S as hi alone: half the tensor-core work, but
+ *                  both operands rounded to 4 significant bits (about 3.7%
+ *                  normwise). Parallel Annealing's operand (+-1) is exact in one
+ *                  term, so FP8 runs it this way too. */
+typedef enum {
+    VELOXQ_PREC_FP32 = 0,
+    VELOXQ_PREC_BF16 = 1,
+    VELOXQ_PREC_FP8 = 2,
+    VELOXQ_PREC_FP8_ONE_TERM = 3
+} veloxq_prec;
 
 /* Kernel path selection (VELOXQ_PATH_AUTO picks by size and format). */
 typedef enum {
@@ -81,7 +95,7 @@ typedef enum {
  *   ASB: adiabatic simulated bifurcation as App. B prints it (quartic
  *        potential, no walls). o = s;
  *        y <- y + dt(-(s^2 + a0 - a_k) s + c0 phi), s <- s + dt a0 y.
- *        Not available with VELOXQ_PREC_FP8 (|s| is unbounded).
+ *        Not available with the FP8 precisions (|s| is unbounded).
  *   PA:  Parallel Annealing (App. B): s holds the analog spins x, y the
  *        momenta m; o = sign(s) (+1 where s > 0, else -1);
  *        g = lambda_k s - c0 phi with lambda_k = (a0 - a_k)/a0,
@@ -320,9 +334,10 @@ int veloxq_energy_dev_noalloc(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, 
 /* Philox initial state S, Y [R][n] for seed and sigma0 (same draw as solve). */
 int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, float* S, float* Y);
 
-/* Local field F = Qoff S for S [R][n] in the given operand precision (FP8 also
- * quantises S with one scale per replica). Errors: EUNSUPPORTED for BF16/FP8
- * on a sparse context. */
+/* Local field F = Qoff S for S [R][n] in the given operand precision (the FP8
+ * forms quantise S with the fixed scale 448, so S must lie in [-1, 1]; FP8
+ * takes two E4M3 terms of S, FP8_ONE_TERM one). Errors: EUNSUPPORTED for
+ * BF16/FP8 on a sparse context. */
 int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F);
 
 /* Advance S, Y [R][n] in place by steps k_begin .. k_begin+k_count-1 of a

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libveloxq.so")
 
 VELOXQ_OK, VELOXQ_EINVAL, VELOXQ_ENOMEM, VELOXQ_ECUDA, VELOXQ_ETIMEDOUT, VELOXQ_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
 VELOXQ_I8, VELOXQ_I32, VELOXQ_F32, VELOXQ_F64 = 0, 1, 2, 3
-VELOXQ_PREC_FP32, VELOXQ_PREC_BF16, VELOXQ_PREC_FP8 = 0, 1, 2
+VELOXQ_PREC_FP32, VELOXQ_PREC_BF16, VELOXQ_PREC_FP8, VELOXQ_PREC_FP8_ONE_TERM = 0, 1, 2, 3
 VELOXQ_PATH_AUTO, VELOXQ_PATH_RESIDENT, VELOXQ_PATH_STREAM, VELOXQ_PATH_DENSE = 0, 1, 2, 3
 VELOXQ_METHOD_BSB, VELOXQ_METHOD_ASB, VELOXQ_METHOD_PA = 0, 1, 2
 

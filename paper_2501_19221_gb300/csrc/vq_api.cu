@@ -87,12 +87,12 @@ int resolve(const veloxq_ctx* ctx, const veloxq_schedule* s_in, int32_t K, RunPa
     if (!(std::isfinite(s.sigma0) && s.sigma0 >= 0)) return fail(VELOXQ_EINVAL, "schedule sigma0 must be finite and >= 0");
     if (s.n_knots < 0 || (s.n_knots > 0 && !s.a_knots)) return fail(VELOXQ_EINVAL, "schedule knots: n_knots < 0 or a_knots NULL");
     if (s.readout_every < 0) return fail(VELOXQ_EINVAL, "schedule readout_every must be >= 0");
-    if (s.prec < VELOXQ_PREC_FP32 || s.prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
+    if (s.prec < VELOXQ_PREC_FP32 || s.prec > VELOXQ_PREC_FP8_ONE_TERM) return fail(VELOXQ_EINVAL, "unknown precision");
     if (s.path < VELOXQ_PATH_AUTO || s.path > VELOXQ_PATH_DENSE) return fail(VELOXQ_EINVAL, "unknown path");
     if (s.method < VELOXQ_METHOD_BSB || s.method > VELOXQ_METHOD_PA) return fail(VELOXQ_EINVAL, "unknown method");
     if (!(std::isfinite(s.momentum) && s.momentum >= 0 && s.momentum < 1))
         return fail(VELOXQ_EINVAL, "schedule momentum must be in [0, 1)");
-    if (s.method == VELOXQ_METHOD_ASB && s.prec == VELOXQ_PREC_FP8)
+    if (s.method == VELOXQ_METHOD_ASB && (s.prec == VELOXQ_PREC_FP8 || s.prec == VELOXQ_PREC_FP8_ONE_TERM))
         return fail(VELOXQ_EUNSUPPORTED, "adiabatic SB leaves [-1, 1]: no FP8 operand with a fixed scale");
     p->dt = s.dt;
     p->a0 = s.a0;
@@ -163,15 +163,19 @@ int check_path(const veloxq_ctx* ctx, veloxq_path path, veloxq_prec prec, int32_
     return VELOXQ_OK;
 }
 
-// Tensor-core operands of one run: quantised Q, two S operand buffers, maps.
+// Tensor-core operands of one run: quantised Q, two S operand buffers (each
+// holding `terms` planes), maps (ms_lo: the lo planes of two-term FP8).
 struct TcRun {
-    CUtensorMap mq, ms[2];
+    CUtensorMap mq, ms[2], ms_lo[2];
     void* sop[2];
+    int terms = 1;
+    const CUtensorMap* lo(int c) const { return terms == 2 ? &ms_lo[c] : nullptr; }
 };
 
-int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t) {
+int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t, int method = VELOXQ_METHOD_BSB) {
     VQ_TRY(tc_prepare_q(ctx, prec));
-    const size_t b = tc_sop_bytes(ctx, prec, R);
+    t->terms = tc_terms(prec, method);
+    const size_t b = tc_sop_bytes(ctx, prec, t->terms, R);
     VQ_TRY(ctx->sop_a.ensure(b));
     VQ_TRY(ctx->sop_b.ensure(b));
     VQ_TRY(ctx->errw.ensure(sizeof(int) * 4));
@@ -181,7 +185,8 @@ int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t) {
     VQ_CUDA(cudaMemsetAsync(ctx->sop_b.p, 0, b, ctx->stream));
     t->sop[0] = ctx->sop_a.p;
     t->sop[1] = ctx->sop_b.p;
-    return tc_maps(ctx, prec, R, t->sop[0], t->sop[1], &t->mq, &t->ms[0], &t->ms[1]);
+    return tc_maps(ctx, prec, t->terms, R, t->sop[0], t->sop[1], &t->mq, &t->ms[0], &t->ms[1], &t->ms_lo[0],
+                   &t->ms_lo[1]);
 }
 
 int check_err_word(veloxq_ctx* ctx) {
@@ -211,8 +216,8 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
     for (int k = 0; k < p.K; ++k) {
         if (tc) {
             const int c = k & 1;   // operand of this step in sop[c], next one into sop[c ^ 1]
-            VQ_TRY(tc_step(ctx, p.prec, R, tc->mq, tc->ms[c], cur, nxt, Y, tc->sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
-                           nullptr, ctx->errw.as<int>(), rule_of(p)));
+            VQ_TRY(tc_step(ctx, p.prec, R, tc->mq, tc->ms[c], tc->lo(c), cur, nxt, Y, tc->sop[c ^ 1], at, k, p.dt,
+                           p.a0, p.c0, nullptr, ctx->errw.as<int>(), rule_of(p)));
         } else if (path == VELOXQ_PATH_DENSE) {
             VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr, rule_of(p)));
         } else {
@@ -440,7 +445,7 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
             VQ_TRY(stream_autotune(ctx, replicas, ctx->s_a.as<float>(), ctx->s_b.as<float>(), ctx->y.as<float>()));
         TcRun tc;
         const bool use_tc = path == VELOXQ_PATH_DENSE && p.prec != VELOXQ_PREC_FP32;
-        if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc));
+        if (use_tc) VQ_TRY(tc_setup(ctx, p.prec, replicas, &tc, p.method));
         if (path == VELOXQ_PATH_DENSE && !use_tc) VQ_TRY(dense_prepare(ctx, replicas));
         if (path == VELOXQ_PATH_DENSE) VQ_TRY(tc_energy_prepare(ctx, replicas));
         const bool tc_e = path == VELOXQ_PATH_DENSE && tc_energy_ready(ctx, replicas);
@@ -683,15 +688,15 @@ int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma
 int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
     if (R < 1 || R > kMaxReplicas || !S || !F) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, F required");
-    if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8) return fail(VELOXQ_EINVAL, "unknown precision");
+    if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8_ONE_TERM) return fail(VELOXQ_EINVAL, "unknown precision");
     if (ctx->dense) {
         if (prec == VELOXQ_PREC_FP32) return dense_field(ctx, R, S, F);
         TcRun tc;
         VQ_TRY(tc_setup(ctx, prec, R, &tc));
         VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
         VQ_TRY(tc_quant_s(ctx, prec, R, S, tc.sop[0]));
-        VQ_TRY(tc_step(ctx, prec, R, tc.mq, tc.ms[0], S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f, 0.f, F,
-                       ctx->errw.as<int>()));
+        VQ_TRY(tc_step(ctx, prec, R, tc.mq, tc.ms[0], tc.lo(0), S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f,
+                       0.f, F, ctx->errw.as<int>()));
         return check_err_word(ctx);
     }
     if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "sparse contexts run the field in FP32 (or exact int8)");
@@ -728,13 +733,13 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
         VQ_CUDA(cudaMemcpyAsync(cur, S, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
         if (p.prec != VELOXQ_PREC_FP32) {
             TcRun tc;
-            VQ_TRY(tc_setup(ctx, p.prec, R, &tc));
+            VQ_TRY(tc_setup(ctx, p.prec, R, &tc, p.method));
             VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
             VQ_TRY(tc_quant_s(ctx, p.prec, R, cur, tc.sop[0], rule_of(p)));
             int c = 0;
             for (int k = k_begin; k < k_end; ++k) {
-                VQ_TRY(tc_step(ctx, p.prec, R, tc.mq, tc.ms[c], cur, nxt, Y, tc.sop[c ^ 1], at, k, p.dt, p.a0, p.c0,
-                               k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>(), rule_of(p)));
+                VQ_TRY(tc_step(ctx, p.prec, R, tc.mq, tc.ms[c], tc.lo(c), cur, nxt, Y, tc.sop[c ^ 1], at, k, p.dt,
+                               p.a0, p.c0, k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>(), rule_of(p)));
                 std::swap(cur, nxt);
                 c ^= 1;
             }

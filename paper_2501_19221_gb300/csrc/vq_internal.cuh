@@ -200,15 +200,17 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
 
 // dense tensor-core kernels (vq_tc.cu)
 int64_t tc_pad(int64_t n);
+int tc_terms(int prec, int method);   // E4M3 terms of the S operand (2 for FP8 unless the operand is exact)
 int tc_prepare_q(veloxq_ctx* ctx, int prec);
-int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtensorMap* mq, CUtensorMap* ms0,
-            CUtensorMap* ms1);
+int tc_maps(veloxq_ctx* ctx, int prec, int terms, int32_t R, void* sop0, void* sop1, CUtensorMap* mq,
+            CUtensorMap* ms0, CUtensorMap* ms1, CUtensorMap* ms0_lo, CUtensorMap* ms1_lo);
 int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule = Rule());
-size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R);
+size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int terms, int32_t R);
 int tc_wait_selftest(long long budget, int* code_out);   // the bounded wait run out on purpose
-int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
-            float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
-            float* F_out, int* err, const Rule& rule = Rule());
+int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur,
+            const CUtensorMap* ms_lo_cur, const float* S_cur, float* S_nxt, float* Y, void* sop_nxt,
+            const float* a_table, int k, float dt, float a0, float c0, float* F_out, int* err,
+            const Rule& rule = Rule());
 int tc_operand_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, bool a_operand);
 int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
 

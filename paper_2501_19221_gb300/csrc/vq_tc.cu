@@ -7,13 +7,21 @@
 // replica-major), 128-byte K blocks with the 128-byte swizzle.
 // CTA pairs (clusters of 2, tcgen05 cta_group::2): a pair computes a
 // 256 x 256 tile with M = 256 MMAs issued by the even CTA. Each CTA stages
-// its own 128 rows of Qoff and its own 128 replicas of S, so a stage is
-// 32 KB per CTA and 6 stages are in flight; each CTA's tensor memory holds
-// the accumulator of its 128 rows for all 256 replicas.
+// its own 128 rows of Qoff and its own 128 replicas of S; each CTA's tensor
+// memory holds the accumulator of its 128 rows for all 256 replicas.
 //   BF16: Qop = bf16(Qoff), Sop = bf16(s)                (kind::f16)
-//   FP8 : Qop = e4m3(Qoff_ij / q_i), q_i = amax_i / 448,
-//         Sop = e4m3(448 s)  (|s| <= 1 by the walls)       (kind::f8f6f4)
+//   FP8 : Qop = e4m3(Qoff_ij / q_i), q_i = amax_i / 448  (kind::f8f6f4)
+//         S in two E4M3 terms of the same scale (TERMS = 2):
+//           v = 448 s (|s| <= 1 by the walls), hi = e4m3(v), lo = e4m3(v - hi)
+//         (v - hi is exact in FP32), so S carries about 7 significant bits
+//         and the product's error is that of Q's rounding alone; both terms
+//         are multiplied by the same Qop tile and accumulate into the same
+//         FP32 accumulator, acc = Qop hi + Qop lo.
+//         One term (TERMS = 1): Sop = hi only (VELOXQ_PREC_FP8_ONE_TERM, and
+//         Parallel Annealing, whose operand +-448 is exact so lo = 0).
 //         F_i = acc q_i / 448
+// A stage is 32 KB per CTA with one S term (6 stages in flight) and 48 KB
+// with two (4 stages); both fill 192 KB of shared memory.
 // The kernel is persistent: one CTA per SM, the pairs walk the pair tiles
 // t = pair, + pairs, ...; two accumulator buffers in tensor memory let the
 // epilogue of one tile overlap the main loop of the next.
@@ -26,6 +34,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include <algorithm>
@@ -37,9 +46,14 @@ namespace vq {
 namespace {
 
 // BM rows per CTA (2 BM per pair), BN replicas per pair (BN / 2 staged per CTA)
-constexpr int BM = 128, BN = 256, BNH = BN / 2, BKB = 128, STAGES = 6;
-constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BNH * BKB, STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr size_t TC_SMEM = (size_t)STAGES * STAGE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
+constexpr int BM = 128, BN = 256, BNH = BN / 2, BKB = 128;
+constexpr uint32_t A_BYTES = BM * BKB, B_BYTES = BNH * BKB;
+// a stage holds the Qop block and TERMS blocks of Sop
+template <int TERMS> constexpr uint32_t stage_bytes() { return A_BYTES + TERMS * B_BYTES; }
+template <int TERMS> constexpr int stages_of() { return TERMS == 2 ? 4 : 6; }
+constexpr uint32_t PIPE_BYTES = 6 * stage_bytes<1>();
+static_assert(stages_of<2>() * stage_bytes<2>() == PIPE_BYTES, "both stage forms fill the same 192 KB");
+constexpr size_t TC_SMEM = (size_t)PIPE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
 enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4, TC_ERR_SELFTEST = 8 };
@@ -212,22 +226,36 @@ struct TcArgs {
     float* F_out;            // [R][n] or null
     int* err;
     float alpha;             // PA momentum
+    int64_t plane;           // elements from the hi plane of sop_nxt to its lo plane (two S terms)
 };
 
-template <int PREC> __device__ __forceinline__ void store_op(void* base, int64_t idx, float s) {
+// Operand of s: bf16(s); or v = 448 s as hi = e4m3(v) and, with two terms,
+// lo = e4m3(v - hi) at idx + plane (v - hi is exact in FP32).
+template <int PREC, int TERMS>
+__device__ __forceinline__ void store_op(void* base, int64_t idx, int64_t plane, float s) {
     if constexpr (PREC == 1) {
         reinterpret_cast<__nv_bfloat16*>(base)[idx] = __float2bfloat16_rn(s);
     } else {
-        reinterpret_cast<__nv_fp8_storage_t*>(base)[idx] =
-            __nv_cvt_float_to_fp8(448.0f * s, __NV_SATFINITE, __NV_E4M3);
+        __nv_fp8_storage_t* o = reinterpret_cast<__nv_fp8_storage_t*>(base);
+        const float v = __fmul_rn(448.0f, s);
+        const __nv_fp8_storage_t hi = __nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+        o[idx] = hi;
+        if constexpr (TERMS == 2) {
+            const float hf = __half2float(__half(__nv_cvt_fp8_to_halfraw(hi, __NV_E4M3)));
+            o[idx + plane] = __nv_cvt_float_to_fp8(__fsub_rn(v, hf), __NV_SATFINITE, __NV_E4M3);
+        }
     }
 }
 
 // METHOD: the integrator (veloxq_method), a template parameter so that each
-// form keeps its own register allocation.
-template <int PREC, bool FIELD_ONLY, int METHOD>
+// form keeps its own register allocation. TERMS: S operand terms (1, or 2 for
+// FP8 hi + lo; tmB2 maps the lo plane, unused with one term).
+template <int PREC, int TERMS, bool FIELD_ONLY, int METHOD>
 __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmB, const TcArgs a) {
+                                                    const __grid_constant__ CUtensorMap tmB,
+                                                    const __grid_constant__ CUtensorMap tmB2, const TcArgs a) {
+    constexpr int STAGES = stages_of<TERMS>();
+    constexpr uint32_t STAGE_BYTES = stage_bytes<TERMS>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);   // even CTA: both stages landed
@@ -290,6 +318,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     const uint32_t fb = mapa(smem_u32(&full[s]), 0);
                     tma_load_2d_pair(sa, &tmA, kb * BK, m0, fb);
                     tma_load_2d_pair(sa + A_BYTES, &tmB, kb * BK, n0, fb);
+                    if constexpr (TERMS == 2) tma_load_2d_pair(sa + A_BYTES + B_BYTES, &tmB2, kb * BK, n0, fb);
                     ++it;
                 }
             }
@@ -310,9 +339,13 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                     tc_fence_after();
                     const uint8_t* sa = smem + s * STAGE_BYTES;
 #pragma unroll
-                    for (int kk = 0; kk < BKB / KSTEP_B; ++kk)
-                        umma<PREC>(d, smem_desc(sa + kk * KSTEP_B), smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc,
-                                   (kb | kk) != 0 ? 1u : 0u);
+                    for (int kk = 0; kk < BKB / KSTEP_B; ++kk) {
+                        const uint64_t da = smem_desc(sa + kk * KSTEP_B);
+                        umma<PREC>(d, da, smem_desc(sa + A_BYTES + kk * KSTEP_B), idesc, (kb | kk) != 0 ? 1u : 0u);
+                        // the lo term of S against the same Qop slice, into the same accumulator
+                        if constexpr (TERMS == 2)
+                            umma<PREC>(d, da, smem_desc(sa + A_BYTES + B_BYTES + kk * KSTEP_B), idesc, 1u);
+                    }
                     umma_commit_pair(&empty[s]);
                     ++it;
                 }
@@ -376,8 +409,8 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                         if (ok) {
                             a.S_nxt[p] = s;
                             a.Y[p] = y;
-                            store_op<PREC>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row,
-                                           METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
+                            store_op<PREC, TERMS>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row, a.plane,
+                                                  METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
                         }
                     }
                 }
@@ -449,12 +482,12 @@ __global__ void k_quant_q_fp8(int64_t n, int64_t n_pad, const float* __restrict_
     if (threadIdx.x == 0) scale[i] = sc;
 }
 
-template <int PREC>
+template <int PREC, int TERMS>
 __global__ void k_quant_s(int64_t R, int64_t n, int64_t n_pad, const float* __restrict__ S, void* out, int method) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= R * n_pad) return;
     const int64_t r = t / n_pad, j = t - r * n_pad;
-    store_op<PREC>(out, t, j < n ? vqd::field_operand(method, S[r * n + j]) : 0.0f);
+    store_op<PREC, TERMS>(out, t, R * n_pad, j < n ? vqd::field_operand(method, S[r * n + j]) : 0.0f);
 }
 
 // ---- tensor maps ------------------------------------------------------------
@@ -488,17 +521,13 @@ int make_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, 
 
 }  // namespace
 
-// ---- state kept per context ------------------------------------------------
-struct TcState {
-    int prec = 0;
-    int64_t n_pad = 0;
-    CUtensorMap mapQ;
-    int32_t R = 0;
-    void* sop[2] = {nullptr, nullptr};
-    CUtensorMap mapS[2];
-};
-
 int64_t tc_pad(int64_t n) { return (n + 15) / 16 * 16; }
+
+// S operand terms: two E4M3 terms for FP8 (hi + lo), one for FP8_ONE_TERM,
+// BF16, and for Parallel Annealing, whose operand +-1 is exact in one term.
+int tc_terms(int prec, int method) {
+    return prec == VELOXQ_PREC_FP8 && method != VELOXQ_METHOD_PA ? 2 : 1;
+}
 
 // Quantise Qoff once per precision (kept in the context).
 int tc_prepare_q(veloxq_ctx* ctx, int prec) {
@@ -521,24 +550,33 @@ int tc_prepare_q(veloxq_ctx* ctx, int prec) {
     return VELOXQ_OK;
 }
 
-// Tensor maps for Q and for the two S operand buffers (bufs: 2 x R x n_pad).
-int tc_maps(veloxq_ctx* ctx, int prec, int32_t R, void* sop0, void* sop1, CUtensorMap* mq, CUtensorMap* ms0,
-            CUtensorMap* ms1) {
+// Tensor maps for Q and for the two S operand buffers (each R x n_pad per
+// term; with two terms the lo plane follows the hi plane, and ms*_lo map it).
+int tc_maps(veloxq_ctx* ctx, int prec, int terms, int32_t R, void* sop0, void* sop1, CUtensorMap* mq,
+            CUtensorMap* ms0, CUtensorMap* ms1, CUtensorMap* ms0_lo, CUtensorMap* ms1_lo) {
     const int64_t n = ctx->n, np = tc_pad(n);
     void* qb = prec == VELOXQ_PREC_BF16 ? ctx->qoff16.p : ctx->qoff8.p;
     VQ_TRY(make_map(mq, qb, prec, n, np, BM));
+    const size_t plane = (size_t)R * (size_t)np * (prec == VELOXQ_PREC_BF16 ? 2 : 1);
     VQ_TRY(make_map(ms0, sop0, prec, R, np, BNH));
-    if (sop1) VQ_TRY(make_map(ms1, sop1, prec, R, np, BNH));
+    if (terms == 2) VQ_TRY(make_map(ms0_lo, static_cast<uint8_t*>(sop0) + plane, prec, R, np, BNH));
+    if (sop1) {
+        VQ_TRY(make_map(ms1, sop1, prec, R, np, BNH));
+        if (terms == 2) VQ_TRY(make_map(ms1_lo, static_cast<uint8_t*>(sop1) + plane, prec, R, np, BNH));
+    }
     return VELOXQ_OK;
 }
 
 int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule) {
     const int64_t n = ctx->n, np = tc_pad(n);
     const int64_t total = (int64_t)R * np;
+    const unsigned blocks = (unsigned)div_up(total, 256);
     if (prec == VELOXQ_PREC_BF16)
-        k_quant_s<1><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
+        k_quant_s<1, 1><<<blocks, 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
+    else if (tc_terms(prec, rule.method) == 2)
+        k_quant_s<2, 2><<<blocks, 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
     else
-        k_quant_s<2><<<(unsigned)div_up(total, 256), 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
+        k_quant_s<2, 1><<<blocks, 256, 0, ctx->stream>>>(R, n, np, S, sop, rule.method);
     VQ_LAUNCH_CHECK("tc quantize S");
     return VELOXQ_OK;
 }
@@ -565,15 +603,38 @@ int tc_wait_selftest(long long budget, int* code_out) {
     return VELOXQ_OK;
 }
 
-size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int32_t R) {
-    return (size_t)R * (size_t)tc_pad(ctx->n) * (prec == VELOXQ_PREC_BF16 ? 2 : 1);
+size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int terms, int32_t R) {
+    return (size_t)terms * (size_t)R * (size_t)tc_pad(ctx->n) * (prec == VELOXQ_PREC_BF16 ? 2 : 1);
 }
 
+namespace {
+using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const TcArgs);
+
+template <int PREC, int TERMS> TcKernel pick_kernel(bool field_only, int method) {
+    if (field_only) return k_tc_step<PREC, TERMS, true, 0>;
+    if (method == VELOXQ_METHOD_PA) return k_tc_step<PREC, TERMS, false, vqd::METHOD_PA>;
+    if (method == VELOXQ_METHOD_ASB) return k_tc_step<PREC, TERMS, false, vqd::METHOD_ASB>;
+    return k_tc_step<PREC, TERMS, false, vqd::METHOD_BSB>;
+}
+
+// SMs and co-resident CTA pairs of the step kernel, per device
+struct TcDevice {
+    int sms = 0, max_pairs = 0;
+};
+constexpr int kMaxDevices = 64;
+TcDevice g_tcdev[kMaxDevices];
+}  // namespace
+
 // One fused step (or the field only when S_nxt is null): reads Sop through
-// mapS_cur, writes the next operand into sop_nxt.
-int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur, const float* S_cur,
-            float* S_nxt, float* Y, void* sop_nxt, const float* a_table, int k, float dt, float a0, float c0,
-            float* F_out, int* err, const Rule& rule) {
+// mapS_cur (and its lo plane through ms_lo_cur with two terms), writes the
+// next operand into sop_nxt.
+int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur,
+            const CUtensorMap* ms_lo_cur, const float* S_cur, float* S_nxt, float* Y, void* sop_nxt,
+            const float* a_table, int k, float dt, float a0, float c0, float* F_out, int* err, const Rule& rule) {
+    const bool field_only = S_nxt == nullptr;
+    // the field alone takes s itself as the operand
+    const int terms = tc_terms(prec, field_only ? VELOXQ_METHOD_BSB : rule.method);
+    if (terms == 2 && !ms_lo_cur) return fail(VELOXQ_EINVAL, "two-term FP8 operand without its lo-plane map");
     TcArgs a;
     a.n = (int32_t)ctx->n;
     a.R = R;
@@ -592,28 +653,15 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     a.F_out = F_out;
     a.err = err;
     a.alpha = rule.alpha;
-    // persistent: one CTA per SM in clusters of two (at most one pair per
-    // pair tile), pair tiles strided over the pairs
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        VQ_CUDA(cudaGetDevice(&dev));
-        VQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    }
+    a.plane = (int64_t)R * a.n_pad;
+    if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(VELOXQ_EUNSUPPORTED, "device ordinal out of range");
+    TcDevice& dv = g_tcdev[ctx->device];
+    if (!dv.sms) VQ_CUDA(cudaDeviceGetAttribute(&dv.sms, cudaDevAttrMultiProcessorCount, ctx->device));
     const int64_t tiles = div_up(ctx->n, 2 * BM) * div_up(R, BN);
-    const bool field_only = S_nxt == nullptr;
-    void (*fn)(const CUtensorMap, const CUtensorMap, const TcArgs);
-    if (prec == VELOXQ_PREC_BF16) {
-        fn = field_only                                  ? k_tc_step<1, true, 0>
-             : rule.method == VELOXQ_METHOD_PA ? k_tc_step<1, false, vqd::METHOD_PA>
-             : rule.method == VELOXQ_METHOD_ASB ? k_tc_step<1, false, vqd::METHOD_ASB>
-                                                : k_tc_step<1, false, vqd::METHOD_BSB>;
-    } else {
-        fn = field_only                                  ? k_tc_step<2, true, 0>
-             : rule.method == VELOXQ_METHOD_PA ? k_tc_step<2, false, vqd::METHOD_PA>
-             : rule.method == VELOXQ_METHOD_ASB ? k_tc_step<2, false, vqd::METHOD_ASB>
-                                                : k_tc_step<2, false, vqd::METHOD_BSB>;
-    }
+    TcKernel fn;
+    if (prec == VELOXQ_PREC_BF16) fn = pick_kernel<1, 1>(field_only, rule.method);
+    else if (terms == 2) fn = pick_kernel<2, 2>(field_only, rule.method);
+    else fn = pick_kernel<2, 1>(field_only, rule.method);
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TC_SMEM));
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(320);
@@ -628,21 +676,22 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    // as many pairs as can be resident at once (one CTA per SM)
-    static int max_pairs = 0;
-    if (!max_pairs) {
-        cfg.gridDim = dim3((unsigned)(sms & ~1));
+    // as many pairs as can be resident at once (one CTA per SM; every form
+    // has the same block size and shared memory)
+    if (!dv.max_pairs) {
+        cfg.gridDim = dim3((unsigned)(dv.sms & ~1));
         int c = 0;
         if (cudaOccupancyMaxActiveClusters(&c, fn, &cfg) != cudaSuccess || c < 1) {
             cudaGetLastError();
-            c = sms / 2;
+            c = dv.sms / 2;
         }
-        max_pairs = std::min(c, sms / 2);
+        dv.max_pairs = std::min(c, dv.sms / 2);
     }
-    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles, max_pairs));
+    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles, dv.max_pairs));
     cfg.gridDim = dim3((unsigned)(2 * pairs));
     cfg.numAttrs = 2;   // with programmatic dependent launch (the occupancy query above used the cluster only)
-    VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms_cur, a));
+    const CUtensorMap& lo = terms == 2 ? *ms_lo_cur : ms_cur;
+    VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms_cur, lo, a));
     VQ_LAUNCH_CHECK("tc step");
     return VELOXQ_OK;
 }

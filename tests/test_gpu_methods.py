@@ -158,23 +158,31 @@ def test_pa_low_precision_field_exact_on_pm1_instance(B):
     n, R = sp.n, 256
     S = I.uniform_state(R, n, -1.0, 1.0, seed=7)
     Y = I.uniform_state(R, n, -0.5, 0.5, seed=8)
-    for prec in (1, 2):
+    got = {}
+    for prec in (1, 2, 3):
         St, Yt = _cuda(S), _cuda(Y)
         Ft = torch.empty(R, n, device="cuda")
         B.veloxq_steps_dev(ctx, R, 3, 1, 10, B.make_schedule(path=3, prec=prec, method=2, c0=0.2), St, Yt, Ft)
         torch.cuda.synchronize()
         F = O.field(p, O.field_operand("pa", S))
         Fg = Ft.cpu().numpy().astype(np.float64)
+        got[prec] = (Fg, St.cpu().numpy(), Yt.cpu().numpy())
         if prec == 1:
             assert np.array_equal(Fg, F)
         else:
             assert np.all(np.abs(Fg - F) <= 4e-7 * np.abs(F))
+    # PA's operand is exact in one E4M3 term: FP8 runs it as FP8_ONE_TERM does, bit for bit
+    for a, b in zip(got[2], got[3]):
+        assert np.array_equal(a, b)
 
 
 def test_method_errors(B):
     ctx, _ = inst_dense_sk(B, 64)
-    with pytest.raises(B.VeloxqError, match="EUNSUPPORTED|status -5"):
-        B.veloxq_solve(ctx, 16, 4, B.make_schedule(prec=2, method=1), seed=0)
+    for prec in (2, 3):
+        with pytest.raises(B.VeloxqError, match="EUNSUPPORTED|status -5"):
+            B.veloxq_solve(ctx, 16, 4, B.make_schedule(prec=prec, method=1), seed=0)
+    with pytest.raises(B.VeloxqError, match="status -1"):
+        B.veloxq_solve(ctx, 16, 4, B.make_schedule(prec=4), seed=0)
     with pytest.raises(B.VeloxqError):
         B.veloxq_solve(ctx, 16, 4, B.make_schedule(method=3), seed=0)
     with pytest.raises(B.VeloxqError):

@@ -1,11 +1,19 @@
 """Tensor-core (tcgen05) dense local field, BF16 and FP8 E4M3 with per-row
 scales, FP32 accumulation, against the FP64 oracle.
 
-Bounds from the operand rounding: BF16 rounds each operand to 8 significant
-bits (relative error <= 2^-9), E4M3 to 4 (<= 2^-4); a product of two rounded
-operands is within (1 + u)^2 - 1 of the exact one, so elementwise
-|dF_ir| <= (2u + u^2) (|Qoff| |S|)_ir + FP32 accumulation. The normwise
-bar of the FP32-vs-mixed-precision comparison is 3e-2.
+Bounds from the operand rounding. BF16 rounds each operand to 8 significant
+bits (relative error <= 2^-9). E4M3 keeps 4 (<= 2^-4 for normal values, an
+absolute 2^-10 of the scale below 2^-6). Qoff is one E4M3 term of Qoff_ij /
+q_i, q_i = amax_i / 448. S is v = 448 s in two E4M3 terms for FP8 (hi =
+e4m3(v), lo = e4m3(v - hi): relative 2^-8 plus the lo term's absolute
+2^-10 / 448), or in one term for FP8_ONE_TERM (2^-4). With uQ, uS the
+relative and aQ_i, aS the absolute parts,
+    |dF_ir| <= (uQ + uS + uQ uS) (|Qoff| |S|)_ir
+               + aQ_i (1 + uS) sum_j |S_jr| + aS (1 + uQ) sum_j |Qoff_ij|
+               + FP32 accumulation.
+The normwise bar of the mixed-precision field is 3e-2; BF16 and FP8 (two
+terms) meet it, FP8_ONE_TERM does not (both operands rounded to 4 bits: about
+3.7%) and its tests hold it to its own estimate instead.
 """
 import json
 import os
@@ -19,7 +27,12 @@ from paper_2501_19221_gb300 import instances as I
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-U = {1: 2.0 ** -9, 2: 2.0 ** -4}
+BF16, FP8, FP8_ONE_TERM = 1, 2, 3
+# relative rounding of (Qoff, S) per precision
+U = {BF16: (2.0 ** -9, 2.0 ** -9), FP8: (2.0 ** -4, 2.0 ** -8 + 2.0 ** -23), FP8_ONE_TERM: (2.0 ** -4, 2.0 ** -4)}
+# normwise bars: the 3e-2 of the mixed-precision field for BF16 and FP8; the
+# one-term form's own estimate (sqrt(2) x 2.7%) with margin
+NORM_BAR = {BF16: 1e-2, FP8: 3e-2, FP8_ONE_TERM: 4.5e-2}
 
 
 def _report(key, value):
@@ -48,13 +61,31 @@ def _cuda(a, dtype=torch.float32):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
 
 
-def _elem_bound(prec, scale):
-    u = U[prec]
-    # the FP8 S operand is e4m3(448 s): values below 2^-6/448 are subnormal (absolute error 2^-9/448)
-    return (2 * u + u * u) * scale + 1e-6 * scale + (2.0 ** -10 / 448 * 4 if prec == 2 else 0.0)
+def _qoff_rows(Q, rows):
+    """Rows of Qoff = offdiag((Q + Q^T)/2) for the given row indices."""
+    Qd = np.asarray(Q, dtype=np.float64)
+    Qs = 0.5 * (Qd[rows, :] + Qd[:, rows].T)
+    Qs[np.arange(len(rows)), rows] = 0.0
+    return Qs
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+def _elem_bound(prec, scale, Qoff_rows=None, S=None):
+    """Elementwise bound on |F_gpu - F| ([R][rows]) from the module docstring;
+    scale = (|Qoff| |S|) for the same entries."""
+    uq, us = U[prec]
+    b = (uq + us + uq * us) * scale + 1e-6 * scale
+    if prec != BF16:
+        aq = np.abs(Qoff_rows).max(axis=1) / 448.0 * 2.0 ** -10          # per row
+        a_s = 2.0 ** -10 / 448.0                                          # S's absolute part
+        b = b + (1 + us) * aq[None, :] * np.abs(S).sum(axis=1)[:, None]
+        b = b + (1 + uq) * a_s * np.abs(Qoff_rows).sum(axis=1)[None, :]
+    return b
+
+
+PRECS = [BF16, FP8, FP8_ONE_TERM]
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,R", [(300, 1), (300, 64), (300, 300), (20, 7), (129, 257)])
 def test_tc_field_matches_oracle(B, prec, n, R):
     Q, _ = I.sk_qubo(n, seed=3)
@@ -68,12 +99,13 @@ def test_tc_field_matches_oracle(B, prec, n, R):
     p = O.problem_from_dense(Q.astype(np.float64))
     ref = O.field(p, S.astype(np.float64))
     scale = O.abs_field(p, S.astype(np.float64))
-    assert np.all(np.abs(Fg - ref) <= _elem_bound(prec, scale) + 1e-30), np.max(np.abs(Fg - ref) / (scale + 1e-30))
+    bound = _elem_bound(prec, scale, _qoff_rows(Q, np.arange(n)), S)
+    assert np.all(np.abs(Fg - ref) <= bound + 1e-30), np.max(np.abs(Fg - ref) / (scale + 1e-30))
     err = np.linalg.norm(Fg - ref) / np.linalg.norm(ref)
-    assert err <= (1e-2 if prec == 1 else 6e-2), err
+    assert err <= NORM_BAR[prec], err
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", PRECS)
 def test_tc_field_full_size_sampled_rows(B, prec):
     """n = 8192, 1024 replicas (the dense benchmark shape), sampled rows."""
     n, R = 8192, 1024
@@ -87,10 +119,10 @@ def test_tc_field_full_size_sampled_rows(B, prec):
     Fg = F[:, torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
     ref = O.field_dense_rows(Q, S, rows)
     scale = O.abs_field_dense_rows(Q, S, rows)
-    assert np.all(np.abs(Fg - ref) <= _elem_bound(prec, scale))
+    assert np.all(np.abs(Fg - ref) <= _elem_bound(prec, scale, _qoff_rows(Q, rows), S))
     err = np.linalg.norm(Fg - ref) / np.linalg.norm(ref)
     _report(f"field_n8192_R1024_prec{prec}", err)
-    assert err <= (1e-2 if prec == 1 else 6e-2), err
+    assert err <= NORM_BAR[prec], err
     # FP32 CUDA-core form on the same sample, for the report
     B.veloxq_field_dev(ctx, R, 0, _cuda(S), F)
     torch.cuda.synchronize()
@@ -100,7 +132,7 @@ def test_tc_field_full_size_sampled_rows(B, prec):
     assert e32 <= 1e-5
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", PRECS)
 def test_tc_step_fuses_the_update(B, prec):
     """One fused step: s, y follow the FP32 update of the oracle up to the
     propagated field error (dy = dt c0 dF / 2, ds = dt a0 dy)."""
@@ -118,7 +150,7 @@ def test_tc_step_fuses_the_update(B, prec):
     p = O.problem_from_dense(Q.astype(np.float64), c)
     a = O.schedule(K, [0.0, 1.0])
     S1, Y1, F = O.bsb_step(p, S, Y, a[k], float(dt), 1.0, float(c0))
-    dF = _elem_bound(prec, O.abs_field(p, S.astype(np.float64)))
+    dF = _elem_bound(prec, O.abs_field(p, S.astype(np.float64)), _qoff_rows(Q, np.arange(n)), S)
     dy = float(dt) * float(c0) * 0.5 * dF + 2e-5
     ds = float(dt) * dy + 2e-5
     Sg, Yg = St.cpu().numpy(), Yt.cpu().numpy()
@@ -130,10 +162,10 @@ def test_tc_step_fuses_the_update(B, prec):
     assert np.all((np.sign(Sg) == np.sign(S1))[wall] | (np.abs(np.abs(S1) - 1) <= ds)[wall])
 
 
-@pytest.mark.parametrize("prec", [1, 2])
-def test_tc_first_50_steps(B, prec):
-    """Free-running from the same Philox start: the field of each of the
-    first 50 steps within the normwise bar of the FP64 trajectory."""
+def _first_50(B, prec, teacher_forced):
+    """Errors of the field of each of the first 50 steps from the same Philox
+    start: against the FP64 field of the GPU's own state before the step
+    (teacher-forced), or against the FP64 trajectory (free-running)."""
     n, R, K, seed = 512, 64, 1000, 3
     Q, c = I.sk_qubo(n, seed=5)
     ctx = B.veloxq_create_dense(Q, c)
@@ -145,20 +177,42 @@ def test_tc_first_50_steps(B, prec):
     Ft = torch.empty(R, n, device="cuda")
     B.veloxq_init_state_dev(ctx, R, seed, 0.1, St, Yt)
     S0, Y0 = O.init_state(n, R, seed, 0.1)
-    ref = O.bsb_run(p, R, 50, 0.5, 1.0, c0, [0.0, 49.0 / (K - 1)], 0, S0, Y0, n_snap=50)
+    ref = None if teacher_forced else O.bsb_run(p, R, 50, 0.5, 1.0, c0, [0.0, 49.0 / (K - 1)], 0, S0, Y0, n_snap=50)
     errs = []
     for k in range(50):
+        Sk = St.cpu().numpy().astype(np.float64)
         B.veloxq_steps_dev(ctx, R, k, 1, K, sched, St, Yt, Ft)
         torch.cuda.synchronize()
-        Fr = ref["F_snap"][k]
+        Fr = O.field(p, Sk) if teacher_forced else ref["F_snap"][k]
         errs.append(np.linalg.norm(Ft.cpu().numpy() - Fr) / np.linalg.norm(Fr))
-    _report(f"first_50_steps_prec{prec}", max(errs))
-    # the mixed-precision bar; E4M3 keeps 3 mantissa bits, so its error sits near the bar
-    bar = 3e-2 if prec == 1 else 6e-2
+    return errs
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_first_50_steps_teacher_forced(B, prec):
+    """The mixed-precision bar, 3e-2 normwise on each of the first 50 steps'
+    fields, for BF16 and FP8 (two S terms); the one-term form against its own
+    estimate."""
+    errs = _first_50(B, prec, True)
+    _report(f"first_50_steps_teacher_forced_prec{prec}", max(errs))
+    bar = 3e-2 if prec in (BF16, FP8) else NORM_BAR[FP8_ONE_TERM]
     assert max(errs) <= bar, (max(errs), errs[:5])
 
 
-@pytest.mark.parametrize("prec", [1, 2])
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_first_50_steps_free_running(B, prec):
+    """Free-running from the same start: the field error then also carries the
+    trajectory's divergence from the FP64 one (every step's rounding is fed
+    back through the dynamics), which the FP32 form holds to 1e-5 elsewhere.
+    Recorded; held to twice the teacher-forced bar so that a broken step
+    still fails."""
+    errs = _first_50(B, prec, False)
+    _report(f"first_50_steps_free_running_prec{prec}", max(errs))
+    bar = 2 * (3e-2 if prec in (BF16, FP8) else NORM_BAR[FP8_ONE_TERM])
+    assert max(errs) <= bar, (max(errs), errs[:5])
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_tc_solve_outputs_consistent(B, prec):
     n = 300
     Q, c = I.sk_qubo(n, seed=6)
