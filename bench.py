@@ -781,10 +781,16 @@ def run_ours(args, rank, world, local_rank):
         pw = dict(w, Q=pinned[0], c=pinned[1])
     torch.cuda.synchronize()
     t0 = time.perf_counter()
+    t_create = t_solve = 0.0
     for i in range(e2e_iters):
+        ta = time.perf_counter()
         r2 = Runner(B, pw, stream, method)
+        tb = time.perf_counter()
         r2.solve(seed0 + 77 + i, want_x=True)
+        tc = time.perf_counter()
         r2.destroy()
+        t_create += tb - ta
+        t_solve += tc - tb
     e2e_s = (time.perf_counter() - t0) / e2e_iters
     nctx = len(run.ctxs)
     if run.grad:
@@ -793,6 +799,7 @@ def run_ours(args, rank, world, local_rank):
         d2h = n + (0 if run.batch else 8 * R + 8 * R) + 32 * nctx   # best x, per-replica energies, argmin records
     e2e = {"value": world * n * R * K / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
+           "create_ms": t_create / e2e_iters * 1e3, "solve_call_ms": t_solve / e2e_iters * 1e3,
            "includes": "context creation (H2D copy, device ingest, power iteration) + "
                        + ("gradient (forward, recompute, reverse)" if run.grad else "solve") + " + D2H of results"}
 

@@ -33,7 +33,10 @@
  *    replicas of n variables is at r*n + i. Binary batches are uint8 [B][n]
  *    with values 0/1.
  *  - A context owns every device buffer it allocates; veloxq_destroy frees
- *    them. A context is not thread-safe; different contexts are independent.
+ *    them. A context is not thread-safe; different contexts are independent
+ *    (they may be created, used and destroyed from different threads at once).
+ *  - A context lives on the device that was current when it was created;
+ *    every later call on it needs that device current (EINVAL otherwise).
  */
 #ifndef VELOXQ_H
 #define VELOXQ_H
@@ -107,7 +110,9 @@ typedef enum { VELOXQ_METHOD_BSB = 0, VELOXQ_METHOD_ASB = 1, VELOXQ_METHOD_PA = 
  * increasing linearly through the bifurcation at a(t) ~ a0; the rest is not
  * given by the paper and has the defaults below. The Ising coupling of the
  * dynamics is J = -Qoff/2, so the default c0 is kappa / rho(J) with rho the
- * spectral radius, computed by power iteration when the context is created. */
+ * spectral radius, estimated when the context is created (48 Lanczos steps;
+ * power iteration in one CTA for small sparse instances): from below, within
+ * 2% of rho on the instance families the tests cover. */
 typedef struct {
     float dt;               /* step size; default 0.5 */
     float a0;               /* default 1 */
@@ -129,7 +134,7 @@ typedef struct {
     int64_t nnz_field;      /* stored off-diagonal entries of Qs (n*(n-1) for dense) */
     int32_t is_dense;       /* 1 for dense contexts */
     int32_t is_integer;     /* 1 when Q and c are integer-valued: energies are exact int64 */
-    double rho;             /* spectral radius of Qoff by power iteration */
+    double rho;             /* spectral radius of Qoff (Lanczos or power-iteration estimate) */
     double K0;              /* E(x) = s^T Qoff s / 4 + b^T s / 2 + K0 for s = 2x - 1 */
     double ising_offset;    /* Ising contexts: H(s) = 2 E(x) + ising_offset; else 0 */
 } veloxq_info;
@@ -161,7 +166,7 @@ void veloxq_schedule_default(veloxq_schedule* s);
 /* Dense QUBO. Q: host, n*n row-major of type vt, used as given (need not be
  * symmetric); c: host, n doubles, or NULL for c = 0. stream: a cudaStream_t to
  * run on, or NULL for the default stream. Q and c are copied to the device,
- * Qs/Qoff/b/K0 are formed there, and rho is computed by power iteration.
+ * Qs/Qoff/b/K0 are formed there, and rho is estimated (see veloxq_schedule).
  * Errors: EINVAL for n < 1, NULL Q, non-finite values or n > 2^20; ENOMEM. */
 int veloxq_create_dense(veloxq_ctx** out, int64_t n, veloxq_vtype vt, const void* Q,
                         const double* c, void* stream);
@@ -309,21 +314,26 @@ int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, i
 int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
 
 /* The same energies as veloxq_energy_dev for callers that must not allocate
- * device memory during the call: code running while a CUDA graph is being
- * captured, code inside a custom allocator that must not re-enter cudaMalloc,
- * and loops that cannot afford the synchronisation an allocation may cause.
- * (The paper has no counterpart; this is a property of the library.)
+ * device memory during the call: code running inside a custom or pooling
+ * allocator (an allocation callback, an out-of-memory handler) that must not
+ * re-enter cudaMalloc, processes that reserve their whole device-memory budget
+ * up front and refuse later allocations, and loops that cannot afford the
+ * device synchronisation an allocation may cause. (The paper has no
+ * counterpart; this is a property of the library.)
  * Scratch is a fixed 4 MiB array in device memory that every GPU loading the
  * library keeps until the process exits; nothing is allocated or freed. The
- * first call on a device looks up that array's device address (a one-time
- * set-up per device, so make that first call before any stream capture), and
- * the context's device must be the current one. Limits: batch <= 65535 and
- * batch * groups <= 2^19, groups = 64 for sparse contexts and ceil(n/64) for
- * dense ones; larger batches are rejected with EINVAL and a message giving the
- * largest accepted batch. All calls share the one array: calls that overlap
- * on the GPU (different streams, or different contexts on one device) race
- * and must be serialised by the caller. X, E, E_int: device pointers as in
- * veloxq_energy_dev; asynchronous on the context's stream. */
+ * first call on a device (and the first after a device reset) looks up that
+ * array's device address, a one-time set-up that may load the library's
+ * device code, so make that first call before any stream capture; the
+ * context's device must be the current one (EINVAL otherwise). Limits:
+ * batch <= 65535 and batch * groups <= 2^19, groups = 64 for sparse contexts
+ * and ceil(n/64) for dense ones; larger batches are rejected with EINVAL and
+ * a message giving the largest accepted batch. Every partial sum is written
+ * before it is read, so nothing needs clearing between calls, but all calls
+ * share the one array: calls that overlap on the GPU (different streams, or
+ * different contexts on one device) race and must be serialised by the
+ * caller. X, E, E_int: device pointers as in veloxq_energy_dev; asynchronous
+ * on the context's stream. */
 int veloxq_energy_dev_noalloc(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int);
 
 /* ---------------------------------------------------------------------------
@@ -347,7 +357,7 @@ int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* 
 int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_count, int32_t K,
                      const veloxq_schedule* sched, float* S, float* Y, float* F_last);
 
-/* Spectral radius of Qoff as used for the default c0 (power iteration). */
+/* Spectral radius of Qoff as used for the default c0 (the creation-time estimate). */
 int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho);
 
 /* ---------------------------------------------------------------------------

@@ -358,6 +358,20 @@ def field_dense_rows(Q: np.ndarray, S: np.ndarray, rows: np.ndarray) -> np.ndarr
     return np.asarray(S, dtype=np.float64) @ Qs.T
 
 
+def bias_dense_rows(Q: np.ndarray, c, rows: np.ndarray) -> np.ndarray:
+    """b[rows] with b = Qs 1 + c, Qs = (Q + Q^T)/2 (the linear term of the
+    spin form under x = (1 + s)/2, Sec. 2 eq. qubo_model), for a dense Q given
+    as is, summed in FP64 by a library routine; for sampled rows of large
+    instances."""
+    Q = np.asarray(Q)
+    rows = np.asarray(rows)
+    Qs = 0.5 * (Q[rows, :].astype(np.float64) + Q[:, rows].T.astype(np.float64))
+    b = Qs.sum(axis=1)
+    if c is not None:
+        b = b + np.asarray(c, dtype=np.float64)[rows]
+    return b
+
+
 def abs_field_dense_rows(Q: np.ndarray, S: np.ndarray, rows: np.ndarray) -> np.ndarray:
     """|Qoff|[rows, :] |S|^T, the scale of the rounding bound for field_dense_rows."""
     Q = np.asarray(Q)

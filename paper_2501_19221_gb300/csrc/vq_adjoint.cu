@@ -25,7 +25,7 @@ namespace vq {
 
 namespace {
 
-constexpr int kAdjBlocks = 1216;   // 8 x 152 SMs, grid-stride
+constexpr int kAdjBlocks = 1216;   // grid-stride; a fixed count fixes the order of the FP64 partial sums
 constexpr int kAdjThreads = 256;
 
 template <int N>

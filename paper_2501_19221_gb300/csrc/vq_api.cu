@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -58,6 +59,10 @@ struct CtxExtra {
     int64_t graph_launches = 0;
     veloxq_timing timing{};
     bool timed = false;
+    // scratch of a batched launch headed by this context (instance table,
+    // per-instance results, error word): owned here, so that batches headed
+    // by different contexts never share it
+    DevBuf bwork, bbest, berr;
     ~CtxExtra() {
         if (graph) cudaGraphExecDestroy(graph);
         for (cudaEvent_t e : {ev, t0, t1, t2, t3})
@@ -66,12 +71,20 @@ struct CtxExtra {
     }
 };
 
+// The extra state of every live context, keyed by the context. Contexts are
+// created and destroyed from any thread, so the map is only touched under its
+// lock; an entry lives as long as its context.
+std::mutex& extras_mu() {
+    static std::mutex mu;
+    return mu;
+}
 std::map<const veloxq_ctx*, std::unique_ptr<CtxExtra>>& extras() {
     static std::map<const veloxq_ctx*, std::unique_ptr<CtxExtra>> m;
     return m;
 }
 
 CtxExtra* extra(const veloxq_ctx* ctx) {
+    std::lock_guard<std::mutex> lk(extras_mu());
     auto it = extras().find(ctx);
     return it == extras().end() ? nullptr : it->second.get();
 }
@@ -189,6 +202,17 @@ int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t, int method = VELOXQ
                    &t->ms_lo[1]);
 }
 
+// Every call on a context runs on the device the context was created on,
+// which must be the current device: its buffers live there.
+int check_device(const veloxq_ctx* ctx) {
+    int dev = -1;
+    VQ_CUDA(cudaGetDevice(&dev));
+    if (dev != ctx->device)
+        return fail(VELOXQ_EINVAL, "the context was created on device " + std::to_string(ctx->device) +
+                                       ", which must be the current device (current: " + std::to_string(dev) + ")");
+    return VELOXQ_OK;
+}
+
 int check_err_word(veloxq_ctx* ctx) {
     int h = 0;
     VQ_CUDA(cudaMemcpyAsync(&h, ctx->errw.p, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
@@ -300,7 +324,10 @@ static int new_ctx(veloxq_ctx** out, int64_t n, void* stream, veloxq_ctx** made)
         delete ctx;
         return cuda_fail(e, "stream creation");
     }
-    extras()[ctx] = std::move(ex);
+    {
+        std::lock_guard<std::mutex> lk(extras_mu());
+        extras()[ctx] = std::move(ex);
+    }
     *made = ctx;
     return VELOXQ_OK;
 }
@@ -352,7 +379,16 @@ int veloxq_create_ising_csr(veloxq_ctx** out, int64_t n, const int64_t* rowptr, 
 void veloxq_destroy(veloxq_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
-    extras().erase(ctx);
+    std::unique_ptr<CtxExtra> gone;
+    {
+        std::lock_guard<std::mutex> lk(extras_mu());
+        auto it = extras().find(ctx);
+        if (it != extras().end()) {
+            gone = std::move(it->second);
+            extras().erase(it);
+        }
+    }
+    gone.reset();
     delete ctx;
 }
 
@@ -391,6 +427,7 @@ int veloxq_spectral_radius(veloxq_ctx* ctx, double* rho) {
 int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                  uint8_t* x_best, double* E_best, int64_t* E_best_int, double* E_per_replica) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (replicas < 1 || replicas > kMaxReplicas) return fail(VELOXQ_EINVAL, "replicas must be in [1, 2^20]");
     if (steps < 1) return fail(VELOXQ_EINVAL, "steps must be >= 1");
     if (E_best_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_best_int requires an integer-valued context");
@@ -545,6 +582,15 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
         if (!ctxs[m]) return fail(VELOXQ_EINVAL, "context " + std::to_string(m) + " is NULL");
     RunParams p;
     VQ_TRY(resolve(ctxs[0], sched, steps, &p));
+    {
+        int dev = 0;
+        VQ_CUDA(cudaGetDevice(&dev));
+        for (int32_t m = 0; m < count; ++m)
+            if (ctxs[m]->device != dev)
+                return fail(VELOXQ_EINVAL, "context " + std::to_string(m) + " was created on device " +
+                                               std::to_string(ctxs[m]->device) + ", not the current device " +
+                                               std::to_string(dev) + ": a batch runs on one device");
+    }
     if (!batch_supported(ctxs, count, replicas, p)) {
         // general case: one solve per context
         for (int32_t m = 0; m < count; ++m) {
@@ -569,19 +615,25 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
         c0->stream = keep;
         VQ_TRY(rc);
     }
-    static DevBuf work, best_all, errw;
+    DevBuf& work = ex->bwork;
+    DevBuf& best_all = ex->bbest;
+    DevBuf& errw = ex->berr;
     VQ_TRY(best_all.ensure(sizeof(int64_t) * 2 * (size_t)count));
     VQ_TRY(errw.ensure(sizeof(int) * 4));
     VQ_CUDA(cudaMemsetAsync(errw.p, 0, sizeof(int), st));
-    // autotune: pipeline depth and CTAs per SM, by timing a 2-step probe (cached per batch shape)
+    // autotune: pipeline depth and CTAs per SM, by timing a 2-step probe (cached per device and batch shape;
+    // the cache is shared by every thread of the process, under a lock)
+    static std::mutex tuned_mu;
     static std::map<std::vector<int64_t>, int> tuned;
-    std::vector<int64_t> shape = {count, replicas};
+    std::vector<int64_t> shape = {c0->device, count, replicas};
     for (int32_t m = 0; m < count; ++m) shape.push_back(ctxs[m]->n);
-    int stages = 6;
-    auto hit = tuned.find(shape);
-    if (hit != tuned.end()) {
-        stages = hit->second;
-    } else {
+    int stages = 0;
+    {
+        std::lock_guard<std::mutex> lk(tuned_mu);
+        auto hit = tuned.find(shape);
+        if (hit != tuned.end()) stages = hit->second;
+    }
+    if (!stages) {
         RunParams probe = p;
         probe.K = std::min(steps, 2);
         float best_ms = 1e30f;
@@ -591,6 +643,7 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
                              errw.as<int>(), &ms));
             if (ms < best_ms) { best_ms = ms; stages = cand; }
         }
+        std::lock_guard<std::mutex> lk(tuned_mu);
         tuned[shape] = stages;
     }
     float ms_main = 0.f;
@@ -645,6 +698,7 @@ static int energy_impl(veloxq_ctx* ctx, int64_t B, const uint8_t* Xd, double* Ed
 
 int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (batch < 0) return fail(VELOXQ_EINVAL, "batch must be >= 0");
     if (batch > 0 && !X) return fail(VELOXQ_EINVAL, "X must not be NULL");
     if (E_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_int requires an integer-valued context");
@@ -653,6 +707,7 @@ int veloxq_energy_dev(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* 
 
 int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, int64_t* E_int) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (batch < 0) return fail(VELOXQ_EINVAL, "batch must be >= 0");
     if (batch > 0 && !X) return fail(VELOXQ_EINVAL, "X must not be NULL");
     if (E_int && !ctx->integer) return fail(VELOXQ_EINVAL, "E_int requires an integer-valued context");
@@ -671,6 +726,7 @@ int veloxq_energy(veloxq_ctx* ctx, int64_t batch, const uint8_t* X, double* E, i
 
 int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y) {
     if (!ctx || !S || !Y) return fail(VELOXQ_EINVAL, "ctx, S and Y must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (ctx->batch_R != R || R < 1) return fail(VELOXQ_EINVAL, "no batched state held for this replica count");
     const size_t b = sizeof(float) * (size_t)(ctx->n * (int64_t)R);
     VQ_CUDA(cudaMemcpyAsync(S, ctx->s_a.p, b, cudaMemcpyDeviceToDevice, ctx->stream));
@@ -680,6 +736,7 @@ int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y) {
 
 int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma0, float* S, float* Y) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (R < 1 || R > kMaxReplicas || !S || !Y) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, Y required");
     if (!(std::isfinite(sigma0) && sigma0 >= 0)) return fail(VELOXQ_EINVAL, "sigma0 must be finite and >= 0");
     return launch_init_state(ctx, R, seed, sigma0, LAYOUT_RN, S, Y);
@@ -687,6 +744,7 @@ int veloxq_init_state_dev(veloxq_ctx* ctx, int32_t R, uint64_t seed, float sigma
 
 int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* S, float* F) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (R < 1 || R > kMaxReplicas || !S || !F) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, F required");
     if (prec < VELOXQ_PREC_FP32 || prec > VELOXQ_PREC_FP8_ONE_TERM) return fail(VELOXQ_EINVAL, "unknown precision");
     if (ctx->dense) {
@@ -711,6 +769,7 @@ int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* 
 int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_count, int32_t K,
                      const veloxq_schedule* sched, float* S, float* Y, float* F_last) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (R < 1 || R > kMaxReplicas || !S || !Y) return fail(VELOXQ_EINVAL, "R in [1, 2^20] and non-NULL S, Y required");
     if (K < 1 || k_begin < 0 || k_count < 0 || (int64_t)k_begin + k_count > K)
         return fail(VELOXQ_EINVAL, "need 0 <= k_begin, 0 <= k_count, k_begin + k_count <= K");
@@ -781,6 +840,7 @@ int veloxq_selftest_timeout(int64_t budget_cycles) {
 int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_schedule* sched, uint64_t seed,
                 int32_t ckpt_every, double* loss, double* d_dt, double* d_kappa, double* d_knots) {
     if (!ctx) return fail(VELOXQ_EINVAL, "ctx must not be NULL");
+    VQ_TRY(check_device(ctx));
     if (replicas < 1 || replicas > kMaxReplicas || steps < 1)
         return fail(VELOXQ_EINVAL, "replicas must be in [1, 2^20] and steps >= 1");
     if (ckpt_every < 1) return fail(VELOXQ_EINVAL, "ckpt_every must be >= 1");

@@ -395,7 +395,7 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
         c->batch_R = R;
     }
     // longest processing time first onto the least loaded CTA
-    const int ctas = 152 * (stages == 4 ? 2 : 1);
+    const int ctas = device_sms(ctxs[0]->device) * (stages == 4 ? 2 : 1);
     std::vector<int> idx((size_t)count);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });

@@ -1,9 +1,23 @@
 // vq_common.cu -- kernels shared by every path: Philox initial state, the
 // per-replica best-so-far update, the bit readout of improved replicas, the
 // argmin over replicas and the unpacking of the winner, energy totals.
+#include <atomic>
+
 #include "vq_internal.cuh"
 
 namespace vq {
+
+int device_sms(int device) {
+    static std::atomic<int> cache[64];
+    int v = (device >= 0 && device < 64) ? cache[device].load(std::memory_order_relaxed) : 0;
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, device) != cudaSuccess || v < 1) {
+        cudaGetLastError();
+        v = 1;
+    }
+    if (device >= 0 && device < 64) cache[device].store(v, std::memory_order_relaxed);
+    return v;
+}
 
 namespace {
 

@@ -214,11 +214,11 @@ __global__ void __launch_bounds__(256) k_dense_energy(int64_t R, int32_t n, cons
 
 // k-splits of the FP32 dense step: enough CTAs to fill the GPU when the
 // output tiles alone cannot, with at least 16 k-tiles per split.
-void dense_split(int64_t n, int32_t R, int* ksplit, int* per) {
+void dense_split(int64_t n, int32_t R, int sms, int* ksplit, int* per) {
     const int64_t ctas = div_up(n, BN) * div_up(R, BM);
     const int ktiles = (int)div_up(n, BK);
     int ks = 1;
-    if (ctas < 152) ks = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(2 * 152, ctas), ktiles / 16));
+    if (ctas < sms) ks = (int)std::max<int64_t>(1, std::min<int64_t>(div_up(2 * (int64_t)sms, ctas), ktiles / 16));
     *per = (int)div_up(ktiles, ks);
     *ksplit = (int)div_up(ktiles, *per);
 }
@@ -228,7 +228,7 @@ int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_n
                       int k, float dt, float a0, float c0, float* F_out, const Rule& rule) {
     const int32_t n = (int32_t)ctx->n;
     int ksplit, per;
-    dense_split(n, R, &ksplit, &per);
+    dense_split(n, R, device_sms(ctx->device), &ksplit, &per);
     float* part = nullptr;
     if (ksplit > 1) {
         // the workspace is sized by dense_prepare before any capture; growing it here is only
@@ -291,7 +291,7 @@ int dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_nxt, flo
 
 int dense_prepare(veloxq_ctx* ctx, int32_t R) {
     int ksplit, per;
-    dense_split(ctx->n, R, &ksplit, &per);
+    dense_split(ctx->n, R, device_sms(ctx->device), &ksplit, &per);
     if (ksplit > 1) VQ_TRY(ctx->dpart.ensure(sizeof(float) * (size_t)ksplit * R * ctx->n));
     return VELOXQ_OK;
 }

@@ -22,7 +22,7 @@ namespace vq {
 
 namespace {
 
-constexpr int kRedBlocks = 304;   // 2 x 152 SMs
+constexpr int kRedBlocks = 304;   // grid-stride; a fixed count fixes the order of the FP64 partial sums
 constexpr int64_t kDenseCsrMax = 512;   // dense instances up to this size also keep CSR rows
 constexpr int kRedThreads = 512;
 
@@ -340,31 +340,48 @@ __device__ __forceinline__ float warp_sum_to_lane0(float a) {
     return a;
 }
 constexpr int kPiBlock = 256;
-struct PiNorm {
+
+// ---- Lanczos estimate of rho(Qoff) (dense, and sparse beyond one CTA) ------
+// Plain Lanczos from the fixed start vector pi_start: m steps
+//   u = A v_j, alpha_j = v_j . u, w_{j+1} = u - alpha_j v_j - beta_j v_{j-1},
+//   beta_{j+1} = |w_{j+1}|, v_{j+1} = w_{j+1} / beta_{j+1},
+// and rho ~ max |extreme eigenvalue| of the m x m tridiagonal T (alpha on the
+// diagonal, beta beside it). Ritz values lie inside the spectrum, so the
+// estimate approaches rho from below, far faster than the power iteration for
+// the continuous spectra of these instances (dense Gaussian, Wishart,
+// lattices: within a few 1e-3 of rho after 48 steps). The vectors are stored
+// unnormalised (w_j, with |w_j|^2 kept in FP64), so that each step is one
+// matrix pass and one vector pass; products are FP32, every sum over blocks
+// FP64 in a fixed order. No reorthogonalisation: the loss of orthogonality
+// repeats converged Ritz values but does not move the extreme ones.
+constexpr int kLzSteps = 48;
+struct LzScal {
     double* part;      // one partial per block
     unsigned* count;   // blocks finished in this launch (reset by the last one)
-    double* nrm2;      // [2] |w|^2, alternating
-    float* inv;        // [2] 1/|w|, alternating
+    double* alpha;     // [kLzSteps]      alpha_j
+    double* nrm2;      // [kLzSteps + 1]  |w_j|^2
 };
-// Called by every thread of the block with its own sum of squares.
-__device__ __forceinline__ void pi_block_finish(float sq, PiNorm nm, int slot) {
+__device__ __forceinline__ float inv_norm(double q) { return q > 0.0 ? (float)(1.0 / sqrt(q)) : 0.0f; }
+// Called by every thread of the block with its own partial; the last block
+// to finish writes the total over blocks (FP64, fixed order) to *out.
+__device__ __forceinline__ void lz_block_finish(float v, LzScal sc, double* out) {
     __shared__ float wsum[kPiBlock / 32];
     __shared__ double dsum[kPiBlock];
     __shared__ bool last;
-    sq = warp_sum_to_lane0(sq);
-    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = sq;
+    v = warp_sum_to_lane0(v);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = v;
     __syncthreads();
     if (threadIdx.x == 0) {
         float b = 0.0f;
         for (int q = 0; q < kPiBlock / 32; ++q) b += wsum[q];
-        nm.part[blockIdx.x] = (double)b;
+        sc.part[blockIdx.x] = (double)b;
         __threadfence();
-        last = atomicAdd(nm.count, 1u) == gridDim.x - 1;
+        last = atomicAdd(sc.count, 1u) == gridDim.x - 1;
     }
     __syncthreads();
     if (!last) return;
     double a = 0.0;
-    for (unsigned i = threadIdx.x; i < gridDim.x; i += kPiBlock) a += __ldcg(nm.part + i);
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += kPiBlock) a += __ldcg(sc.part + i);
     dsum[threadIdx.x] = a;
     __syncthreads();
     for (int s = kPiBlock / 2; s > 0; s >>= 1) {
@@ -372,73 +389,127 @@ __device__ __forceinline__ void pi_block_finish(float sq, PiNorm nm, int slot) {
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        nm.nrm2[slot] = dsum[0];
-        nm.inv[slot] = dsum[0] > 0.0 ? (float)(1.0 / sqrt(dsum[0])) : 0.0f;
-        *nm.count = 0u;
+        *out = dsum[0];
+        *sc.count = 0u;
     }
 }
-__global__ void __launch_bounds__(kPiBlock) k_pi_init(int64_t n, float* __restrict__ v, PiNorm nm) {
+// w_0 = the fixed start vector; |w_0|^2
+__global__ void __launch_bounds__(kPiBlock) k_lz_start(int64_t n, float* __restrict__ w, LzScal sc) {
     float sq = 0.0f;
     for (int64_t i = (int64_t)blockIdx.x * kPiBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPiBlock) {
         const float x = pi_start(i);
-        v[i] = x;
+        w[i] = x;
         sq = fmaf(x, x, sq);
     }
-    pi_block_finish(sq, nm, 0);
+    lz_block_finish(sq, sc, sc.nrm2);
 }
-// w = Qoff (v / |v|) for CSR rows; odd launches walk the rows backwards so
-// that the ones the previous launch read last (still in L2) come first.
-__global__ void __launch_bounds__(kPiBlock) k_pi_spmv(int64_t n, const int64_t* __restrict__ rp,
-                                                     const int32_t* __restrict__ col, const float* __restrict__ w8,
-                                                     const float* __restrict__ v, float* __restrict__ out, PiNorm nm,
-                                                     int t) {
-    const float inv = nm.inv[t & 1];
-    const bool rev = t & 1;
-    float sq = 0.0f;
+// u = A v_j (v_j = w_j / |w_j|) for CSR rows, and alpha_j = v_j . u; odd
+// steps walk the rows backwards so that the ones the previous pass read last
+// (still in L2) come first.
+__global__ void __launch_bounds__(kPiBlock) k_lz_spmv(int64_t n, const int64_t* __restrict__ rp,
+                                                     const int32_t* __restrict__ col, const float* __restrict__ wf,
+                                                     const float* __restrict__ wj, float* __restrict__ u, LzScal sc,
+                                                     int j) {
+    const float inv = inv_norm(sc.nrm2[j]);
+    const bool rev = j & 1;
+    float dot = 0.0f;
     for (int64_t k = (int64_t)blockIdx.x * kPiBlock + threadIdx.x; k < n; k += (int64_t)gridDim.x * kPiBlock) {
         const int64_t i = rev ? n - 1 - k : k;
         float a = 0.0f;
-        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(w8[p], v[col[p]], a);
+        for (int64_t p = rp[i]; p < rp[i + 1]; ++p) a = fmaf(wf[p], wj[col[p]], a);
         a *= inv;
-        out[i] = a;
-        sq = fmaf(a, a, sq);
+        u[i] = a;
+        dot = fmaf(a, wj[i] * inv, dot);
     }
-    pi_block_finish(sq, nm, (t + 1) & 1);
+    lz_block_finish(dot, sc, sc.alpha + j);
 }
 // The same for a dense Qoff: one warp per row, 16-byte loads when n % 4 == 0.
-__global__ void __launch_bounds__(kPiBlock) k_pi_gemv(int64_t n, const float* __restrict__ q,
-                                                     const float* __restrict__ v, float* __restrict__ out, PiNorm nm,
-                                                     int t) {
-    const float inv = nm.inv[t & 1];
-    const bool rev = t & 1;
+__global__ void __launch_bounds__(kPiBlock) k_lz_gemv(int64_t n, const float* __restrict__ q,
+                                                     const float* __restrict__ wj, float* __restrict__ u, LzScal sc,
+                                                     int j) {
+    const float inv = inv_norm(sc.nrm2[j]);
+    const bool rev = j & 1;
     const int lane = threadIdx.x & 31;
     const int64_t nwarps = (int64_t)gridDim.x * (kPiBlock / 32);
-    float sq = 0.0f;
+    float dot = 0.0f;
     for (int64_t k = (int64_t)blockIdx.x * (kPiBlock / 32) + (threadIdx.x >> 5); k < n; k += nwarps) {
         const int64_t i = rev ? n - 1 - k : k;
         const float* row = q + i * n;
         float a = 0.0f;
         if ((n & 3) == 0) {
             const float4* r4 = reinterpret_cast<const float4*>(row);
-            const float4* v4 = reinterpret_cast<const float4*>(v);
-            for (int64_t j = lane; j < n / 4; j += 32) {
-                const float4 x = r4[j], y = v4[j];
+            const float4* v4 = reinterpret_cast<const float4*>(wj);
+            for (int64_t c = lane; c < n / 4; c += 32) {
+                const float4 x = __ldcs(r4 + c), y = v4[c];
                 a = fmaf(x.x, y.x, a);
                 a = fmaf(x.y, y.y, a);
                 a = fmaf(x.z, y.z, a);
                 a = fmaf(x.w, y.w, a);
             }
         } else {
-            for (int64_t j = lane; j < n; j += 32) a = fmaf(row[j], v[j], a);
+            for (int64_t c = lane; c < n; c += 32) a = fmaf(row[c], wj[c], a);
         }
         a = warp_sum_to_lane0(a);
         if (lane == 0) {
             a *= inv;
-            out[i] = a;
-            sq = fmaf(a, a, sq);
+            u[i] = a;
+            dot = fmaf(a, wj[i] * inv, dot);
         }
     }
-    pi_block_finish(sq, nm, (t + 1) & 1);
+    lz_block_finish(dot, sc, sc.alpha + j);
+}
+// w_{j+1} = u - alpha_j v_j - beta_j v_{j-1} in place of u, and |w_{j+1}|^2
+// (beta_j = |w_j|, v_j = w_j / |w_j|).
+__global__ void __launch_bounds__(kPiBlock) k_lz_update(int64_t n, float* __restrict__ u, const float* __restrict__ wj,
+                                                       const float* __restrict__ wjm1, LzScal sc, int j) {
+    const double nj = sc.nrm2[j];
+    const float c1 = (float)(sc.alpha[j] * (nj > 0.0 ? 1.0 / sqrt(nj) : 0.0));
+    const float c2 = (j > 0 && sc.nrm2[j - 1] > 0.0) ? (float)sqrt(nj / sc.nrm2[j - 1]) : 0.0f;
+    float sq = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * kPiBlock + threadIdx.x; i < n; i += (int64_t)gridDim.x * kPiBlock) {
+        float w = fmaf(-c1, wj[i], u[i]);
+        if (j > 0) w = fmaf(-c2, wjm1[i], w);
+        u[i] = w;
+        sq = fmaf(w, w, sq);
+    }
+    lz_block_finish(sq, sc, sc.nrm2 + j + 1);
+}
+
+// Extreme eigenvalues of the symmetric tridiagonal matrix (diagonal a[0..m),
+// off-diagonal b[0..m-1)) by bisection on the Sturm count (the number of
+// negative pivots of T - x I counts the eigenvalues below x).
+int sturm_below(const std::vector<double>& a, const std::vector<double>& b, double x) {
+    int c = 0;
+    double d = 1.0;
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double off = i ? b[i - 1] * b[i - 1] : 0.0;
+        d = a[i] - x - (i ? off / d : 0.0);
+        if (d == 0.0) d = -1e-300;
+        if (d < 0.0) ++c;
+    }
+    return c;
+}
+void tridiag_extremes(const std::vector<double>& a, const std::vector<double>& b, double* lo, double* hi) {
+    double g0 = a[0], g1 = a[0];
+    for (size_t i = 0; i < a.size(); ++i) {
+        const double r = (i ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < a.size() ? std::fabs(b[i]) : 0.0);
+        g0 = std::min(g0, a[i] - r);
+        g1 = std::max(g1, a[i] + r);
+    }
+    const int m = (int)a.size();
+    double l = g0, h = g1;   // smallest eigenvalue: largest x with no eigenvalue below
+    for (int it = 0; it < 200 && h - l > 1e-15 * std::max(1.0, std::fabs(l) + std::fabs(h)); ++it) {
+        const double x = 0.5 * (l + h);
+        if (sturm_below(a, b, x) >= 1) h = x; else l = x;
+    }
+    *lo = 0.5 * (l + h);
+    l = g0;
+    h = g1;                  // largest eigenvalue: smallest x with every eigenvalue below
+    for (int it = 0; it < 200 && h - l > 1e-15 * std::max(1.0, std::fabs(l) + std::fabs(h)); ++it) {
+        const double x = 0.5 * (l + h);
+        if (sturm_below(a, b, x) >= m) h = x; else l = x;
+    }
+    *hi = 0.5 * (l + h);
 }
 
 // The same power iteration for a small sparse instance in ONE CTA (no launch
@@ -567,7 +638,7 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     if (ch) VQ_CUDA(cudaMemcpyAsync(lin, ch, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     else VQ_CUDA(cudaMemsetAsync(lin, 0, sizeof(double) * n, st));
     const int64_t total = n * n;
-    const int gb = (int)std::min<int64_t>(div_up(total, 256), 152 * 16);
+    const int gb = (int)std::min<int64_t>(div_up(total, 256), (int64_t)device_sms(ctx->device) * 16);
     k_dense_check<T><<<gb, 256, 0, st>>>(q, total, err);
     if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
     k_dense_rows<T><<<(unsigned)n, 256, 0, st>>>(q, n, rowsum, absrow, diag);
@@ -599,7 +670,10 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     } else {
         int e = 0;
         std::frexp(Tsum > 0 ? Tsum : 1.0, &e);     // Tsum < 2^e
-        ctx->energy_shift = std::max(0, std::min(200, 61 - e));
+        // every fixed-point sum stays below 2^62 only while Tsum < 2^61
+        if (61 - e < 0) return fail(VELOXQ_EUNSUPPORTED, "real couplings too large for exact fixed-point energies "
+                                                         "(sum |Q| + sum |c| must be below 2^61)");
+        ctx->energy_shift = std::min(200, 61 - e);
     }
     VQ_TRY(ctx->dfix.ensure(sizeof(int64_t) * n));
     k_fix<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, d, ctx->energy_shift, ctx->dfix.as<int64_t>());
@@ -731,7 +805,9 @@ int ingest_csr_t(veloxq_ctx* ctx, const int64_t* rph, const int32_t* colh, const
     } else {
         int e = 0;
         std::frexp(Tm > 0 ? Tm : 1.0, &e);
-        ctx->energy_shift = std::max(0, std::min(200, 61 - e));
+        if (61 - e < 0) return fail(VELOXQ_EUNSUPPORTED, "real couplings too large for exact fixed-point energies "
+                                                         "(sum |Q| + sum |c| must be below 2^61)");
+        ctx->energy_shift = std::min(200, 61 - e);
     }
     const bool use8 = integer && hmaxw <= 127;
     ctx->wf_half_exact = integer && hmaxw <= 2047;
@@ -820,7 +896,9 @@ int ingest_csr(veloxq_ctx* ctx, const int64_t* rowptr, const int32_t* col, velox
     return fail(VELOXQ_EINVAL, "unknown value type");
 }
 
-// rho(Qoff) by power iteration: w_t = Qoff (w_{t-1} / |w_{t-1}|), rho ~ |w_T|.
+// rho(Qoff): by power iteration in one CTA for small sparse instances
+// (w_t = Qoff (w_{t-1} / |w_{t-1}|), rho ~ |w_T| after `iters` iterations), by
+// kLzSteps steps of Lanczos otherwise.
 int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
     const int64_t n = ctx->n;
     cudaStream_t st = ctx->stream;
@@ -850,33 +928,41 @@ int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
         *rho = std::sqrt(h);
         return VELOXQ_OK;
     }
-    const int64_t grid_cap = 152 * (2048 / kPiBlock);
+    const int64_t grid_cap = (int64_t)device_sms(ctx->device) * (2048 / kPiBlock);
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(ctx->dense ? div_up(n, kPiBlock / 32) : div_up(n, kPiBlock), grid_cap));
+    const int m = (int)std::min<int64_t>(kLzSteps, n);
     DevBuf buf;
-    const size_t vbytes = (sizeof(float) * (size_t)(2 * n) + 15) & ~size_t(15);
-    VQ_TRY(buf.ensure(vbytes + sizeof(double) * ((size_t)grid + 4) + 16));
-    float* v = buf.as<float>();
-    float* w = v + n;
-    PiNorm nm;
-    nm.part = reinterpret_cast<double*>(buf.as<uint8_t>() + vbytes);
-    nm.nrm2 = nm.part + grid;
-    nm.inv = reinterpret_cast<float*>(nm.nrm2 + 2);
-    nm.count = reinterpret_cast<unsigned*>(nm.inv + 2);
-    VQ_CUDA(cudaMemsetAsync(nm.count, 0, sizeof(unsigned), st));
-    k_pi_init<<<grid, kPiBlock, 0, st>>>(n, v, nm);
-    for (int t = 0; t < iters; ++t) {
+    const size_t vbytes = (sizeof(float) * (size_t)(3 * n) + 15) & ~size_t(15);
+    VQ_TRY(buf.ensure(vbytes + sizeof(double) * ((size_t)grid + 2 * kLzSteps + 4) + 16));
+    float* wv[3] = {buf.as<float>(), buf.as<float>() + n, buf.as<float>() + 2 * n};
+    LzScal sc;
+    sc.part = reinterpret_cast<double*>(buf.as<uint8_t>() + vbytes);
+    sc.alpha = sc.part + grid;
+    sc.nrm2 = sc.alpha + kLzSteps;
+    sc.count = reinterpret_cast<unsigned*>(sc.nrm2 + kLzSteps + 2);
+    VQ_CUDA(cudaMemsetAsync(sc.count, 0, sizeof(unsigned), st));
+    k_lz_start<<<grid, kPiBlock, 0, st>>>(n, wv[0], sc);
+    for (int j = 0; j < m; ++j) {
+        float* wj = wv[j % 3];
+        float* u = wv[(j + 1) % 3];
         if (ctx->dense)
-            k_pi_gemv<<<grid, kPiBlock, 0, st>>>(n, ctx->qoff32.as<float>(), v, w, nm, t);
+            k_lz_gemv<<<grid, kPiBlock, 0, st>>>(n, ctx->qoff32.as<float>(), wj, u, sc, j);
         else
-            k_pi_spmv<<<grid, kPiBlock, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
-                                                 ctx->wf.as<float>(), v, w, nm, t);
-        std::swap(v, w);
+            k_lz_spmv<<<grid, kPiBlock, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
+                                                 ctx->wf.as<float>(), wj, u, sc, j);
+        if (j + 1 < m) k_lz_update<<<grid, kPiBlock, 0, st>>>(n, u, wj, wv[(j + 2) % 3], sc, j);
     }
-    VQ_LAUNCH_CHECK("power iteration");
-    VQ_CUDA(cudaMemcpyAsync(&h, nm.nrm2 + (iters & 1), sizeof(double), cudaMemcpyDeviceToHost, st));
+    VQ_LAUNCH_CHECK("Lanczos");
+    std::vector<double> al((size_t)m), n2((size_t)m);
+    VQ_CUDA(cudaMemcpyAsync(al.data(), sc.alpha, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+    VQ_CUDA(cudaMemcpyAsync(n2.data(), sc.nrm2, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
     VQ_CUDA(cudaStreamSynchronize(st));
-    *rho = std::sqrt(h);
+    std::vector<double> be((size_t)std::max(0, m - 1));
+    for (int j = 0; j + 1 < m; ++j) be[j] = std::sqrt(std::max(0.0, n2[j + 1]));
+    double lo = 0.0, hi = 0.0;
+    tridiag_extremes(al, be, &lo, &hi);
+    *rho = std::max(std::fabs(lo), std::fabs(hi));
     return VELOXQ_OK;
 }
 

@@ -133,6 +133,7 @@ namespace vq {
 
 // sizes and helpers
 __host__ __device__ inline int64_t div_up(int64_t a, int64_t b) { return (a + b - 1) / b; }
+int device_sms(int device);   // multiprocessors of a device (queried once per device)
 
 // ingest (vq_ingest.cu)
 int ingest_dense(veloxq_ctx* ctx, veloxq_vtype vt, const void* Qh, const double* ch, bool ising);

@@ -42,6 +42,7 @@ static int pow2_at_least(int v) {
 // interleaved, and a CTA step costs about (3 + RC) instructions per coupling
 // (the column and value loads are shared by its RC replicas).
 ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
+    const int sms = device_sms(ctx->device);
     ResPlan best{0, 0, 0, false, false, 0, 0, false};
     if (!ctx->has_csr || ctx->n > 8192 || ctx->n < 1 || ctx->nnz >= (int64_t)1 << 31) return best;
     const int n = (int)ctx->n;
@@ -71,7 +72,7 @@ ResPlan make_plan(const veloxq_ctx* ctx, int32_t R) {
                                          ell ? ell_d : 0);
             if (p.total > (size_t)kSmemMax) continue;
             const int64_t ctas = div_up(R, rc);
-            const double cost = (double)div_up(ctas, 152) * (3.0 + rc) * (csr_smem ? 1.0 : 1.3);
+            const double cost = (double)div_up(ctas, sms) * (3.0 + rc) * (csr_smem ? 1.0 : 1.3);
             if (cost < best_cost - 1e-9) {
                 best_cost = cost;
                 best = ResPlan{rc, threads, rpt, csr_smem, csr_smem && packed, ell ? ell_d : 0, p.total, true};

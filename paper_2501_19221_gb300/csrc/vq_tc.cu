@@ -656,7 +656,7 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     a.plane = (int64_t)R * a.n_pad;
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(VELOXQ_EUNSUPPORTED, "device ordinal out of range");
     TcDevice& dv = g_tcdev[ctx->device];
-    if (!dv.sms) VQ_CUDA(cudaDeviceGetAttribute(&dv.sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    if (!dv.sms) dv.sms = device_sms(ctx->device);
     const int64_t tiles = div_up(ctx->n, 2 * BM) * div_up(R, BN);
     TcKernel fn;
     if (prec == VELOXQ_PREC_BF16) fn = pick_kernel<1, 1>(field_only, rule.method);

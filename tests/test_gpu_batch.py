@@ -105,3 +105,94 @@ def test_batch_falls_back_when_not_supported(B):
     for ctx, E in zip(ctxs, a["E"]):
         single = B.veloxq_solve(ctx, 32, 100, B.make_schedule(readout_every=10), seed=3)
         assert single["E"] == E
+
+
+def _sym_normal(n, seed):
+    """A symmetric dense instance with N(0, 1/n) couplings, zero diagonal
+    (float32; the SK recipe, cheap enough for hundreds of instances)."""
+    g = np.random.default_rng(seed).standard_normal((n, n), dtype=np.float32)
+    Q = (g + g.T) * np.float32(1.0 / np.sqrt(2.0 * n))
+    np.fill_diagonal(Q, 0.0)
+    return Q
+
+
+def test_batch_config4_shapes_one_step(B):
+    """The batched-instance workload's own shapes in ONE launch: 512
+    instances with n drawn uniformly from [100, 2000] (the Wishart batch's
+    sizes), 64 replicas, one step from the Philox start. For every instance,
+    sampled rows (the first and last of each 128-row tile boundary pair and a
+    few random ones) of S and Y match the oracle's FP64 step (field of the
+    sampled rows by a library matmul, bias of those rows, the oracle's update)
+    within the BF16 field bound propagated through the update."""
+    R, dt, c0 = 64, np.float32(0.5), np.float32(0.3)
+    sizes = I.wishart_sizes(512, 100, 2000, seed=0)
+    ctxs, refs = [], []
+    rng = np.random.default_rng(123)
+    for m, n in enumerate(sizes):
+        n = int(n)
+        Q = _sym_normal(n, 5000 + m)
+        c = np.zeros(n)
+        ctxs.append(B.veloxq_create_dense(Q, c))
+        rows = {0, n - 1, min(127, n - 1), min(128, n - 1)}
+        rows |= set(rng.choice(n, size=4, replace=False).tolist())
+        rows = np.array(sorted(rows))
+        S0, Y0 = O.init_state(n, R, 4, 0.1)
+        F = O.field_dense_rows(Q, S0, rows)
+        b = O.bias_dense_rows(Q, c, rows)
+        S1, Y1 = O.update("bsb", F, b, 0.0, float(dt), 1.0, float(c0), S0[:, rows], Y0[:, rows])
+        dF = (2 * U + U * U) * O.abs_field_dense_rows(Q, S0, rows) + 1e-6
+        refs.append((rows, S1, Y1, dF))
+    sched = B.make_schedule(prec=1, readout_every=0, c0=float(c0), dt=float(dt))
+    B.veloxq_solve_batch(ctxs, R, 1, sched, seed=4, want_x=False)
+    assert B.veloxq_last_timing(ctxs[0]).main_launches == 1
+    for ctx, (rows, S1, Y1, dF) in zip(ctxs, refs):
+        n = ctx.info.n
+        S = torch.empty(R, n, device="cuda")
+        Y = torch.empty(R, n, device="cuda")
+        B.veloxq_batch_state_dev(ctx, R, S, Y)
+        torch.cuda.synchronize()
+        ti = torch.as_tensor(rows, device="cuda")
+        Sg, Yg = S[:, ti].cpu().numpy(), Y[:, ti].cpu().numpy()
+        dy = float(dt) * float(c0) * 0.5 * dF + 2e-6
+        ds = float(dt) * dy + 2e-6
+        assert np.all(np.abs(Yg - Y1) <= dy), n
+        assert np.all(np.abs(Sg - S1) <= ds), n
+    for ctx in ctxs:
+        ctx.destroy()
+
+
+def test_two_batches_on_two_streams(B):
+    """Two batches headed by different contexts, on two streams and from two
+    host threads at once, give exactly the results each gives alone: the
+    batched launch's scratch belongs to the batch's first context."""
+    import threading
+    sets = [[_sk(n, 70 + 10 * k + i) for i, n in enumerate(sizes)]
+            for k, sizes in enumerate(([90, 300, 210, 64], [150, 37, 400]))]
+    ctx_sets = [[B.veloxq_create_dense(Q, c) for Q, c in s] for s in sets]
+    sched = B.make_schedule(prec=1, readout_every=0)
+    alone = [B.veloxq_solve_batch(cs, 32, 150, sched, seed=5 + k) for k, cs in enumerate(ctx_sets)]
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for cs, st in zip(ctx_sets, streams):
+        for cx in cs:
+            B.veloxq_set_stream(cx, st.cuda_stream)
+    got, errs = [None, None], []
+
+    def run(k):
+        try:
+            got[k] = B.veloxq_solve_batch(ctx_sets[k], 32, 150, sched, seed=5 + k)
+        except Exception as e:                      # reported below
+            errs.append(e)
+
+    th = [threading.Thread(target=run, args=(k,)) for k in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join(timeout=300)
+    assert not errs, errs
+    for a, g in zip(alone, got):
+        assert np.array_equal(a["E"], g["E"])
+        for xa, xg in zip(a["x"], g["x"]):
+            assert np.array_equal(xa, xg)
+    for cs in ctx_sets:
+        for cx in cs:
+            cx.destroy()

@@ -355,8 +355,8 @@ def test_rho_and_K0(B, name):
 
 def test_rho_multi_launch_sparse(B):
     """A sparse problem too large for the one-CTA power iteration (n = 13824)
-    runs one launch per iteration with the rows walked backwards on odd
-    launches. Ferromagnetic periodic cubic lattice: rho = 6 exactly."""
+    takes the Lanczos estimate (rows walked backwards on odd steps).
+    Ferromagnetic periodic cubic lattice: rho = 6 exactly."""
     L = I.cubic_lattice_ising(24, seed=0)
     ctx = B.veloxq_create_csr(L.n, L.rowptr, L.col, np.abs(L.val).astype(np.int32))
     assert 6.0 * (1 - 2e-2) <= ctx.info.rho <= 6.0 * (1 + 1e-6)
@@ -366,6 +366,22 @@ def test_rho_multi_launch_dense_unaligned(B):
     """Dense, n % 4 != 0 and above the CSR size: the GEMV's scalar loop."""
     n = 517
     Q, c = I.sk_qubo(n, seed=3)
+    ctx = B.veloxq_create_dense(Q, c)
+    rho = O.spectral_radius(O.problem_from_dense(Q.astype(np.float64), c))
+    assert rho * (1 - 2e-2) <= ctx.info.rho <= rho * (1 + 1e-6)
+
+
+def test_rho_lanczos_wishart_and_sk(B):
+    """The Lanczos estimate on dense spectra of the benchmark families: a
+    Wishart planted instance (negative semi-definite coupling, rho at the
+    Marchenko-Pastur edge) and an SK instance above the CSR size, against the
+    oracle's dense eigensolver: from below, within 2%."""
+    w = I.wishart_ising(1200, 0.75, seed=8)
+    ctx = B.veloxq_create_ising_dense(-w["J"], None)
+    Qd, _ = O.ising_to_qubo(-w["J"], np.zeros(1200))
+    rho = O.spectral_radius(O.problem_from_dense(Qd))
+    assert rho * (1 - 2e-2) <= ctx.info.rho <= rho * (1 + 1e-6)
+    Q, c = I.sk_qubo(3000, seed=9)
     ctx = B.veloxq_create_dense(Q, c)
     rho = O.spectral_radius(O.problem_from_dense(Q.astype(np.float64), c))
     assert rho * (1 - 2e-2) <= ctx.info.rho <= rho * (1 + 1e-6)
@@ -425,6 +441,26 @@ def test_malformed_inputs_rejected(B):
     with pytest.raises(B.VeloxqError) as e:
         B.veloxq_solve(ctx, 4, 10, B.make_schedule(prec=B.VELOXQ_PREC_FP8))
     assert e.value.status == B.VELOXQ_EUNSUPPORTED
+
+
+def test_real_couplings_beyond_fixed_point_range(B):
+    """Real couplings whose absolute sum reaches 2^61 cannot keep exact int64
+    fixed-point energies: creation refuses them (dense and sparse) instead of
+    overflowing silently; just below the limit they are accepted and the
+    energy of a vector is the oracle's within its FP64 bound."""
+    big = np.array([[0.0, 3e18], [3e18, 0.0]])                 # sum |Q| = 6e18 > 2^61
+    with pytest.raises(B.VeloxqError) as e:
+        B.veloxq_create_dense(big)
+    assert e.value.status == B.VELOXQ_EUNSUPPORTED and "2^61" in e.value.message
+    with pytest.raises(B.VeloxqError) as e:
+        B.veloxq_create_csr(2, np.array([0, 1, 2]), np.array([1, 0], np.int32), np.array([3e18, 3e18]))
+    assert e.value.status == B.VELOXQ_EUNSUPPORTED
+    ok = np.array([[0.0, 5e17], [5e17, 0.25]])                 # sum |Q| just above 1e18 < 2^61
+    ctx = B.veloxq_create_dense(ok)
+    X = np.array([[1, 1], [1, 0], [0, 1]], np.uint8)
+    E = B.veloxq_energy(ctx, X)["E"]
+    Eo = O.energy(O.problem_from_dense(ok), X)
+    assert np.all(np.abs(E - Eo) <= 4 * 2.0 ** -52 * np.sum(np.abs(ok)))
 
 
 def test_degenerate_sizes(B):

@@ -430,6 +430,22 @@ def test_field_dense_rows_equals_full_field():
     assert np.all(O.abs_field_dense_rows(Q, S, rows) >= np.abs(full[:, rows]) - 1e-12)
 
 
+def test_bias_dense_rows():
+    """The sampled-rows bias equals the coordinate-list bias on a
+    non-symmetric matrix with c, and the closed form n + c_i for Q = all ones
+    (each row of Qs sums to n)."""
+    rng = np.random.default_rng(4)
+    n = 37
+    Q = rng.normal(size=(n, n))
+    c = rng.normal(size=n)
+    rows = np.array([0, 5, 36, 20])
+    b, _ = O.bias(O.problem_from_dense(Q, c))
+    assert np.allclose(O.bias_dense_rows(Q, c, rows), b[rows], atol=1e-12)
+    ones = np.ones((n, n))
+    assert np.array_equal(O.bias_dense_rows(ones, c, rows), n + c[rows])
+    assert np.array_equal(O.bias_dense_rows(ones, None, rows), np.full(rows.shape, float(n)))
+
+
 def test_dense_n20_ground_file_matches_enumeration():
     """tests/golden/dense_n20_ground.txt (written by make_dense_n20_ground.py)
     is the oracle's exhaustive minimum of the seeded dense n = 20 instance."""

@@ -1,12 +1,15 @@
 """veloxq_energy_dev_noalloc: the energy entry point for callers that cannot
-allocate device memory during a call (for example while a CUDA graph is
-being captured). It must give the same energies as veloxq_energy_dev, call
-after call, while its scratch is a fixed array shared by all calls. This
-file is collected last so that a run stopping at its first failure has run
-every other test before it."""
+allocate device memory during a call (code inside a custom allocator that must
+not re-enter cudaMalloc, processes with a fixed device-memory budget, loops
+that cannot absorb an allocation's synchronisation). It must give the same
+energies as veloxq_energy_dev, call after call, while its scratch is a fixed
+array shared by all calls; and those energies are the oracle's. This file is
+collected last so that a run stopping at its first failure has run every other
+test before it."""
 import numpy as np
 import pytest
 
+import oracle as O
 from paper_2501_19221_gb300 import instances as I
 
 pytestmark = pytest.mark.gpu
@@ -42,14 +45,22 @@ def test_noalloc_energy_matches_allocating_entry_point_twice(B):
     sparse = B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
     Q, c = I.sk_qubo(300, seed=2)
     dense = B.veloxq_create_dense(Q, c)
-    for ctx, n, integer in [(sparse, sp.n, True), (dense, 300, False)]:
+    p_sparse, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+    p_dense = O.problem_from_dense(Q.astype(np.float64), c)
+    for ctx, p, n, integer in [(sparse, p_sparse, sp.n, True), (dense, p_dense, 300, False)]:
         for call in range(2):                      # two calls in a row share the scratch
             X = I.random_binary(97 + 31 * call, n, seed=call + 5)
             E1, E2, I1, I2 = _both(B, ctx, X, integer)
             # same kernels, same fixed-point sums: identical results
             assert np.array_equal(E1, E2)
+            Eo = O.energy(p, X)
             if integer:
                 assert np.array_equal(I1, I2)
+                assert np.array_equal(I2, Eo)            # exact int64 energies
+            else:
+                # within the oracle's own FP64 summation bound
+                tol = (p.nnz + n) * 2.0 ** -52 * (np.sum(np.abs(Q)) + np.sum(np.abs(c)))
+                assert np.all(np.abs(E2 - Eo) <= tol)
 
 
 def test_noalloc_rejects_batches_beyond_its_scratch(B):
