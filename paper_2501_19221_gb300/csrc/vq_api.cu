@@ -182,6 +182,7 @@ struct TcRun {
     CUtensorMap mq, ms[2], ms_lo[2];
     void* sop[2];
     int terms = 1;
+    const CUtensorMap* lo() const { return terms == 2 ? ms_lo : nullptr; }
     const CUtensorMap* lo(int c) const { return terms == 2 ? &ms_lo[c] : nullptr; }
 };
 
@@ -192,6 +193,8 @@ int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t, int method = VELOXQ
     VQ_TRY(ctx->sop_a.ensure(b));
     VQ_TRY(ctx->sop_b.ensure(b));
     VQ_TRY(ctx->errw.ensure(sizeof(int) * 4));
+    // completion counters of multi-step runs, one per replica column block (sized before any capture)
+    VQ_TRY(ctx->tcdone.ensure(sizeof(uint32_t) * (size_t)div_up(R, 256)));
     // the K padding columns [n, n_pad) of both operand buffers must stay zero:
     // the epilogue never writes them
     VQ_CUDA(cudaMemsetAsync(ctx->sop_a.p, 0, b, ctx->stream));
@@ -237,17 +240,26 @@ int enqueue_loop(veloxq_ctx* ctx, veloxq_path path, int32_t R, const RunParams& 
     float* Y = ctx->y.as<float>();
     const float* at = ctx->a_table.as<float>();
     int np = nparts;
+    int cb = 0;   // tensor-core path: the operand of the next step is in sop[cb]
     for (int k = 0; k < p.K; ++k) {
         if (tc) {
-            const int c = k & 1;   // operand of this step in sop[c], next one into sop[c ^ 1]
-            VQ_TRY(tc_step(ctx, p.prec, R, tc->mq, tc->ms[c], tc->lo(c), cur, nxt, Y, tc->sop[c ^ 1], at, k, p.dt,
-                           p.a0, p.c0, nullptr, ctx->errw.as<int>(), rule_of(p)));
+            // every step up to the next readout in one launch
+            int k1 = k;
+            while (!is_readout(p, k1)) ++k1;
+            VQ_TRY(tc_run(ctx, p.prec, R, tc->mq, tc->ms, tc->lo(), cb, cur, nxt, Y, tc->sop, at, k, k1 + 1, p.dt,
+                          p.a0, p.c0, nullptr, ctx->errw.as<int>(), rule_of(p)));
+            const int L = k1 + 1 - k;
+            if (L & 1) {
+                std::swap(cur, nxt);
+                cb ^= 1;
+            }
+            k = k1;
         } else if (path == VELOXQ_PATH_DENSE) {
             VQ_TRY(dense_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr, rule_of(p)));
         } else {
             VQ_TRY(stream_step(ctx, R, cur, nxt, Y, at, k, p.dt, p.a0, p.c0, nullptr, rule_of(p)));
         }
-        std::swap(cur, nxt);
+        if (!tc) std::swap(cur, nxt);
         // an event node of the graph (a plain record during capture would only order streams)
         if (ev_steps && k == p.K - 1) VQ_CUDA(cudaEventRecordWithFlags(ev_steps, ctx->stream, cudaEventRecordExternal));
         if (!is_readout(p, k)) continue;
@@ -541,6 +553,11 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         VQ_CUDA(cudaEventRecord(ex->t3, ctx->stream));
         launches = 1 + (use_tc ? 1 : 0) + ex->graph_launches;   // init (+ operand) kernels + graph nodes
         main_launches = steps;
+        if (use_tc) {
+            // one launch per run of steps up to a readout
+            main_launches = 0;
+            for (int k = 0; k < steps; ++k) main_launches += is_readout(p, k) ? 1 : 0;
+        }
         if (use_tc || tc_e) VQ_TRY(check_err_word(ctx));
     }
     std::vector<int64_t> be((size_t)R);
@@ -753,8 +770,7 @@ int veloxq_field_dev(veloxq_ctx* ctx, int32_t R, veloxq_prec prec, const float* 
         VQ_TRY(tc_setup(ctx, prec, R, &tc));
         VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
         VQ_TRY(tc_quant_s(ctx, prec, R, S, tc.sop[0]));
-        VQ_TRY(tc_step(ctx, prec, R, tc.mq, tc.ms[0], tc.lo(0), S, nullptr, nullptr, nullptr, nullptr, 0, 0.f, 0.f,
-                       0.f, F, ctx->errw.as<int>()));
+        VQ_TRY(tc_field(ctx, prec, R, tc.mq, tc.ms[0], tc.lo(0), F, ctx->errw.as<int>()));
         return check_err_word(ctx);
     }
     if (prec != VELOXQ_PREC_FP32) return fail(VELOXQ_EUNSUPPORTED, "sparse contexts run the field in FP32 (or exact int8)");
@@ -795,13 +811,10 @@ int veloxq_steps_dev(veloxq_ctx* ctx, int32_t R, int32_t k_begin, int32_t k_coun
             VQ_TRY(tc_setup(ctx, p.prec, R, &tc, p.method));
             VQ_CUDA(cudaMemsetAsync(ctx->errw.p, 0, sizeof(int), ctx->stream));
             VQ_TRY(tc_quant_s(ctx, p.prec, R, cur, tc.sop[0], rule_of(p)));
-            int c = 0;
-            for (int k = k_begin; k < k_end; ++k) {
-                VQ_TRY(tc_step(ctx, p.prec, R, tc.mq, tc.ms[c], tc.lo(c), cur, nxt, Y, tc.sop[c ^ 1], at, k, p.dt,
-                               p.a0, p.c0, k == k_end - 1 ? F_last : nullptr, ctx->errw.as<int>(), rule_of(p)));
-                std::swap(cur, nxt);
-                c ^= 1;
-            }
+            // the whole range in one launch (the solve's form)
+            VQ_TRY(tc_run(ctx, p.prec, R, tc.mq, tc.ms, tc.lo(), 0, cur, nxt, Y, tc.sop, at, k_begin, k_end, p.dt,
+                          p.a0, p.c0, F_last, ctx->errw.as<int>(), rule_of(p)));
+            if (k_count & 1) std::swap(cur, nxt);
             VQ_CUDA(cudaMemcpyAsync(S, cur, sizeof(float) * nR, cudaMemcpyDeviceToDevice, ctx->stream));
             return check_err_word(ctx);
         }

@@ -200,8 +200,8 @@ int tc_energy(veloxq_ctx* ctx, int64_t R, const float* S, const uint8_t* X, int6
     for (int k = 0; k < ctx->eplanes; ++k) {
         CUtensorMap mp;
         VQ_TRY(tc_operand_map(&mp, ctx->eplane.as<__nv_bfloat16>() + (size_t)k * n * np, VELOXQ_PREC_BF16, n, np, true));
-        VQ_TRY(tc_step(ctx, VELOXQ_PREC_BF16, (int32_t)R, mp, mx, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                       0, 0.f, 0.f, 0.f, ctx->efield.as<float>(), ctx->errw.as<int>()));
+        VQ_TRY(tc_field(ctx, VELOXQ_PREC_BF16, (int32_t)R, mp, mx, nullptr, ctx->efield.as<float>(),
+                        ctx->errw.as<int>()));
         if (X)
             k_plane_combine<true><<<cg, 256, 0, st>>>(R, n, k, ctx->efield.as<float>(), nullptr, X,
                                                       ctx->dfix.as<int64_t>(), parts);

@@ -123,6 +123,7 @@ struct veloxq_ctx {
     vq::DevBuf sop_a, sop_b;      // tensor-core operand copies of S (ping-pong)
     vq::DevBuf dpart;             // float [ksplit][R][n] split-k partial fields of the FP32 dense step
     vq::DevBuf errw;              // device error word of bounded waits
+    vq::DevBuf tcdone;            // uint32 [replica column blocks] completion counters of a tensor-core run
     int stream_unroll = 0;        // gather variant of the streaming kernels: 1, 4, or 6 (rows of exactly
                                   // 6 couplings); 0: not tuned yet
     int32_t stream_tuned_R = -1;  // replica count the variant was tuned for
@@ -208,10 +209,20 @@ int tc_maps(veloxq_ctx* ctx, int prec, int terms, int32_t R, void* sop0, void* s
 int tc_quant_s(veloxq_ctx* ctx, int prec, int32_t R, const float* S, void* sop, const Rule& rule = Rule());
 size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int terms, int32_t R);
 int tc_wait_selftest(long long budget, int* code_out);   // the bounded wait run out on purpose
-int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur,
-            const CUtensorMap* ms_lo_cur, const float* S_cur, float* S_nxt, float* Y, void* sop_nxt,
-            const float* a_table, int k, float dt, float a0, float c0, float* F_out, int* err,
-            const Rule& rule = Rule());
+// Steps k_begin .. k_end - 1 in one launch (tiles of consecutive steps
+// overlap, each waiting only for the column block of the state it reads).
+// ms, ms_lo: maps of the two operand buffers sop[0..1] (their lo planes with
+// two FP8 terms, else NULL); the first step reads the operand in sop[cur] and
+// the state in S_a, and the steps alternate between the two buffers of each
+// (after an odd number of steps the state is in S_b and the operand in
+// sop[cur ^ 1]). F_out (or NULL): the field of the last step.
+int tc_run(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap* ms,
+           const CUtensorMap* ms_lo, int cur, const float* S_a, float* S_b, float* Y, void* const* sop,
+           const float* a_table, int k_begin, int k_end, float dt, float a0, float c0, float* F_out, int* err,
+           const Rule& rule = Rule());
+// The field alone, F = Qoff S, of the operand behind ms (and ms_lo).
+int tc_field(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms,
+             const CUtensorMap* ms_lo, float* F_out, int* err);
 int tc_operand_map(CUtensorMap* m, void* base, int prec, int64_t rows, int64_t n_pad, bool a_operand);
 int launch_sum_parts(veloxq_ctx* ctx, int64_t B, int nparts, const int64_t* parts, double* E, int64_t* E_int);
 

@@ -56,7 +56,7 @@ static_assert(stages_of<2>() * stage_bytes<2>() == PIPE_BYTES, "both stage forms
 constexpr size_t TC_SMEM = (size_t)PIPE_BYTES + 1024 /*align*/ + 256 /*barriers, tensor-memory slot*/;
 constexpr long long kWaitCycles = 4000000000LL;   // ~2 s at 2 GHz
 
-enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4, TC_ERR_SELFTEST = 8 };
+enum { TC_ERR_PRODUCER = 1, TC_ERR_MMA = 2, TC_ERR_EPILOGUE = 4, TC_ERR_SELFTEST = 8, TC_ERR_DEPEND = 16 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -136,6 +136,52 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
         ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cl)
         : "memory");
 }
+// The same with an L2 cache policy (the coupling operand, which every column
+// block of every step reads again, is kept in L2 ahead of streaming data).
+__device__ __forceinline__ void tma_load_2d_pair_hint(void* dst, const CUtensorMap* map, int x, int y,
+                                                      uint32_t bar_cl, uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2.L2::cache_hint "
+        "[%0], [%1, {%2, %3}], [%4], %5;"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cl), "l"(pol)
+        : "memory");
+}
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+// ---- completion counters between CTAs of one grid (steps of a run) ----
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void red_release_add(uint32_t* p, uint32_t v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+// Generic-proxy writes to global memory made visible to (and ordered with)
+// the async proxy: the bulk tensor copies of another CTA read them.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+// Bounded wait until *c >= target: false (and the error word set) if it is
+// not reached within the budget or another thread already gave up.
+__device__ __forceinline__ bool count_wait(const uint32_t* c, uint32_t target, int* err, int code) {
+    const long long t0 = clock64();
+    uint32_t spins = 0;
+    while (ld_acquire_u32(c) < target) {
+        if ((++spins & 255u) == 0) {
+            if (*(volatile int*)err) return false;
+            if (clock64() - t0 > kWaitCycles) {
+                atomicOr(err, code);
+                return false;
+            }
+        }
+    }
+    return true;
+}
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -214,19 +260,23 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&v)[16]) {
 }
 
 struct TcArgs {
-    int32_t n, R, n_pad, k;
+    int32_t n, R, n_pad;
+    int32_t k, k_end;        // steps k .. k_end - 1 of the schedule (one launch)
     float dt, a0, c0;
-    const float* S_cur;      // [R][n] fp32
-    float* S_nxt;            // [R][n] fp32 (null: field only)
+    const float* S_a;        // [R][n] fp32 state of the first step (even steps of the run read it)
+    float* S_b;              // [R][n] the other state buffer (null: field only)
     float* Y;                // [R][n]
-    void* sop_nxt;           // [R][n_pad] operand of the next step (null: do not write)
+    void* sop[2];            // [R][n_pad] per term: operand buffers; the first step reads sop[cur]
+    int32_t cur;
+    int32_t colmajor;        // tiles of a step column block by column block (runs of several steps)
     const float* bf;         // [n]
     const float* qscale;     // [n] FP8 row scales (FP8 only)
     const float* a_table;
-    float* F_out;            // [R][n] or null
+    float* F_out;            // [R][n] field of the last step, or null
     int* err;
     float alpha;             // PA momentum
-    int64_t plane;           // elements from the hi plane of sop_nxt to its lo plane (two S terms)
+    int64_t plane;           // elements from the hi plane of an operand buffer to its lo plane (two S terms)
+    uint32_t* done;          // [NT] epilogue warps finished per replica column block (zeroed per launch)
 };
 
 // Operand of s: bf16(s); or v = 448 s as hi = e4m3(v) and, with two terms,
@@ -247,13 +297,34 @@ __device__ __forceinline__ void store_op(void* base, int64_t idx, int64_t plane,
     }
 }
 
+// One launch runs steps k .. k_end - 1. The pairs walk the pair tiles of all
+// those steps, g = pair, pair + pairs, ... with g = j * tiles + t for step
+// k + j. A step's tile (row block r, replica column block c) reads the
+// operand of column block c over every variable, which the previous step's
+// tiles (all r, same c) write: with colmajor, t = c * MT + r, so a step's
+// first column block is ready as soon as the previous step's is, and pairs
+// flow from one step into the next without a grid-wide barrier. The
+// dependency is counted per column block: every epilogue warp adds 1 to
+// done[c] (release) once its rows and columns of the tile are written; a
+// tile of step j > 0 starts loading the operand (and the epilogue reads its
+// state) only after done[c] >= 16 MT j (acquire), i.e. when the whole column
+// block of every earlier step of the launch is written. That also orders the
+// reuse of the ping-pong buffers: what a tile overwrites was last read by the
+// previous step's tiles of the same column block. A pair only ever waits for
+// tiles with a lower g, all CTAs of the grid are resident (one per SM, at
+// most the co-resident clusters), and every wait is bounded.
+// One step (k_end = k + 1) is the plain fused step (row-major tiles, odd
+// steps walked backwards so that a step starts on the state the previous
+// one wrote last).
 // METHOD: the integrator (veloxq_method), a template parameter so that each
 // form keeps its own register allocation. TERMS: S operand terms (1, or 2 for
-// FP8 hi + lo; tmB2 maps the lo plane, unused with one term).
+// FP8 hi + lo; tmL* map the lo planes, unused with one term).
 template <int PREC, int TERMS, bool FIELD_ONLY, int METHOD>
 __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUtensorMap tmA,
-                                                    const __grid_constant__ CUtensorMap tmB,
-                                                    const __grid_constant__ CUtensorMap tmB2, const TcArgs a) {
+                                                    const __grid_constant__ CUtensorMap tmB0,
+                                                    const __grid_constant__ CUtensorMap tmB1,
+                                                    const __grid_constant__ CUtensorMap tmL0,
+                                                    const __grid_constant__ CUtensorMap tmL1, const TcArgs a) {
     constexpr int STAGES = stages_of<TERMS>();
     constexpr uint32_t STAGE_BYTES = stage_bytes<TERMS>();
     extern __shared__ uint8_t smem_raw[];
@@ -273,10 +344,21 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     constexpr int KSTEP_B = 32;                  // bytes of K per MMA (16 bf16 / 32 e4m3)
     const int num_kb = (a.n_pad + BK - 1) / BK;
     const int MT = (a.n + 2 * BM - 1) / (2 * BM), NT = (a.R + BN - 1) / BN;
-    const int tiles = MT * NT;                   // pair tile t: rows (t / NT) * 2BM, replicas (t % NT) * BN
-    // Odd steps walk the tiles in reverse, so a step starts on the tiles whose
-    // state the previous step wrote last (still in L2).
-    const bool rev = (a.k & 1) != 0;
+    const int tiles = MT * NT;
+    const int steps = a.k_end - a.k;
+    const int64_t work = (int64_t)steps * tiles;
+    const uint32_t per_col = 16u * (uint32_t)MT;   // epilogue warps of one column block of one step
+    // tile t of step j: row block r, column block c
+    auto tile_rc = [&](int j, int t, int& r, int& c) {
+        if (a.colmajor) {
+            c = t / MT;
+            r = t - c * MT;
+        } else {
+            const int tt2 = ((a.k + j) & 1) ? tiles - 1 - t : t;
+            r = tt2 / NT;
+            c = tt2 - r * NT;
+        }
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -298,27 +380,38 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     // Programmatic dependent launch: everything above (barriers, tensor
     // memory, the cluster handshake) may overlap the previous kernel on the
     // stream; nothing it wrote is read before this wait returns. The next
-    // step may then be scheduled, onto SMs this grid frees as it exits (every
-    // CTA of this grid is resident by now, one per SM).
+    // kernel may then be scheduled, onto SMs this grid frees as it exits
+    // (every CTA of this grid is resident by now, one per SM).
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     if (warp == 0) {
         if (lane == 0) {
+            const uint64_t qpol = l2_evict_last_policy();
             uint32_t it = 0;
             bool ok = true;
-            for (int tw = pair; tw < tiles && ok; tw += pairs) {
-                const int t = rev ? tiles - 1 - tw : tw;
-                const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN + (int)rank * BNH;
+            for (int64_t g = pair; g < work && ok; g += pairs) {
+                const int j = (int)(g / tiles), t = (int)(g - (int64_t)j * tiles);
+                int r, c;
+                tile_rc(j, t, r, c);
+                const int m0 = r * (2 * BM) + (int)rank * BM, n0 = c * BN + (int)rank * BNH;
+                // the previous steps' column block c: every operand block this tile reads
+                if (j > 0) {
+                    if (!count_wait(a.done + c, per_col * (uint32_t)j, a.err, TC_ERR_DEPEND)) break;
+                    fence_proxy_async_global();
+                }
+                const int buf = (a.cur + j) & 1;
+                const CUtensorMap* mb = buf ? &tmB1 : &tmB0;
+                const CUtensorMap* ml = buf ? &tmL1 : &tmL0;
                 for (int kb = 0; kb < num_kb; ++kb) {
                     const uint32_t s = it % STAGES, u = it / STAGES;
                     if (u > 0 && !mbar_wait<true>(&empty[s], (u - 1) & 1, a.err, TC_ERR_PRODUCER)) { ok = false; break; }
                     uint8_t* sa = smem + s * STAGE_BYTES;
                     if (leader) mbar_expect_tx(&full[s], 2 * STAGE_BYTES);
                     const uint32_t fb = mapa(smem_u32(&full[s]), 0);
-                    tma_load_2d_pair(sa, &tmA, kb * BK, m0, fb);
-                    tma_load_2d_pair(sa + A_BYTES, &tmB, kb * BK, n0, fb);
-                    if constexpr (TERMS == 2) tma_load_2d_pair(sa + A_BYTES + B_BYTES, &tmB2, kb * BK, n0, fb);
+                    tma_load_2d_pair_hint(sa, &tmA, kb * BK, m0, fb, qpol);
+                    tma_load_2d_pair(sa + A_BYTES, mb, kb * BK, n0, fb);
+                    if constexpr (TERMS == 2) tma_load_2d_pair(sa + A_BYTES + B_BYTES, ml, kb * BK, n0, fb);
                     ++it;
                 }
             }
@@ -328,7 +421,7 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
             constexpr uint32_t idesc = instr_desc<PREC>();
             uint32_t it = 0, tt = 0;
             bool ok = true;
-            for (int tw = pair; tw < tiles && ok; tw += pairs, ++tt) {
+            for (int64_t g = pair; g < work && ok; g += pairs, ++tt) {
                 const uint32_t b = tt & 1u;
                 if (tt >= 2 && !mbar_wait<true>(&acce[b], ((tt >> 1) - 1) & 1u, a.err, TC_ERR_MMA)) { ok = false; break; }
                 tc_fence_after();
@@ -358,14 +451,23 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
         // [0, BN/2), the next four the rest
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
-        const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + a.k);
-        const float lam = (FIELD_ONLY || METHOD != vqd::METHOD_PA) ? 0.0f : vqd::pa_lambda(a_k, a.a0);
         const uint32_t acce_cl = mapa(smem_u32(&acce[0]), 0);
+        constexpr int CW = 16;   // columns per tensor-memory load
+        const int c_begin = half * (BN / (2 * CW)), c_end = c_begin + BN / (2 * CW);   // 8 chunks, even
         uint32_t tt = 0;
-        for (int tw = pair; tw < tiles; tw += pairs, ++tt) {
+        for (int64_t g = pair; g < work; g += pairs, ++tt) {
             const uint32_t b = tt & 1u;
-            const int t = rev ? tiles - 1 - tw : tw;
-            const int m0 = (t / NT) * (2 * BM) + (int)rank * BM, n0 = (t % NT) * BN;
+            const int j = (int)(g / tiles), t = (int)(g - (int64_t)j * tiles);
+            int r, c;
+            tile_rc(j, t, r, c);
+            const int k = a.k + j;
+            const float a_k = FIELD_ONLY ? 0.0f : __ldg(a.a_table + k);
+            const float lam = (FIELD_ONLY || METHOD != vqd::METHOD_PA) ? 0.0f : vqd::pa_lambda(a_k, a.a0);
+            const float* S_cur = (j & 1) ? a.S_b : a.S_a;
+            float* S_nxt = (j & 1) ? const_cast<float*>(a.S_a) : a.S_b;
+            void* sop_nxt = a.sop[(a.cur + j + 1) & 1];
+            float* F_out = j == steps - 1 ? a.F_out : nullptr;
+            const int m0 = r * (2 * BM) + (int)rank * BM, n0 = c * BN;
             const int row = m0 + q * 32 + lane;
             const bool row_ok = row < a.n;
             float fscale = 1.0f, bi = 0.0f;
@@ -373,43 +475,49 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
                 if constexpr (PREC == 2) fscale = __ldg(a.qscale + row) * (1.0f / 448.0f);
                 if constexpr (!FIELD_ONLY) bi = __ldg(a.bf + row);
             }
-            constexpr int CW = 16;   // columns per tensor-memory load
-            const int c_begin = half * (BN / (2 * CW)), c_end = c_begin + BN / (2 * CW);   // 8 chunks, even
+            // the state of these rows was written by the previous step's tile
+            if (j > 0) {
+                bool got = false;
+                if (lane == 0) got = count_wait(a.done + c, per_col * (uint32_t)j, a.err, TC_ERR_DEPEND);
+                if (__shfl_sync(0xffffffffu, got ? 1 : 0, 0) == 0) break;
+                (void)ld_acquire_u32(a.done + c);
+            }
             // Positions and momenta of a chunk: loaded one chunk ahead of its
             // use (the first before the accumulator is ready), so two chunks'
-            // loads are in flight while one is updated.
+            // loads are in flight while one is updated. They are read once per
+            // step and kept out of L2's way (evict-first).
             float sv0[CW], yv0[CW], sv1[CW], yv1[CW];
-            auto load_chunk = [&](int c, float (&sv)[CW], float (&yv)[CW]) {
+            auto load_chunk = [&](int cc, float (&sv)[CW], float (&yv)[CW]) {
                 if constexpr (!FIELD_ONLY) {
-                    const int r0 = n0 + c * CW;
+                    const int r0 = n0 + cc * CW;
 #pragma unroll
-                    for (int j = 0; j < CW; ++j) {
-                        const bool ok = row_ok && r0 + j < a.R;
-                        const int64_t p = (int64_t)(r0 + j) * a.n + row;
-                        sv[j] = ok ? a.S_cur[p] : 0.0f;
-                        yv[j] = ok ? a.Y[p] : 0.0f;
+                    for (int jj = 0; jj < CW; ++jj) {
+                        const bool ok = row_ok && r0 + jj < a.R;
+                        const int64_t p = (int64_t)(r0 + jj) * a.n + row;
+                        sv[jj] = ok ? __ldcs(S_cur + p) : 0.0f;
+                        yv[jj] = ok ? __ldcs(a.Y + p) : 0.0f;
                     }
                 }
             };
-            auto update_chunk = [&](int c, const float (&sv)[CW], const float (&yv)[CW]) {
+            auto update_chunk = [&](int cc, const float (&sv)[CW], const float (&yv)[CW]) {
                 uint32_t v[CW];
-                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)(c * CW), v);
-                const int r0 = n0 + c * CW;
+                tmem_ld16(tmem + ((uint32_t)(q * 32) << 16) + b * BN + (uint32_t)(cc * CW), v);
+                const int r0 = n0 + cc * CW;
 #pragma unroll
-                for (int j = 0; j < CW; ++j) {
-                    const bool ok = row_ok && r0 + j < a.R;
-                    const int64_t p = (int64_t)(r0 + j) * a.n + row;
-                    const float F = __uint_as_float(v[j]) * fscale;
-                    if (ok && a.F_out) a.F_out[p] = F;
+                for (int jj = 0; jj < CW; ++jj) {
+                    const bool ok = row_ok && r0 + jj < a.R;
+                    const int64_t p = (int64_t)(r0 + jj) * a.n + row;
+                    const float F = __uint_as_float(v[jj]) * fscale;
+                    if (ok && F_out) F_out[p] = F;
                     if constexpr (!FIELD_ONLY) {
-                        float s = sv[j], y = yv[j];
+                        float s = sv[jj], y = yv[jj];
                         if constexpr (METHOD == vqd::METHOD_PA) vqd::pa_update(F, bi, lam, a.dt, a.alpha, a.c0, s, y);
                         else if constexpr (METHOD == vqd::METHOD_ASB) vqd::asb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
                         else vqd::bsb_update(F, bi, a_k, a.dt, a.a0, a.c0, s, y);
                         if (ok) {
-                            a.S_nxt[p] = s;
-                            a.Y[p] = y;
-                            store_op<PREC, TERMS>(a.sop_nxt, (int64_t)(r0 + j) * a.n_pad + row, a.plane,
+                            __stcs(S_nxt + p, s);
+                            __stcs(a.Y + p, y);
+                            store_op<PREC, TERMS>(sop_nxt, (int64_t)(r0 + jj) * a.n_pad + row, a.plane,
                                                   METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
                         }
                     }
@@ -419,16 +527,25 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
             if (!mbar_wait<true>(&accf[b], (tt >> 1) & 1u, a.err, TC_ERR_EPILOGUE)) break;
             tc_fence_after();
 #pragma unroll 1
-            for (int c = c_begin; c < c_end; c += 2) {
-                load_chunk(c + 1, sv1, yv1);
-                update_chunk(c, sv0, yv0);
-                if (c + 2 < c_end) load_chunk(c + 2, sv0, yv0);
-                update_chunk(c + 1, sv1, yv1);
+            for (int cc = c_begin; cc < c_end; cc += 2) {
+                load_chunk(cc + 1, sv1, yv1);
+                update_chunk(cc, sv0, yv0);
+                if (cc + 2 < c_end) load_chunk(cc + 2, sv0, yv0);
+                update_chunk(cc + 1, sv1, yv1);
             }
-            // hand the accumulator buffer back to the even CTA's MMA thread
+            // hand the accumulator buffer back to the even CTA's MMA thread,
+            // and count this warp's part of the tile as written (for the
+            // bulk copies and loads of the next step's tiles)
+            if (steps > 1) {
+                fence_proxy_async_global();
+                __threadfence();
+            }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_remote(acce_cl + b * 8);
+            if (lane == 0) {
+                mbar_arrive_remote(acce_cl + b * 8);
+                if (steps > 1) red_release_add(a.done + c, 1u);
+            }
         }
     }
     // neither CTA leaves while the other may still read its shared memory or
@@ -608,7 +725,8 @@ size_t tc_sop_bytes(veloxq_ctx* ctx, int prec, int terms, int32_t R) {
 }
 
 namespace {
-using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const TcArgs);
+using TcKernel = void (*)(const CUtensorMap, const CUtensorMap, const CUtensorMap, const CUtensorMap,
+                          const CUtensorMap, const TcArgs);
 
 template <int PREC, int TERMS> TcKernel pick_kernel(bool field_only, int method) {
     if (field_only) return k_tc_step<PREC, TERMS, true, 0>;
@@ -617,47 +735,28 @@ template <int PREC, int TERMS> TcKernel pick_kernel(bool field_only, int method)
     return k_tc_step<PREC, TERMS, false, vqd::METHOD_BSB>;
 }
 
-// SMs and co-resident CTA pairs of the step kernel, per device
-struct TcDevice {
-    int sms = 0, max_pairs = 0;
-};
+// co-resident CTA pairs of the step kernel, per device
 constexpr int kMaxDevices = 64;
-TcDevice g_tcdev[kMaxDevices];
+int g_max_pairs[kMaxDevices];
+
+// Steps per launch at most: the completion counters (16 MT per column block
+// and step) stay far below 2^32.
+constexpr int kMaxRunSteps = 4096;
 }  // namespace
 
-// One fused step (or the field only when S_nxt is null): reads Sop through
-// mapS_cur (and its lo plane through ms_lo_cur with two terms), writes the
-// next operand into sop_nxt.
-int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms_cur,
-            const CUtensorMap* ms_lo_cur, const float* S_cur, float* S_nxt, float* Y, void* sop_nxt,
-            const float* a_table, int k, float dt, float a0, float c0, float* F_out, int* err, const Rule& rule) {
-    const bool field_only = S_nxt == nullptr;
+int tc_run(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap* ms,
+           const CUtensorMap* ms_lo, int cur, const float* S_a, float* S_b, float* Y, void* const* sop,
+           const float* a_table, int k_begin, int k_end, float dt, float a0, float c0, float* F_out, int* err,
+           const Rule& rule) {
+    const bool field_only = S_b == nullptr;
+    if (k_end <= k_begin) return VELOXQ_OK;
+    if (field_only && k_end != k_begin + 1) return fail(VELOXQ_EINVAL, "the field alone is one step");
     // the field alone takes s itself as the operand
     const int terms = tc_terms(prec, field_only ? VELOXQ_METHOD_BSB : rule.method);
-    if (terms == 2 && !ms_lo_cur) return fail(VELOXQ_EINVAL, "two-term FP8 operand without its lo-plane map");
-    TcArgs a;
-    a.n = (int32_t)ctx->n;
-    a.R = R;
-    a.n_pad = (int32_t)tc_pad(ctx->n);
-    a.k = k;
-    a.dt = dt;
-    a.a0 = a0;
-    a.c0 = c0;
-    a.S_cur = S_cur;
-    a.S_nxt = S_nxt;
-    a.Y = Y;
-    a.sop_nxt = sop_nxt;
-    a.bf = ctx->bf.as<float>();
-    a.qscale = ctx->qscale8.as<float>();
-    a.a_table = a_table;
-    a.F_out = F_out;
-    a.err = err;
-    a.alpha = rule.alpha;
-    a.plane = (int64_t)R * a.n_pad;
+    if (terms == 2 && !ms_lo) return fail(VELOXQ_EINVAL, "two-term FP8 operand without its lo-plane maps");
     if (ctx->device < 0 || ctx->device >= kMaxDevices) return fail(VELOXQ_EUNSUPPORTED, "device ordinal out of range");
-    TcDevice& dv = g_tcdev[ctx->device];
-    if (!dv.sms) dv.sms = device_sms(ctx->device);
-    const int64_t tiles = div_up(ctx->n, 2 * BM) * div_up(R, BN);
+    const int sms = device_sms(ctx->device);
+    const int64_t MT = div_up(ctx->n, 2 * BM), NT = div_up(R, BN), tiles = MT * NT;
     TcKernel fn;
     if (prec == VELOXQ_PREC_BF16) fn = pick_kernel<1, 1>(field_only, rule.method);
     else if (terms == 2) fn = pick_kernel<2, 2>(field_only, rule.method);
@@ -678,22 +777,71 @@ int tc_step(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const C
     cfg.numAttrs = 1;
     // as many pairs as can be resident at once (one CTA per SM; every form
     // has the same block size and shared memory)
-    if (!dv.max_pairs) {
-        cfg.gridDim = dim3((unsigned)(dv.sms & ~1));
+    int& max_pairs = g_max_pairs[ctx->device];
+    if (!max_pairs) {
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
         int c = 0;
         if (cudaOccupancyMaxActiveClusters(&c, fn, &cfg) != cudaSuccess || c < 1) {
             cudaGetLastError();
-            c = dv.sms / 2;
+            c = sms / 2;
         }
-        dv.max_pairs = std::min(c, dv.sms / 2);
+        max_pairs = std::max(1, std::min(c, sms / 2));
     }
-    const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles, dv.max_pairs));
-    cfg.gridDim = dim3((unsigned)(2 * pairs));
-    cfg.numAttrs = 2;   // with programmatic dependent launch (the occupancy query above used the cluster only)
-    const CUtensorMap& lo = terms == 2 ? *ms_lo_cur : ms_cur;
-    VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms_cur, lo, a));
-    VQ_LAUNCH_CHECK("tc step");
+    const CUtensorMap& lo0 = terms == 2 ? ms_lo[0] : ms[0];
+    const CUtensorMap& lo1 = terms == 2 ? ms_lo[1] : ms[1];
+    for (int k0 = k_begin; k0 < k_end; k0 += kMaxRunSteps) {
+        const int k1 = std::min(k_end, k0 + kMaxRunSteps);
+        const int steps = k1 - k0;
+        TcArgs a;
+        a.n = (int32_t)ctx->n;
+        a.R = R;
+        a.n_pad = (int32_t)tc_pad(ctx->n);
+        a.k = k0;
+        a.k_end = k1;
+        a.dt = dt;
+        a.a0 = a0;
+        a.c0 = c0;
+        // a launch after an odd number of steps starts from the other buffers
+        const bool flip = ((k0 - k_begin) & 1) != 0;
+        a.S_a = flip ? S_b : S_a;
+        a.S_b = field_only ? nullptr : (flip ? const_cast<float*>(S_a) : S_b);
+        a.Y = Y;
+        a.sop[0] = sop ? sop[0] : nullptr;
+        a.sop[1] = sop ? sop[1] : nullptr;
+        a.cur = (cur + (k0 - k_begin)) & 1;
+        a.colmajor = steps > 1 ? 1 : 0;
+        a.bf = ctx->bf.as<float>();
+        a.qscale = ctx->qscale8.as<float>();
+        a.a_table = a_table;
+        a.F_out = k1 == k_end ? F_out : nullptr;
+        a.err = err;
+        a.alpha = rule.alpha;
+        a.plane = (int64_t)R * a.n_pad;
+        a.done = nullptr;
+        if (steps > 1) {
+            // sized by the caller before any stream capture (256 replicas per column block)
+            if (ctx->tcdone.bytes < sizeof(uint32_t) * (size_t)NT)
+                return fail(VELOXQ_EINVAL, "tensor-core run without its completion counters");
+            VQ_CUDA(cudaMemsetAsync(ctx->tcdone.p, 0, sizeof(uint32_t) * (size_t)NT, ctx->stream));
+            a.done = ctx->tcdone.as<uint32_t>();
+        }
+        const int64_t pairs = std::max<int64_t>(1, std::min<int64_t>(tiles * steps, max_pairs));
+        cfg.gridDim = dim3((unsigned)(2 * pairs));
+        cfg.numAttrs = 2;   // with programmatic dependent launch (the occupancy query above used the cluster only)
+        VQ_CUDA(cudaLaunchKernelEx(&cfg, fn, mq, ms[0], ms[1], lo0, lo1, a));
+        VQ_LAUNCH_CHECK("tc step");
+    }
     return VELOXQ_OK;
+}
+
+// The field alone, F = Qoff S, from the operand behind ms (and ms_lo).
+int tc_field(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap& ms,
+             const CUtensorMap* ms_lo, float* F_out, int* err) {
+    const CUtensorMap mss[2] = {ms, ms};
+    CUtensorMap lo[2];
+    if (ms_lo) lo[0] = lo[1] = *ms_lo;
+    return tc_run(ctx, prec, R, mq, mss, ms_lo ? lo : nullptr, 0, nullptr, nullptr, nullptr, nullptr, nullptr, 0, 1,
+                  0.f, 0.f, 0.f, F_out, err, Rule());
 }
 
 }  // namespace vq

@@ -226,4 +226,80 @@ def test_tc_solve_outputs_consistent(B, prec):
     # it actually optimises: far below random vectors
     assert out["E"] < np.min(O.energy(p, I.random_binary(256, n, seed=2)))
     t = B.veloxq_last_timing(ctx)
-    assert t.path == 3 and t.main_launches == 400
+    # one launch per run of steps up to a readout: 400 steps, a readout every 40
+    assert t.path == 3 and t.main_launches == 10
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,R", [(2048, 256), (3000, 300)])
+def test_tc_field_mid_sizes(B, prec, n, R):
+    """Mid-size shapes (8 and 24 pair tiles, ragged row and replica tiles):
+    the field matches the oracle within the rounding bound on sampled rows
+    (tile boundaries included), and two runs give the same bits."""
+    Q, _ = I.sk_qubo(n, seed=11)
+    ctx = B.veloxq_create_dense(Q, np.zeros(n))
+    S = I.uniform_state(R, n, seed=12)
+    F = torch.empty(R, n, device="cuda")
+    F2 = torch.empty(R, n, device="cuda")
+    B.veloxq_field_dev(ctx, R, prec, _cuda(S), F)
+    B.veloxq_field_dev(ctx, R, prec, _cuda(S), F2)
+    torch.cuda.synchronize()
+    assert torch.equal(F, F2)
+    rows = np.sort(np.random.default_rng(2).choice(n, size=128, replace=False))
+    rows = np.unique(np.concatenate([rows, [0, 255, 256, n - 1]]))
+    Fg = F[:, torch.as_tensor(rows, device="cuda")].cpu().numpy().astype(np.float64)
+    ref = O.field_dense_rows(Q, S, rows)
+    scale = O.abs_field_dense_rows(Q, S, rows)
+    assert np.all(np.abs(Fg - ref) <= _elem_bound(prec, scale, _qoff_rows(Q, rows), S))
+    assert np.linalg.norm(Fg - ref) / np.linalg.norm(ref) <= NORM_BAR[prec]
+
+
+@pytest.mark.parametrize("method", [0, 2])
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,R", [(3000, 1024), (700, 96)])
+def test_tc_run_equals_single_steps(B, prec, method, n, R):
+    """Several steps in one launch (the solve's form: tiles of consecutive
+    steps overlap, each waiting for the column block of the state it reads)
+    give bit for bit the state and last field of the same steps launched one
+    at a time: the per-tile arithmetic is the same, only the schedule differs."""
+    if method == 2 and prec == FP8_ONE_TERM:
+        pytest.skip("Parallel Annealing's FP8 forms are the same run")
+    Q, c = I.sk_qubo(n, seed=13)
+    ctx = B.veloxq_create_dense(Q, c)
+    sched = B.make_schedule(prec=prec, method=method)
+    K, k0, steps = 100, 7, 20
+    runs = []
+    for one_launch in (True, False):
+        St = torch.empty(R, n, device="cuda")
+        Yt = torch.empty(R, n, device="cuda")
+        Ft = torch.empty(R, n, device="cuda")
+        B.veloxq_init_state_dev(ctx, R, 5, 0.3, St, Yt)
+        if one_launch:
+            B.veloxq_steps_dev(ctx, R, k0, steps, K, sched, St, Yt, Ft)
+        else:
+            for k in range(k0, k0 + steps):
+                B.veloxq_steps_dev(ctx, R, k, 1, K, sched, St, Yt, Ft)
+        torch.cuda.synchronize()
+        runs.append((St, Yt, Ft))
+    for a, b in zip(*runs):
+        assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_tc_steps_deterministic(B, prec):
+    """Ten fused steps in one launch at the dense benchmark's shape (n = 8192,
+    1024 replicas: 128 pair tiles per step over the pairs): two runs from the
+    same state give the same bits."""
+    n, R = 8192, 1024
+    Q, c = I.sk_qubo(n, seed=0)
+    ctx = B.veloxq_create_dense(Q, c)
+    sched = B.make_schedule(prec=prec)
+    outs = []
+    for _ in range(2):
+        St = torch.empty(R, n, device="cuda")
+        Yt = torch.empty(R, n, device="cuda")
+        B.veloxq_init_state_dev(ctx, R, 3, 0.1, St, Yt)
+        B.veloxq_steps_dev(ctx, R, 0, 10, 200, sched, St, Yt, None)
+        torch.cuda.synchronize()
+        outs.append((St, Yt))
+    assert torch.equal(outs[0][0], outs[1][0]) and torch.equal(outs[0][1], outs[1][1])
