@@ -119,35 +119,50 @@ __global__ void k_dense_rows(const T* __restrict__ q, int64_t n, double* rowsum,
     }
 }
 
-// Per column: off-diagonal column sum (coalesced over columns).
+// Per column: off-diagonal column sums, as partial sums over chunks of
+// kColRows rows (grid: column blocks x row chunks, loads coalesced over the
+// columns), then the chunks added in order for each column.
+constexpr int kColRows = 256;
 template <typename T>
-__global__ void k_dense_cols(const T* __restrict__ q, int64_t n, double* colsum) {
+__global__ void k_dense_cols_part(const T* __restrict__ q, int64_t n, double* __restrict__ part) {
+    const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t i0 = (int64_t)blockIdx.y * kColRows, i1 = i0 + kColRows < n ? i0 + kColRows : n;
+    if (j >= n) return;
+    double a = 0.0;
+#pragma unroll 8
+    for (int64_t i = i0; i < i1; ++i)
+        if (i != j) a += to_d(q[i * n + j]);
+    part[(int64_t)blockIdx.y * n + j] = a;
+}
+__global__ void k_dense_cols_sum(int64_t n, int chunks, const double* __restrict__ part, double* colsum) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     double a = 0.0;
-    // one column in row order; unrolled so that many rows' loads are in
-    // flight ahead of the (sequential) additions
-#pragma unroll 16
-    for (int64_t i = 0; i < n; ++i)
-        if (i != j) a += to_d(q[i * n + j]);
+    for (int c = 0; c < chunks; ++c) a += part[(int64_t)c * n + j];
     colsum[j] = a;
 }
 
-// Qoff_ij = (Q_ij + Q_ji)/2 off the diagonal, 0 on it; 32x32 tiles through shared memory.
+// Qoff_ij = (Q_ij + Q_ji)/2 off the diagonal, 0 on it; 32x32 tiles through
+// shared memory. The sum is formed in double and rounded once to float; for
+// float input the float sum scaled by 1/2 is the same value (a power-of-two
+// scaling commutes with the rounding), so that case stays in float.
+template <typename T> struct QoffAcc { using type = double; };
+template <> struct QoffAcc<float> { using type = float; };
 template <typename T>
 __global__ void k_dense_qoff(const T* __restrict__ q, int64_t n, float* __restrict__ out) {
-    __shared__ double tile[32][33];
+    using A = typename QoffAcc<T>::type;
+    __shared__ A tile[32][33];
     const int64_t bi = (int64_t)blockIdx.y * 32, bj = (int64_t)blockIdx.x * 32;
     // load the transposed tile Q[bj.., bi..]
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t gi = bj + r, gj = bi + threadIdx.x;
-        tile[r][threadIdx.x] = (gi < n && gj < n) ? to_d(q[gi * n + gj]) : 0.0;
+        tile[r][threadIdx.x] = (gi < n && gj < n) ? (A)to_d(q[gi * n + gj]) : (A)0;
     }
     __syncthreads();
     for (int r = threadIdx.y; r < 32; r += blockDim.y) {
         const int64_t gi = bi + r, gj = bj + threadIdx.x;
         if (gi < n && gj < n) {
-            const double v = 0.5 * (to_d(q[gi * n + gj]) + tile[threadIdx.x][r]);
+            const A v = (A)0.5 * ((A)to_d(q[gi * n + gj]) + tile[threadIdx.x][r]);
             out[gi * n + gj] = (gi == gj) ? 0.0f : (float)v;
         }
     }
@@ -354,7 +369,7 @@ constexpr int kPiBlock = 256;
 // matrix pass and one vector pass; products are FP32, every sum over blocks
 // FP64 in a fixed order. No reorthogonalisation: the loss of orthogonality
 // repeats converged Ritz values but does not move the extreme ones.
-constexpr int kLzSteps = 48;
+constexpr int kLzSteps = 32;
 struct LzScal {
     double* part;      // one partial per block
     unsigned* count;   // blocks finished in this launch (reset by the last one)
@@ -439,7 +454,25 @@ __global__ void __launch_bounds__(kPiBlock) k_lz_gemv(int64_t n, const float* __
         if ((n & 3) == 0) {
             const float4* r4 = reinterpret_cast<const float4*>(row);
             const float4* v4 = reinterpret_cast<const float4*>(wj);
-            for (int64_t c = lane; c < n / 4; c += 32) {
+            // eight 16-byte loads per lane in flight, summed in a fixed order
+            const int64_t n4 = n / 4;
+            int64_t c = lane;
+            for (; c + 7 * 32 < n4; c += 8 * 32) {
+                float4 x[8], y[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    x[u] = __ldcs(r4 + c + u * 32);
+                    y[u] = v4[c + u * 32];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    a = fmaf(x[u].x, y[u].x, a);
+                    a = fmaf(x[u].y, y[u].y, a);
+                    a = fmaf(x[u].z, y[u].z, a);
+                    a = fmaf(x[u].w, y[u].w, a);
+                }
+            }
+            for (; c < n4; c += 32) {
                 const float4 x = __ldcs(r4 + c), y = v4[c];
                 a = fmaf(x.x, y.x, a);
                 a = fmaf(x.y, y.y, a);
@@ -622,8 +655,9 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     VQ_CUDA(cudaMemcpyAsync(ctx->qx.p, Qh, qbytes, cudaMemcpyHostToDevice, st));
     T* q = ctx->qx.as<T>();
     DevBuf tmp;
-    // rowsum, colsum, absrow, diag, lin, d, absd, part, scalars
-    VQ_TRY(tmp.ensure(sizeof(double) * (size_t)(7 * n + kRedBlocks + 8) + 64));
+    // rowsum, colsum, absrow, diag, lin, d, absd, part, scalars, column-sum chunks
+    const int col_chunks = (int)div_up(n, kColRows);
+    VQ_TRY(tmp.ensure(sizeof(double) * (size_t)(7 * n + kRedBlocks + 16 + (int64_t)col_chunks * n) + 64));
     double* rowsum = tmp.as<double>();
     double* colsum = rowsum + n;
     double* absrow = colsum + n;
@@ -634,6 +668,7 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     double* part = absd + n;
     double* scal = part + kRedBlocks;          // [0] sum rowsum [1] sum d [2] sum absrow [3] sum absd [4] sum lin
     int* err = (int*)(scal + 8);
+    double* cpart = scal + 8 + 8;              // [col_chunks][n]
     VQ_CUDA(cudaMemsetAsync(err, 0, sizeof(int), st));
     if (ch) VQ_CUDA(cudaMemcpyAsync(lin, ch, sizeof(double) * n, cudaMemcpyHostToDevice, st));
     else VQ_CUDA(cudaMemsetAsync(lin, 0, sizeof(double) * n, st));
@@ -642,7 +677,8 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     k_dense_check<T><<<gb, 256, 0, st>>>(q, total, err);
     if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
     k_dense_rows<T><<<(unsigned)n, 256, 0, st>>>(q, n, rowsum, absrow, diag);
-    k_dense_cols<T><<<(unsigned)div_up(n, 64), 64, 0, st>>>(q, n, colsum);
+    k_dense_cols_part<T><<<dim3((unsigned)div_up(n, 128), (unsigned)col_chunks), 128, 0, st>>>(q, n, cpart);
+    k_dense_cols_sum<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, col_chunks, cpart, colsum);
     VQ_TRY(ctx->qoff32.ensure(sizeof(float) * (size_t)total));
     dim3 tb(32, 8), tg((unsigned)div_up(n, 32), (unsigned)div_up(n, 32));
     k_dense_qoff<T><<<tg, tb, 0, st>>>(q, n, ctx->qoff32.as<float>());
