@@ -51,6 +51,7 @@ NCU_TRAFFIC = {
     ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_batch", "wishart_b512"): 2_259_262_096,
+    ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
