@@ -50,7 +50,6 @@ NCU_TRAFFIC = {
     ("k_stream_step", "lattice_l100"): 4_104_791_000,
     ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
-    ("k_batch", "wishart_b512"): 2_259_262_096,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
@@ -107,11 +106,13 @@ def workload(name: str) -> dict:
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
                 "readout_every": 50, "desc": "periodic 3-D +-J lattice L=464 (n ~ 1e8), int8 CSR"}
-    if name == "wishart_b512":
+    if name in ("wishart_b512", "wishart_b512_fp8"):
         sizes = I.wishart_sizes(512, 100, 2000, seed=0)
+        fp8 = name.endswith("fp8")
         return {"name": name, "kind": "batch", "sizes": sizes, "n": int(sizes.sum()), "R": 64, "K": 1000,
-                "readout_every": 0, "prec": 1,
-                "desc": "512 Wishart planted instances, n_i uniform in [100, 2000], alpha 0.75, BF16 field"}
+                "readout_every": 0, "prec": 2 if fp8 else 1,
+                "desc": "512 Wishart planted instances, n_i uniform in [100, 2000], alpha 0.75, "
+                        + ("FP8 E4M3 field (S in two terms)" if fp8 else "BF16 field") + ", one persistent launch"}
     if name in ("sk_n8192_fp32", "sk_n8192_bf16", "sk_n8192_fp8", "sk_n8192_fp8_one_term"):
         Q, c = I.sk_qubo(8192, seed=0)
         form = name[len("sk_n8192_"):]
@@ -454,8 +455,12 @@ def roofline(B, w, runner, path, main_ms, main_launches):
     peaks, src = _peaks()
     n, R, K = runner.n_total, w["R"], w["K"]
     if runner.batch:
-        qbytes = sum(2 * int(m) * int(m) for m in w["sizes"])
-        hbm = K * (qbytes + 18 * n * R)              # BF16 Q streamed per step + state r/w + operand write
+        # Q streamed per step (BF16 2 B, E4M3 1 B per entry) + state r/w (16 B) + the next operand
+        # (2 B BF16, 1 B per E4M3 term) per variable-replica
+        fp8 = w.get("prec", 1) != 1
+        terms = 2 if w.get("prec", 1) == 2 and w.get("method", "bsb") != "pa" else 1
+        qbytes = sum((1 if fp8 else 2) * int(m) * int(m) for m in w["sizes"])
+        hbm = K * (qbytes + (16 + (terms if fp8 else 2)) * n * R)
         ach = hbm / (main_ms / 1e3) / 1e9
         return {"kernel": "k_batch", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
@@ -619,8 +624,8 @@ def time_to_target(B, stream, seeds=32, n=8192, R=1024, K=200, method=0):
 
 
 def time_to_target_batch(B, stream, seeds=4, K=1000, R=64):
-    """Time-to-target of the batched form (one persistent BF16 launch for the
-    512 Wishart instances) against the plain FP32 form (each instance solved
+    """Time-to-target of the batched forms (one persistent BF16 or FP8 launch
+    for the 512 Wishart instances) against the plain FP32 form (each instance solved
     in turn with the library's own path choice: the resident kernel up to
     n = 512, the split-k SGEMM step above). Per instance, the target is the median
     over `seeds` of the FP32 form's best energy after K steps; a form's
@@ -644,25 +649,26 @@ def time_to_target_batch(B, stream, seeds=4, K=1000, R=64):
         return np.asarray(E), e0.elapsed_time(e1)
 
     out = {"workload": f"Wishart batch of {len(ctxs)} instances, {R} replicas, final readout only", "seeds": seeds,
-           "note": "one batched BF16 launch against the FP32 form solving the instances one by one: the ratio "
-                   "combines batching and precision"}
+           "note": "one batched BF16 or FP8 launch against the FP32 form solving the instances one by one: "
+                   "each ratio combines batching and precision"}
     with torch.cuda.stream(stream):
         fp32 = [run(0, K, 300 + s) for s in range(seeds)]
         E32 = np.stack([e for e, _ in fp32])                     # [seeds][instances]
         E_star = np.median(E32, axis=0)
         t32 = float(np.median([t for _, t in fp32]))
         out["fp32"] = {"steps": K, "ms": t32, "success": float(np.mean(E32 <= E_star[None, :]))}
-        run(1, 4, 0)
-        best = None
-        for k2 in (100, 250, 500, K, 2 * K):
-            runs = [run(1, k2, 300 + s) for s in range(seeds)]
-            Eb = np.stack([e for e, _ in runs])
-            p = float(np.mean(Eb <= E_star[None, :]))
-            if p >= 0.5:
-                best = {"steps": k2, "ms": float(np.median([t for _, t in runs])), "success": p}
-                break
-        out["batched_bf16"] = best
-        out["speedup"] = (t32 / best["ms"]) if best else None
+        for name, prec in (("bf16", 1), ("fp8", 2)):
+            run(prec, 4, 0)
+            best = None
+            for k2 in (100, 250, 500, K, 2 * K):
+                runs = [run(prec, k2, 300 + s) for s in range(seeds)]
+                Eb = np.stack([e for e, _ in runs])
+                p = float(np.mean(Eb <= E_star[None, :]))
+                if p >= 0.5:
+                    best = {"steps": k2, "ms": float(np.median([t for _, t in runs])), "success": p}
+                    break
+            out[f"batched_{name}"] = best
+            out[f"speedup_{name}"] = (t32 / best["ms"]) if best else None
     for cx in ctxs:
         cx.destroy()
     return out

@@ -153,6 +153,9 @@ typedef struct {
                                and replica count); else 0 */
     int32_t stream_chunk;   /* streaming path: replicas per chunk of the step's thread order (every row of
                                one chunk before the next; 0: all replicas at once); else 0 */
+    int32_t batch_stages;   /* one-launch veloxq_solve_batch: pipeline stages of the autotuned form; else 0 */
+    int32_t batch_group;    /* one-launch veloxq_solve_batch: replicas per work item (an instance's
+                               replicas in groups of this size, each on its own CTA); else 0 */
 } veloxq_timing;
 
 /* Fill *s with the defaults listed above. */
@@ -288,16 +291,22 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
                        const veloxq_schedule* sched, uint64_t seed, uint8_t* const* x_best,
                        double* E_best);
 /* (veloxq_solve_batch, continued) When every context is dense, replicas is a
- * multiple of 16 in [16, 128], sched->prec is BF16 and sched->readout_every is
- * 0, the whole batch runs as ONE persistent tensor-core launch (instances
- * assigned to CTAs longest-first; pipeline depth picked by timing a short
- * probe the first time a batch shape is seen), followed by the exact
- * final-readout energies; otherwise each context is solved in turn. Every
- * integrator (sched->method) runs in both forms. */
+ * multiple of 16 in [16, 128], sched->prec is BF16, FP8 or FP8_ONE_TERM (not
+ * with adiabatic SB) and sched->readout_every is 0, the whole batch runs as ONE
+ * persistent tensor-core launch followed by the exact final-readout energies;
+ * otherwise each context is solved in turn. The launch's work items are
+ * replica groups of instances, assigned to CTAs longest-first; its form
+ * (pipeline depth, replicas per work item) is picked by timing a short probe
+ * of each candidate the first time a kind of batch is seen on a device, kept
+ * for the process and, when the environment variable VELOXQ_TUNE_CACHE names
+ * a file, read from and appended to it ("key=stages group" lines); the
+ * environment variable VELOXQ_BATCH_FORM="stages group" fixes the form instead
+ * (EINVAL if it does not fit). Every integrator (sched->method) runs in both
+ * forms. */
 
 /* Final state of context ctx after the last veloxq_solve_batch that ran the
- * persistent batched kernel (BF16 dense instances, readout only after the
- * last step): S, Y device [R][n] float32, R the replicas of that batch.
+ * persistent batched kernel (dense instances, readout only after the last
+ * step): S, Y device [R][n] float32, R the replicas of that batch.
  * Errors: EINVAL if no such state is held for R replicas. */
 int veloxq_batch_state_dev(veloxq_ctx* ctx, int32_t R, float* S, float* Y);
 

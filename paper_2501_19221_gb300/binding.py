@@ -55,7 +55,8 @@ class Info(ctypes.Structure):
 class Timing(ctypes.Structure):
     _fields_ = [("ms_total", ctypes.c_double), ("ms_main", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("path", ctypes.c_int32), ("main_launches", ctypes.c_int32),
-                ("stream_gather", ctypes.c_int32), ("stream_chunk", ctypes.c_int32)]
+                ("stream_gather", ctypes.c_int32), ("stream_chunk", ctypes.c_int32),
+                ("batch_stages", ctypes.c_int32), ("batch_group", ctypes.c_int32)]
 
 
 class VeloxqError(RuntimeError):

@@ -3,6 +3,8 @@
 // step loops or a single resident launch) and host <-> device marshalling.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <memory>
@@ -63,6 +65,7 @@ struct CtxExtra {
     // per-instance results, error word): owned here, so that batches headed
     // by different contexts never share it
     DevBuf bwork, bbest, berr;
+    int tune_stages = 0, tune_split = 0;   // form of the last batched launch headed by this context
     ~CtxExtra() {
         if (graph) cudaGraphExecDestroy(graph);
         for (cudaEvent_t e : {ev, t0, t1, t2, t3})
@@ -199,10 +202,87 @@ int tc_setup(veloxq_ctx* ctx, int prec, int32_t R, TcRun* t, int method = VELOXQ
     // the epilogue never writes them
     VQ_CUDA(cudaMemsetAsync(ctx->sop_a.p, 0, b, ctx->stream));
     VQ_CUDA(cudaMemsetAsync(ctx->sop_b.p, 0, b, ctx->stream));
+    ctx->sop_tag = 0;
     t->sop[0] = ctx->sop_a.p;
     t->sop[1] = ctx->sop_b.p;
     return tc_maps(ctx, prec, t->terms, R, t->sop[0], t->sop[1], &t->mq, &t->ms[0], &t->ms[1], &t->ms_lo[0],
                    &t->ms_lo[1]);
+}
+
+// ---- autotuned form of the batched launch ---------------------------------
+// Key of a batch kind: the device (name and SM count, so that a kept cache
+// carries over to another machine with the same GPU), the field precision and
+// integrator, the replicas, the instance count rounded up to a power of two,
+// and the mean and largest n rounded up to multiples of 128.
+std::string tune_key(const veloxq_ctx* c0, veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p) {
+    cudaDeviceProp prop{};
+    if (cudaGetDeviceProperties(&prop, c0->device) != cudaSuccess) {
+        cudaGetLastError();
+        prop.name[0] = 0;
+    }
+    int64_t sum = 0, mx = 0;
+    for (int32_t m = 0; m < count; ++m) {
+        sum += ctxs[m]->n;
+        mx = std::max<int64_t>(mx, ctxs[m]->n);
+    }
+    int64_t cnt = 1;
+    while (cnt < count) cnt <<= 1;
+    const int64_t mean = div_up(div_up(sum, std::max(1, count)), 128) * 128;
+    std::string k = "batch|" + std::string(prop.name) + "|" + std::to_string(prop.multiProcessorCount) + "|prec" +
+                    std::to_string((int)p.prec) + "|m" + std::to_string(p.method) + "|R" + std::to_string(R) + "|c" +
+                    std::to_string(cnt) + "|nmean" + std::to_string(mean) + "|nmax" +
+                    std::to_string(div_up(mx, 128) * 128);
+    for (char& ch : k)
+        if (ch == ' ' || ch == '=' || ch == '\n') ch = '_';
+    return k;
+}
+
+namespace {
+std::mutex g_tune_mu;
+std::map<std::string, std::pair<int, int>> g_tune;   // key -> (stages, replicas per work item)
+bool g_tune_loaded = false;
+
+// Lines "key=stages group" of the file VELOXQ_TUNE_CACHE names (read once).
+void tune_load_locked() {
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = std::getenv("VELOXQ_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = std::fopen(path, "r");
+    if (!f) return;
+    char line[1024];
+    while (std::fgets(line, sizeof(line), f)) {
+        char* eq = std::strchr(line, '=');
+        if (!eq) continue;
+        *eq = 0;
+        int st = 0, grp = 0;
+        if (std::sscanf(eq + 1, "%d %d", &st, &grp) == 2 && (st == 4 || st == 6) && grp >= 16 && grp % 16 == 0)
+            g_tune[line] = {st, grp};
+    }
+    std::fclose(f);
+}
+}  // namespace
+
+bool tune_lookup(const std::string& key, int* stages, int* group) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *stages = it->second.first;
+    *group = it->second.second;
+    return true;
+}
+
+void tune_store(const std::string& key, int stages, int group) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    tune_load_locked();
+    g_tune[key] = {stages, group};
+    const char* path = std::getenv("VELOXQ_TUNE_CACHE");
+    if (!path || !*path) return;
+    if (FILE* f = std::fopen(path, "a")) {
+        std::fprintf(f, "%s=%d %d\n", key.c_str(), stages, group);
+        std::fclose(f);
+    }
 }
 
 // Every call on a context runs on the device the context was created on,
@@ -579,6 +659,8 @@ int veloxq_solve(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_
         const bool streamed = path == VELOXQ_PATH_STREAM;
         ex->timing.stream_gather = streamed ? ctx->stream_unroll : 0;
         ex->timing.stream_chunk = streamed ? ctx->stream_cvec * vec_width(replicas) : 0;
+        ex->timing.batch_stages = 0;
+        ex->timing.batch_group = 0;
         ex->timed = true;
     }
     const int sh = ctx->energy_shift;
@@ -638,34 +720,54 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
     VQ_TRY(best_all.ensure(sizeof(int64_t) * 2 * (size_t)count));
     VQ_TRY(errw.ensure(sizeof(int) * 4));
     VQ_CUDA(cudaMemsetAsync(errw.p, 0, sizeof(int), st));
-    // autotune: pipeline depth and CTAs per SM, by timing a 2-step probe (cached per device and batch shape;
-    // the cache is shared by every thread of the process, under a lock)
-    static std::mutex tuned_mu;
-    static std::map<std::vector<int64_t>, int> tuned;
-    std::vector<int64_t> shape = {c0->device, count, replicas};
-    for (int32_t m = 0; m < count; ++m) shape.push_back(ctxs[m]->n);
-    int stages = 0;
-    {
-        std::lock_guard<std::mutex> lk(tuned_mu);
-        auto hit = tuned.find(shape);
-        if (hit != tuned.end()) stages = hit->second;
-    }
-    if (!stages) {
+    // autotune the form of the launch: pipeline depth (4 stages at two CTAs
+    // per SM, or 6 at one) and replicas per CTA (R, R/2, R/4: every work item a
+    // replica group of an instance), by timing a probe of at most 2 steps of
+    // every candidate; cached per device and batch kind (tune_key), shared by
+    // every thread under a lock, and kept in the file VELOXQ_TUNE_CACHE names
+    // (if set) for later processes
+    const std::string key = tune_key(c0, ctxs, count, replicas, p);
+    int stages = 0, split = 1;
+    if (const char* form = std::getenv("VELOXQ_BATCH_FORM")) {
+        // a form fixed by the caller: "stages group"
+        int st2 = 0, grp = 0;
+        if (std::sscanf(form, "%d %d", &st2, &grp) != 2 || (st2 != 4 && st2 != 6) || grp < 16 || grp % 16 != 0 ||
+            replicas % grp != 0 || !batch_stages_fit(p.prec, p.method, st2, grp))
+            return fail(VELOXQ_EINVAL, "VELOXQ_BATCH_FORM must be \"stages group\" with stages 4 or 6 and a group of "
+                                       "16k replicas dividing the replica count that fits shared memory");
+        stages = st2;
+        split = replicas / grp;
+    } else if (int grp = 0; tune_lookup(key, &stages, &grp) && grp <= replicas && replicas % grp == 0 &&
+                            batch_stages_fit(p.prec, p.method, stages, grp)) {
+        split = replicas / grp;
+    } else {
+        stages = 0;
         RunParams probe = p;
         probe.K = std::min(steps, 2);
         float best_ms = 1e30f;
-        for (int cand : {4, 6}) {
-            float ms = 0.f;
-            VQ_TRY(batch_run(ctxs, count, replicas, probe, seed, st, cand, work, best_all.as<int64_t>(),
-                             errw.as<int>(), &ms));
-            if (ms < best_ms) { best_ms = ms; stages = cand; }
+        for (int sp : {1, 2, 4}) {
+            if (replicas % sp != 0 || (replicas / sp) % 16 != 0) continue;
+            for (int cand : {4, 6}) {
+                if (!batch_stages_fit(p.prec, p.method, cand, replicas / sp)) continue;
+                float ms = 0.f;
+                VQ_TRY(batch_run(ctxs, count, replicas, probe, seed, st, cand, sp, work, best_all.as<int64_t>(),
+                                 errw.as<int>(), &ms));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    stages = cand;
+                    split = sp;
+                }
+            }
         }
-        std::lock_guard<std::mutex> lk(tuned_mu);
-        tuned[shape] = stages;
+        if (!stages) return fail(VELOXQ_EUNSUPPORTED, "no batched form fits this replica count");
+        tune_store(key, stages, replicas / split);
     }
+    ex->tune_stages = stages;
+    ex->tune_split = split;
     float ms_main = 0.f;
-    VQ_TRY(batch_run(ctxs, count, replicas, p, seed, st, stages, work, best_all.as<int64_t>(), errw.as<int>(),
-                     &ms_main));
+    int64_t nlaunch = 0;
+    VQ_TRY(batch_run(ctxs, count, replicas, p, seed, st, stages, split, work, best_all.as<int64_t>(), errw.as<int>(),
+                     &ms_main, &nlaunch));
     int herr = 0;
     std::vector<int64_t> h((size_t)(2 * count));
     VQ_CUDA(cudaMemcpyAsync(&herr, errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -679,11 +781,13 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
         for (int32_t m = 0; m < count; ++m) E_best[m] = std::ldexp((double)h[2 * m + 1], -ctxs[m]->energy_shift);
     ex->timing.ms_total = ms_main;
     ex->timing.ms_main = ms_main;
-    ex->timing.launches = 1 + 5 * (int64_t)count;
+    ex->timing.launches = nlaunch;
     ex->timing.path = VELOXQ_PATH_DENSE;
     ex->timing.main_launches = 1;
     ex->timing.stream_gather = 0;
     ex->timing.stream_chunk = 0;
+    ex->timing.batch_stages = stages;
+    ex->timing.batch_group = replicas / split;
     ex->timed = true;
     return VELOXQ_OK;
 }
@@ -895,6 +999,8 @@ int veloxq_grad(veloxq_ctx* ctx, int32_t replicas, int32_t steps, const veloxq_s
     ex->timing.main_launches = tm.reverse_launches;
     ex->timing.stream_gather = 0;
     ex->timing.stream_chunk = 0;
+    ex->timing.batch_stages = 0;
+    ex->timing.batch_group = 0;
     ex->timed = true;
     if (d_kappa) {
         // c0 = kappa / rho(J) = 2 kappa / rho(Qoff) unless c0 was given

@@ -107,6 +107,8 @@ struct veloxq_ctx {
     vq::DevBuf qscale8;           // float [n] per-row FP8 scales
     vq::DevBuf qtile;             // pre-tiled swizzled BF16 Qoff for the batched kernel
     size_t qtile_bytes = 0;
+    int qtile_fp8 = 0;            // 1: qtile holds the E4M3 form (row scales in qscale8)
+    int64_t sop_tag = 0;          // layout the operand buffers sop_a/sop_b last held (0: the single-solve one)
     int32_t batch_R = 0;          // replicas of the state left by the last batched run (0: none)
     // exact readout energies on the tensor cores (vq_energy_tc.cu)
     int eplanes = 0;              // digit planes of round(Q 2^S): 0 not built yet, -1 not used
@@ -188,8 +190,12 @@ int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts
 
 // persistent batched kernel (vq_batch.cu)
 bool batch_supported(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p);
+bool batch_stages_fit(int prec, int method, int stages, int32_t R);   // the form fits shared memory
+// stages: pipeline depth (4 or 6); split: replica groups per instance, each a
+// work item of R / split replicas (a multiple of 16)
 int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p, uint64_t seed, cudaStream_t st,
-              int stages, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main);
+              int stages, int split, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main,
+              int64_t* launches = nullptr);
 
 // adjoint of the step (vq_adjoint.cu); the timing covers the whole gradient
 // and, separately, the reverse-step kernels (k_adj_a, k_adj_b, k_adj_reduce)

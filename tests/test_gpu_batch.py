@@ -11,6 +11,26 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 U = 2.0 ** -9       # BF16 operand rounding
+# relative rounding of (Qoff, S) per field precision: BF16; FP8 with S in two
+# E4M3 terms; FP8 with one term (E4M3 keeps 4 significant bits)
+UQS = {1: (2.0 ** -9, 2.0 ** -9), 2: (2.0 ** -4, 2.0 ** -8 + 2.0 ** -23), 3: (2.0 ** -4, 2.0 ** -4)}
+
+
+def _field_bound(prec, Q, S, rows=None):
+    """Elementwise bound on the field error of one batched step ([R][rows]):
+    (uQ + uS + uQ uS)(|Qoff||S|) plus, for E4M3, the absolute error of its
+    subnormal range (2^-10 of the row scale for Qoff, 2^-10/448 for S)."""
+    rows = np.arange(Q.shape[0]) if rows is None else np.asarray(rows)
+    uq, us = UQS[prec]
+    Qd = np.asarray(Q, dtype=np.float64)
+    Qr = 0.5 * (Qd[rows, :] + Qd[:, rows].T)
+    Qr[np.arange(len(rows)), rows] = 0.0
+    b = (uq + us + uq * us) * (np.abs(S).astype(np.float64) @ np.abs(Qr).T) + 1e-6
+    if prec != 1:
+        aq = np.abs(Qr).max(axis=1) / 448.0 * 2.0 ** -10
+        b = b + (1 + us) * aq[None, :] * np.abs(S).sum(axis=1)[:, None]
+        b = b + (1 + uq) * 2.0 ** -10 / 448.0 * np.abs(Qr).sum(axis=1)[None, :]
+    return b
 
 
 @pytest.fixture(scope="module")
@@ -29,17 +49,18 @@ def _sk(n, seed):
     return Q, c
 
 
-@pytest.mark.parametrize("R", [16, 64, 128])
-def test_batch_one_step_parity(B, R):
+@pytest.mark.parametrize("prec,R", [(1, 16), (1, 64), (1, 128), (2, 16), (2, 64), (2, 128), (3, 64)])
+def test_batch_one_step_parity(B, prec, R):
     """K = 1 from the Philox start: every instance's state equals the oracle's
-    FP32-input FP64 step up to the BF16 field bound propagated through the
-    update."""
+    FP32-input FP64 step up to the field bound of the precision (BF16; FP8
+    with S in two E4M3 terms; FP8 with one) propagated through the update."""
     sizes = [20, 100, 129, 300, 511, 640, 128, 64]
     insts = [_sk(n, 10 + i) for i, n in enumerate(sizes)]
     ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
     dt, c0 = np.float32(0.5), np.float32(0.3)
-    sched = B.make_schedule(prec=1, readout_every=0, c0=float(c0), dt=float(dt))
+    sched = B.make_schedule(prec=prec, readout_every=0, c0=float(c0), dt=float(dt))
     out = B.veloxq_solve_batch(ctxs, R, 1, sched, seed=4)
+    assert B.veloxq_last_timing(ctxs[0]).main_launches == 1
     for (Q, c), ctx in zip(insts, ctxs):
         n = Q.shape[0]
         S = torch.empty(R, n, device="cuda")
@@ -49,7 +70,7 @@ def test_batch_one_step_parity(B, R):
         p = O.problem_from_dense(Q.astype(np.float64), c)
         S0, Y0 = O.init_state(n, R, 4, 0.1)
         ref = O.bsb_run(p, R, 1, float(dt), 1.0, float(c0), [0.0, 1.0], 0, S0, Y0)
-        dF = (2 * U + U * U) * O.abs_field(p, S0.astype(np.float64)) + 1e-6
+        dF = _field_bound(prec, Q, S0)
         dy = float(dt) * float(c0) * 0.5 * dF + 2e-6
         ds = float(dt) * dy + 2e-6
         assert np.all(np.abs(Y.cpu().numpy() - ref["Y"]) <= dy)
@@ -57,11 +78,12 @@ def test_batch_one_step_parity(B, R):
     assert len(out["E"]) == len(sizes)
 
 
-def test_batch_outputs_exact_and_consistent(B):
+@pytest.mark.parametrize("prec,method", [(1, 0), (2, 0), (3, 0), (2, 2)])
+def test_batch_outputs_exact_and_consistent(B, prec, method):
     sizes = [37, 200, 150, 480, 99]
     insts = [_sk(n, 30 + i) for i, n in enumerate(sizes)]
     ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
-    out = B.veloxq_solve_batch(ctxs, 64, 200, B.make_schedule(prec=1, readout_every=0), seed=2)
+    out = B.veloxq_solve_batch(ctxs, 64, 200, B.make_schedule(prec=prec, readout_every=0, method=method), seed=2)
     t = B.veloxq_last_timing(ctxs[0])
     assert t.main_launches == 1
     for (Q, c), x, E in zip(insts, out["x"], out["E"]):
@@ -116,7 +138,8 @@ def _sym_normal(n, seed):
     return Q
 
 
-def test_batch_config4_shapes_one_step(B):
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_config4_shapes_one_step(B, prec):
     """The batched-instance workload's own shapes in ONE launch: 512
     instances with n drawn uniformly from [100, 2000] (the Wishart batch's
     sizes), 64 replicas, one step from the Philox start. For every instance,
@@ -140,9 +163,9 @@ def test_batch_config4_shapes_one_step(B):
         F = O.field_dense_rows(Q, S0, rows)
         b = O.bias_dense_rows(Q, c, rows)
         S1, Y1 = O.update("bsb", F, b, 0.0, float(dt), 1.0, float(c0), S0[:, rows], Y0[:, rows])
-        dF = (2 * U + U * U) * O.abs_field_dense_rows(Q, S0, rows) + 1e-6
+        dF = _field_bound(prec, Q, S0, rows)
         refs.append((rows, S1, Y1, dF))
-    sched = B.make_schedule(prec=1, readout_every=0, c0=float(c0), dt=float(dt))
+    sched = B.make_schedule(prec=prec, readout_every=0, c0=float(c0), dt=float(dt))
     B.veloxq_solve_batch(ctxs, R, 1, sched, seed=4, want_x=False)
     assert B.veloxq_last_timing(ctxs[0]).main_launches == 1
     for ctx, (rows, S1, Y1, dF) in zip(ctxs, refs):
@@ -196,3 +219,55 @@ def test_two_batches_on_two_streams(B):
     for cs in ctx_sets:
         for cx in cs:
             cx.destroy()
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_batch_forms_agree(B, prec, monkeypatch):
+    """Every form of the launch the autotuner chooses from (4 or 6 pipeline
+    stages; an instance's 64 replicas in one work item or in groups of 32 or
+    16 on separate CTAs) gives the same final states and energies: the
+    replicas are independent and each keeps its own arithmetic."""
+    sizes = [150, 77, 300, 129, 512]
+    insts = [_sk(n, 90 + i) for i, n in enumerate(sizes)]
+    ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    sched = B.make_schedule(prec=prec, readout_every=0)
+    results = {}
+    for form in ("6 64", "4 64", "6 32", "4 16"):
+        monkeypatch.setenv("VELOXQ_BATCH_FORM", form)
+        out = B.veloxq_solve_batch(ctxs, 64, 60, sched, seed=8)
+        t = B.veloxq_last_timing(ctxs[0])
+        assert (t.batch_stages, t.batch_group) == tuple(int(v) for v in form.split())
+        states = []
+        for ctx in ctxs:
+            n = ctx.info.n
+            S = torch.empty(64, n, device="cuda")
+            Y = torch.empty(64, n, device="cuda")
+            B.veloxq_batch_state_dev(ctx, 64, S, Y)
+            torch.cuda.synchronize()
+            states.append((S.cpu().numpy(), Y.cpu().numpy()))
+        results[form] = (out["E"], states)
+    E0, st0 = results["6 64"]
+    for form, (E, st) in results.items():
+        assert np.array_equal(E, E0), form
+        for (S, Y), (S0, Y0) in zip(st, st0):
+            assert np.array_equal(S, S0) and np.array_equal(Y, Y0), form
+    monkeypatch.setenv("VELOXQ_BATCH_FORM", "5 64")
+    with pytest.raises(B.VeloxqError, match="VELOXQ_BATCH_FORM"):
+        B.veloxq_solve_batch(ctxs, 64, 2, sched, seed=8)
+
+
+def test_batch_tune_cache_file(B, tmp_path, monkeypatch):
+    """The autotuner keeps what it picked in the file VELOXQ_TUNE_CACHE names,
+    one "key=stages group" line per kind of batch, and the launch runs in that
+    form."""
+    path = tmp_path / "tune.txt"
+    monkeypatch.setenv("VELOXQ_TUNE_CACHE", str(path))
+    monkeypatch.delenv("VELOXQ_BATCH_FORM", raising=False)
+    sizes = [211, 97, 333]                      # a kind of batch no other test uses
+    ctxs = [B.veloxq_create_dense(*_sk(n, 120 + i)) for i, n in enumerate(sizes)]
+    B.veloxq_solve_batch(ctxs, 48, 20, B.make_schedule(prec=1, readout_every=0), seed=1)
+    t = B.veloxq_last_timing(ctxs[0])
+    lines = [ln for ln in path.read_text().splitlines() if ln.startswith("batch|")]
+    assert len(lines) == 1 and "|R48|" in lines[0]
+    st, grp = (int(v) for v in lines[0].split("=")[1].split())
+    assert (st, grp) == (t.batch_stages, t.batch_group) and st in (4, 6) and 48 % grp == 0
