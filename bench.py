@@ -74,7 +74,9 @@ def _peaks():
 
 
 # ----------------------------------------------------------------------------- workloads
-def workload(name: str) -> dict:
+def workload(name: str, for_oracle: bool = False) -> dict:
+    """The workload `name`. for_oracle: only what the oracle's timed sample
+    needs (the full instance is not drawn when the sample is a smaller one)."""
     if name == "chimera_c16":
         sp = I.chimera_ising(16, 16, 4, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 1024, "K": 5000,
@@ -89,13 +91,20 @@ def workload(name: str) -> dict:
                 "readout_every": 0, "dt": 0.5, "knots": [0.0, 0.5, 1.0],
                 "desc": "gradient of the mean relaxed energy w.r.t. dt, kappa and 3 schedule knots, periodic "
                         "3-D +-J lattice L=100, int8 CSR, 400 unrolled steps, checkpoint every 20"}
-    if name == "hubo_chain_1e7":
-        inst = I.hubo_chain_3body(10 ** 7, seed=0)
-        n3 = inst.triples[0].shape[0]
-        return {"name": name, "kind": "hubo", "hubo": inst, "local": True, "n": inst.n + n3, "R": 8, "K": 200,
-                "readout_every": 50,
-                "desc": "3-body +-Gaussian spin-glass chain (Sec. HUBO eq. nn), N = 1e7, reduced to second order "
-                        "by eq. reduction (one auxiliary spin per cubic term, numbered next to it: n = 2e7 - 2), float CSR"}
+    if name in ("hubo_chain_1e7", "hubo_chain_5e7"):
+        N = 10 ** 7 if name.endswith("1e7") else 5 * 10 ** 7
+        inst = None if (for_oracle and N > 10 ** 7) else I.hubo_chain_3body(N, seed=0)
+        n_red = N + max(N - 2, 0)             # one auxiliary spin per cubic term
+        w = {"name": name, "kind": "hubo", "hubo": inst, "local": True, "n": n_red, "R": 8, "K": 200,
+             "readout_every": 50,
+             "desc": f"3-body +-Gaussian spin-glass chain (Sec. HUBO eq. nn), N = {N:.0e}, reduced to second order "
+                     f"by eq. reduction (one auxiliary spin per cubic term, numbered next to it: n = {n_red}), "
+                     "float CSR"}
+        if N > 10 ** 7:
+            # the oracle's sample: a chain of 1e6 spins drawn by the same recipe (the same local structure;
+            # the whole instance does not fit one host process per core)
+            w["oracle_chain"] = 10 ** 6
+        return w
     if name == "xorsat_3r3x_1e5":
         x = I.xorsat_3r3x(10 ** 5, seed=0)
         return {"name": name, "kind": "hubo", "hubo": x.hubo, "E0_hubo": x.E0, "n": 2 * 10 ** 5, "R": 256,
@@ -178,7 +187,7 @@ def input_arrays(w) -> list:
 def oracle_problem(w):
     import oracle as O
     if w["kind"] == "hubo":
-        inst = w["hubo"]
+        inst = I.hubo_chain_3body(w["oracle_chain"], seed=0) if "oracle_chain" in w else w["hubo"]
         N, (qi, qj, qv), lin, _ = O.hubo3_reduce(inst.n, inst.h, inst.pairs, inst.triples)
         p, _ = O.ising_pairs_to_qubo(N, qi, qj, qv, lin)
         return p
@@ -225,18 +234,18 @@ def oracle_timed_run(w, p, c0, R_s: int, K_s: int, seed: int = 0, barrier=None) 
 
 
 def oracle_sample_rate(w, R_s: int, K_s: int, seed: int = 0) -> tuple:
-    """(spin-updates/s, seconds) of one single-thread oracle sample."""
+    """(spin-updates/s, seconds, variables) of one single-thread oracle sample."""
     p, c0 = oracle_setup(w)
     dt = oracle_timed_run(w, p, c0, R_s, K_s, seed)
-    return p.n * R_s * K_s / dt, dt
+    return p.n * R_s * K_s / dt, dt, p.n
 
 
 def oracle_plan(w, target_s: float, max_R: int) -> tuple:
     """(R_s, K_s) for about target_s seconds of single-thread oracle work on
     the workload (at most max_R replicas and the workload's steps), from a
     one-replica calibration run of two steps."""
-    rate0, _ = oracle_sample_rate(w, 1, min(w["K"], 2))
-    budget = max(1.0, target_s * rate0 / w["n"])                # replica-steps in the target
+    rate0, _, n_s = oracle_sample_rate(w, 1, min(w["K"], 2))
+    budget = max(1.0, target_s * rate0 / n_s)                   # replica-steps in the target
     R_s = int(min(w["R"], max_R, budget))
     K_s = int(min(w["K"], max(1, budget / max(1, R_s))))
     return max(1, R_s), K_s
@@ -263,13 +272,14 @@ def oracle_procs(w, R_s: int) -> int:
                 avail = min(avail, int(v)) if avail else int(v)
     except OSError:
         pass
+    n_eff = 2 * int(w["oracle_chain"]) if "oracle_chain" in w else int(w["n"])
     if "Q" in w:
-        nnz = int(w["n"]) ** 2
-    elif "sp" in w:
-        nnz = int(np.asarray(w["sp"].rowptr)[-1]) + int(w["n"])
+        nnz = n_eff ** 2
+    elif "sp" in w and "oracle_chain" not in w:
+        nnz = int(np.asarray(w["sp"].rowptr)[-1]) + n_eff
     else:
-        nnz = 8 * int(w["n"])
-    per_proc = 1.5 * 24 * nnz + 32 * int(w["n"]) * R_s + (512 << 20)
+        nnz = 8 * n_eff
+    per_proc = 1.5 * 24 * nnz + 32 * n_eff * R_s + (512 << 20)
     if not avail:
         return cores
     return int(max(1, min(cores, 0.5 * avail // per_proc)))
@@ -279,7 +289,7 @@ def _crew_member(name, method, c0, seed, barrier, jobs, results):
     """A worker process of OracleCrew: builds the problem once, then runs the
     rounds it is given, each released by the shared barrier."""
     try:
-        w = dict(workload(name), method=method)
+        w = dict(workload(name, for_oracle=True), method=method)
         p = oracle_problem(w)
         while True:
             job = jobs.get()
@@ -302,7 +312,8 @@ class OracleCrew:
     def __init__(self, w, procs: int):
         import multiprocessing as mp
         self.w, self.procs = w, procs
-        _, self.c0 = oracle_setup(w)                      # rho once, in the parent
+        p, self.c0 = oracle_setup(w)                      # rho once, in the parent
+        self.n = p.n                                      # variables of the sampled instance
         ctx = mp.get_context("spawn")
         self.barrier = ctx.Barrier(procs, timeout=600)
         self.results = ctx.Queue()
@@ -331,7 +342,7 @@ class OracleCrew:
         if bad:
             raise RuntimeError(f"oracle sample failed: {bad[0]}")
         wall = max(r for _, r in got)
-        return self.w["n"] * R_s * K_s * self.procs / wall, wall
+        return self.n * R_s * K_s * self.procs / wall, wall
 
     def close(self):
         for q in self.jobs:
@@ -343,7 +354,7 @@ class OracleCrew:
 def oracle_parallel_rate(w, R_s: int, K_s: int, procs: int) -> tuple:
     """One replica-parallel round (see OracleCrew): (rate, seconds, processes)."""
     if procs <= 1:
-        rate, dt = oracle_sample_rate(w, R_s, K_s)
+        rate, dt, _ = oracle_sample_rate(w, R_s, K_s)
         return rate, dt, 1
     crew = OracleCrew(w, procs)
     try:
@@ -837,13 +848,15 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and world == 1 and not args.no_cpu_baseline and not run.batch:
         # calibrate on a short run, then time about 12 s of oracle work
         R_s, K_s2 = oracle_plan(w, 12.0, 4 if run.grad else 64)
-        rate1, dt1 = oracle_sample_rate(w, R_s, K_s2)
+        rate1, dt1, n_s = oracle_sample_rate(w, R_s, K_s2)
         # each process holds its own copy of the instance: fewer of them when memory is short
         procs = oracle_procs(w, R_s)
         rate, dt, used = oracle_parallel_rate(w, R_s, K_s2, procs)
         what = "reverse-mode gradient over" if run.grad else "solve of"
+        inst = ("the same instance" if "oracle_chain" not in w else
+                f"a chain of {w['oracle_chain']:.0e} spins by the same recipe (n = {n_s} after reduction)")
         cpu = {"value": rate, "unit": "spin-updates/s", "cores": used, "kind": "oracle",
-               "sample": f"{what} {R_s} replicas x first {K_s2} of {K} steps of the same instance, FP64, "
+               "sample": f"{what} {R_s} replicas x first {K_s2} of {K} steps of {inst}, FP64, "
                          f"{used} independent processes at once (replica-parallel, {dt:.1f} s wall)",
                "single_thread": {"value": rate1, "sample_s": dt1}}
 
@@ -920,7 +933,7 @@ def run_reference(args, rank, world):
         crew.close()
     used = procs
     total = sum(times)
-    value = w["n"] * R_s * K_s * used * args.steps / total
+    value = crew.n * R_s * K_s * used * args.steps / total
     what = "reverse-mode gradient, " if w["kind"] == "grad" else ""
     sample = (f"{what}{R_s} replicas x first {K_s} of {w['K']} steps per step in each of {used} independent "
               f"processes at once, FP64 oracle")

@@ -293,8 +293,10 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
 /* (veloxq_solve_batch, continued) When every context is dense, replicas is a
  * multiple of 16 in [16, 128], sched->prec is BF16, FP8 or FP8_ONE_TERM (not
  * with adiabatic SB) and sched->readout_every is 0, the whole batch runs as ONE
- * persistent tensor-core launch followed by the exact final-readout energies;
- * otherwise each context is solved in turn. The launch's work items are
+ * persistent tensor-core launch followed by the exact final-readout energies
+ * of every instance in two more launches, captured as one CUDA graph that is
+ * replayed by later solves of the same contexts, replicas, steps and schedule
+ * (any seed); otherwise each context is solved in turn. The launch's work items are
  * replica groups of instances, assigned to CTAs longest-first; its form
  * (pipeline depth, replicas per work item) is picked by timing a short probe
  * of each candidate the first time a kind of batch is seen on a device, kept

@@ -66,6 +66,7 @@ struct CtxExtra {
     // by different contexts never share it
     DevBuf bwork, bbest, berr;
     int tune_stages = 0, tune_split = 0;   // form of the last batched launch headed by this context
+    BatchGraph bgraph;                     // its captured device part
     ~CtxExtra() {
         if (graph) cudaGraphExecDestroy(graph);
         for (cudaEvent_t e : {ev, t0, t1, t2, t3})
@@ -767,7 +768,7 @@ int veloxq_solve_batch(veloxq_ctx* const* ctxs, int32_t count, int32_t replicas,
     float ms_main = 0.f;
     int64_t nlaunch = 0;
     VQ_TRY(batch_run(ctxs, count, replicas, p, seed, st, stages, split, work, best_all.as<int64_t>(), errw.as<int>(),
-                     &ms_main, &nlaunch));
+                     &ms_main, &nlaunch, &ex->bgraph));
     int herr = 0;
     std::vector<int64_t> h((size_t)(2 * count));
     VQ_CUDA(cudaMemcpyAsync(&herr, errw.p, sizeof(int), cudaMemcpyDeviceToHost, st));

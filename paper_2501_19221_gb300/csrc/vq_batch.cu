@@ -27,6 +27,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstring>
 #include <numeric>
 #include <queue>
 #include <vector>
@@ -174,7 +175,8 @@ struct BatchArgs {
     int32_t R, K;               // replicas of every instance, steps
     int32_t G, RG;              // replica groups per instance and replicas per group (R = G RG)
     float dt, a0, sigma0;
-    uint64_t seed;
+    const uint64_t* seed;       // device: the Philox key of this solve (uploaded per solve, so that a
+                                // captured graph of the launch serves every seed)
     const float* a_table;
     int* err;
     float alpha;                // PA momentum
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
             for (int64_t e = et; e < (int64_t)R * n; e += 128) {
                 const int r = (int)(e / n), i = (int)(e - (int64_t)r * n);
                 float s0, y0;
-                vqd::init_pair(i, r0 + r, a.seed, a.sigma0, &s0, &y0);
+                vqd::init_pair(i, r0 + r, *a.seed, a.sigma0, &s0, &y0);
                 S[e] = s0;
                 Y[e] = y0;
                 put_op<PREC, TERMS>(in.sop0 + (size_t)(i / TK) * B_STRIDE + swz<EB>(r0 + r, i % TK), lo_off,
@@ -604,8 +606,9 @@ bool batch_supported(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const Ru
 // the argmin of every instance. stages: 4 (two CTAs per SM) or 6 (one).
 int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p, uint64_t seed, cudaStream_t st,
               int stages, int split, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main,
-              int64_t* launches) {
+              int64_t* launches, BatchGraph* graph) {
     int64_t nl = 0;
+    std::vector<std::pair<void*, size_t>> zero;   // operand buffers whose padding is zeroed
     const int terms = batch_terms(p.prec, p.method);
     if (split < 1 || R % split != 0 || (R / split) % 16 != 0)
         return fail(VELOXQ_EINVAL, "replica groups must hold a multiple of 16 replicas");
@@ -649,11 +652,12 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
         VQ_TRY(c->sop_a.ensure(sopb));
         VQ_TRY(c->sop_b.ensure(sopb));
         // the K padding of the operand tiles is never written: zero it when the
-        // buffers last held another layout (or were just allocated)
+        // buffers last held another layout (or were just allocated); a captured
+        // launch zeroes it on every replay
         const int64_t tag = ((int64_t)R << 16) | ((int64_t)p.prec << 8) | ((int64_t)terms << 4) | 1;
-        if (c->sop_tag != tag || c->sop_a.p != pa || c->sop_b.p != pb) {
-            VQ_CUDA(cudaMemsetAsync(c->sop_a.p, 0, sopb, st));
-            VQ_CUDA(cudaMemsetAsync(c->sop_b.p, 0, sopb, st));
+        if (graph || c->sop_tag != tag || c->sop_a.p != pa || c->sop_b.p != pb) {
+            zero.push_back({c->sop_a.p, sopb});
+            zero.push_back({c->sop_b.p, sopb});
             c->sop_tag = tag;
         }
         BatchInst b{};
@@ -723,6 +727,7 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
     }
     VQ_TRY(work.ensure(ib + ob + bb + rb + wtot + 64));
     uint8_t* w = work.as<uint8_t>();
+    uint64_t* seed_dev = reinterpret_cast<uint64_t*>(w + ib + ob + bb + rb + wtot);
     VQ_CUDA(cudaMemcpyAsync(w, host.data(), sizeof(BatchInst) * (size_t)count, cudaMemcpyHostToDevice, st));
     VQ_CUDA(cudaMemcpyAsync(w + ib, order.data(), sizeof(int32_t) * order.size(), cudaMemcpyHostToDevice, st));
     VQ_CUDA(cudaMemcpyAsync(w + ib + ob, begin.data(), sizeof(int32_t) * begin.size(), cudaMemcpyHostToDevice, st));
@@ -739,6 +744,7 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
             at += wb[t];
         }
     }
+    VQ_CUDA(cudaMemcpyAsync(seed_dev, &seed, sizeof(uint64_t), cudaMemcpyHostToDevice, st));
     BatchArgs a;
     a.inst = reinterpret_cast<const BatchInst*>(w);
     a.order = reinterpret_cast<const int32_t*>(w + ib);
@@ -750,42 +756,99 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
     a.dt = p.dt;
     a.a0 = p.a0;
     a.sigma0 = p.sigma0;
-    a.seed = seed;
+    a.seed = seed_dev;
     a.a_table = ctxs[0]->a_table.as<float>();
     a.err = d_err;
     a.alpha = p.alpha;
-    cudaEvent_t e0, e1;
-    VQ_CUDA(cudaEventCreate(&e0));
-    VQ_CUDA(cudaEventCreate(&e1));
-    VQ_CUDA(cudaEventRecord(e0, st));
-    fn<<<ctas, 192, smem, st>>>(a);
-    VQ_LAUNCH_CHECK("batch kernel");
-    VQ_CUDA(cudaEventRecord(e1, st));
-    // exact final-readout energies and the best replica of every instance:
-    // one energy launch per element type of Q in the batch, one finish launch
     const ReadInst* rdev = reinterpret_cast<const ReadInst*>(wr);
-    for (int t = 0; t < 4; ++t) {
-        const unsigned blocks = (unsigned)(rwork[t].size() / 2);
-        if (!blocks) continue;
-        const int32_t* wd = reinterpret_cast<const int32_t*>(wl[t]);
-        ++nl;
-        switch (t) {
-            case VELOXQ_I8: k_batch_energy<int8_t><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
-            case VELOXQ_I32: k_batch_energy<int32_t><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
-            case VELOXQ_F32: k_batch_energy<float><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
-            default: k_batch_energy<double><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
-        }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (graph) {
+        if (!graph->e0) VQ_CUDA(cudaEventCreate(&graph->e0));
+        if (!graph->e1) VQ_CUDA(cudaEventCreate(&graph->e1));
+        e0 = graph->e0;
+        e1 = graph->e1;
+    } else {
+        VQ_CUDA(cudaEventCreate(&e0));
+        VQ_CUDA(cudaEventCreate(&e1));
     }
-    k_batch_finish<<<(unsigned)count, 256, 0, st>>>(rdev, R, d_best_all);
-    VQ_LAUNCH_CHECK("batch readout");
+    // the device part of the solve: operand padding, the persistent kernel
+    // between two timing events, and the final readout (one energy launch per
+    // element type of Q in the batch, one finish launch)
+    auto enqueue = [&]() -> int {
+        const unsigned flags = graph ? cudaEventRecordExternal : cudaEventRecordDefault;
+        for (const auto& z : zero) VQ_CUDA(cudaMemsetAsync(z.first, 0, z.second, st));
+        VQ_CUDA(cudaEventRecordWithFlags(e0, st, flags));
+        fn<<<ctas, 192, smem, st>>>(a);
+        VQ_LAUNCH_CHECK("batch kernel");
+        VQ_CUDA(cudaEventRecordWithFlags(e1, st, flags));
+        for (int t = 0; t < 4; ++t) {
+            const unsigned blocks = (unsigned)(rwork[t].size() / 2);
+            if (!blocks) continue;
+            const int32_t* wd = reinterpret_cast<const int32_t*>(wl[t]);
+            switch (t) {
+                case VELOXQ_I8: k_batch_energy<int8_t><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
+                case VELOXQ_I32: k_batch_energy<int32_t><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
+                case VELOXQ_F32: k_batch_energy<float><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
+                default: k_batch_energy<double><<<blocks, 256, 0, st>>>(rdev, wd, R); break;
+            }
+        }
+        k_batch_finish<<<(unsigned)count, 256, 0, st>>>(rdev, R, d_best_all);
+        VQ_LAUNCH_CHECK("batch readout");
+        return VELOXQ_OK;
+    };
+    for (int t = 0; t < 4; ++t) nl += rwork[t].empty() ? 0 : 1;
     nl += 2;   // the batched kernel and the finish
     if (launches) *launches = nl;
+    if (!graph) {
+        VQ_TRY(enqueue());
+    } else {
+        // one graph per kind of launch: everything the captured nodes bake in
+        std::vector<uint64_t> key = {(uint64_t)(uintptr_t)fn, (uint64_t)ctas, (uint64_t)smem, (uint64_t)(uintptr_t)w,
+                                     (uint64_t)(uintptr_t)d_best_all, (uint64_t)(uintptr_t)d_err, (uint64_t)R,
+                                     (uint64_t)split, (uint64_t)p.K, (uint64_t)count,
+                                     (uint64_t)(uintptr_t)a.a_table};
+        for (float f : {p.dt, p.a0, p.sigma0, p.alpha}) {
+            uint32_t u;
+            std::memcpy(&u, &f, 4);
+            key.push_back(u);
+        }
+        for (int t = 0; t < 4; ++t) key.push_back(rwork[t].size());
+        for (const auto& z : zero) {
+            key.push_back((uint64_t)(uintptr_t)z.first);
+            key.push_back(z.second);
+        }
+        if (!graph->exec || graph->key != key) {
+            if (graph->exec) {
+                cudaGraphExecDestroy(graph->exec);
+                graph->exec = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            VQ_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            const int rc = enqueue();
+            const cudaError_t ce = cudaStreamEndCapture(st, &g);
+            if (rc != VELOXQ_OK) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (ce != cudaSuccess) return cuda_fail(ce, "batch graph capture");
+            const cudaError_t ie = cudaGraphInstantiate(&graph->exec, g, 0);
+            cudaGraphDestroy(g);
+            if (ie != cudaSuccess) {
+                graph->exec = nullptr;
+                return cuda_fail(ie, "batch graph instantiate");
+            }
+            graph->key = key;
+        }
+        VQ_CUDA(cudaGraphLaunch(graph->exec, st));
+    }
     VQ_CUDA(cudaStreamSynchronize(st));
     float ms = 0.f;
     VQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
     if (ms_main) *ms_main = ms;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    if (!graph) {
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
     return VELOXQ_OK;
 }
 

@@ -29,7 +29,7 @@ static int reduce3(int64_t n, const double* h, int64_t n2, const int64_t* pi, co
     const int64_t N = n + n3;
     if (N > INT32_MAX) return fail(VELOXQ_EINVAL, "n + n3 must fit 32-bit column indices");
     struct Pair {
-        int64_t a, b;   // a < b
+        int32_t a, b;   // a < b (N fits 32 bits)
         double v;
     };
     std::vector<Pair> pairs;
@@ -39,7 +39,7 @@ static int reduce3(int64_t n, const double* h, int64_t n2, const int64_t* pi, co
         a = at(a);
         b = at(b);
         if (a > b) std::swap(a, b);
-        pairs.push_back(Pair{a, b, v});
+        pairs.push_back(Pair{(int32_t)a, (int32_t)b, v});
     };
     for (int64_t q = 0; q < n2; ++q) {
         if (pi[q] < 0 || pi[q] >= n || pj[q] < 0 || pj[q] >= n || pi[q] == pj[q])
@@ -71,10 +71,35 @@ static int reduce3(int64_t n, const double* h, int64_t n2, const int64_t* pi, co
         add(j, k, m);
         add(i, k, m);
     }
-    // stable: repeated pairs keep the order of the terms that made them, so
-    // their values are summed in that order under any numbering
-    std::stable_sort(pairs.begin(), pairs.end(),
-                     [](const Pair& x, const Pair& y) { return x.a != y.a ? x.a < y.a : x.b < y.b; });
+    // Sort by (a, b), stably: repeated pairs keep the order of the terms that
+    // made them, so their values are summed in that order under any
+    // numbering. A stable counting sort by a, then a stable insertion sort by
+    // b within each row (rows hold a handful of pairs): the order of one
+    // stable sort by (a, b), in linear time.
+    {
+        std::vector<int64_t> start((size_t)N + 1, 0);
+        for (const Pair& p : pairs) ++start[(size_t)p.a + 1];
+        for (int64_t i = 0; i < N; ++i) start[(size_t)i + 1] += start[(size_t)i];
+        std::vector<Pair> byrow(pairs.size());
+        {
+            std::vector<int64_t> fill(start.begin(), start.end() - 1);
+            for (const Pair& p : pairs) byrow[(size_t)fill[(size_t)p.a]++] = p;
+        }
+        for (int64_t i = 0; i < N; ++i) {
+            Pair* r = byrow.data() + start[(size_t)i];
+            const int64_t len = start[(size_t)i + 1] - start[(size_t)i];
+            for (int64_t x = 1; x < len; ++x) {
+                const Pair key = r[x];
+                int64_t y = x - 1;
+                while (y >= 0 && r[y].b > key.b) {
+                    r[y + 1] = r[y];
+                    --y;
+                }
+                r[y + 1] = key;
+            }
+        }
+        pairs.swap(byrow);
+    }
     // merge repeated pairs
     size_t m = 0;
     for (size_t q = 0; q < pairs.size(); ++q) {

@@ -191,11 +191,24 @@ int sparse_energy_x(veloxq_ctx* ctx, int64_t B, const uint8_t* X, int64_t* parts
 // persistent batched kernel (vq_batch.cu)
 bool batch_supported(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p);
 bool batch_stages_fit(int prec, int method, int stages, int32_t R);   // the form fits shared memory
+// The captured device part of a batched solve, reused while its key (every
+// pointer, size and parameter its nodes bake in) is unchanged.
+struct BatchGraph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;   // around the persistent kernel
+    ~BatchGraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
 // stages: pipeline depth (4 or 6); split: replica groups per instance, each a
-// work item of R / split replicas (a multiple of 16)
+// work item of R / split replicas (a multiple of 16); graph (or null): run the
+// device part as a captured graph kept there
 int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams& p, uint64_t seed, cudaStream_t st,
               int stages, int split, DevBuf& work, int64_t* d_best_all, int* d_err, float* ms_main,
-              int64_t* launches = nullptr);
+              int64_t* launches = nullptr, BatchGraph* graph = nullptr);
 
 // adjoint of the step (vq_adjoint.cu); the timing covers the whole gradient
 // and, separately, the reverse-step kernels (k_adj_a, k_adj_b, k_adj_reduce)

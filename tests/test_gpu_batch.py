@@ -271,3 +271,23 @@ def test_batch_tune_cache_file(B, tmp_path, monkeypatch):
     assert len(lines) == 1 and "|R48|" in lines[0]
     st, grp = (int(v) for v in lines[0].split("=")[1].split())
     assert (st, grp) == (t.batch_stages, t.batch_group) and st in (4, 6) and 48 % grp == 0
+
+
+def test_batch_graph_replays_with_new_seeds(B, monkeypatch):
+    """The captured batch solve is replayed for a new seed: seeds 5, 6, 5 in a
+    row give two different results and the first one again, bit for bit,
+    each equal to an uncaptured run (a fresh batch of the same instances)."""
+    monkeypatch.delenv("VELOXQ_BATCH_FORM", raising=False)
+    sizes = [120, 260, 64, 333]
+    insts = [_sk(n, 140 + i) for i, n in enumerate(sizes)]
+    ctxs = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    sched = B.make_schedule(prec=1, readout_every=0)
+    runs = [B.veloxq_solve_batch(ctxs, 32, 80, sched, seed=s) for s in (5, 6, 5)]
+    assert np.array_equal(runs[0]["E"], runs[2]["E"])
+    assert all(np.array_equal(a, b) for a, b in zip(runs[0]["x"], runs[2]["x"]))
+    assert not np.array_equal(runs[0]["E"], runs[1]["E"])
+    t = B.veloxq_last_timing(ctxs[0])
+    assert t.main_launches == 1 and t.launches <= 4
+    fresh = [B.veloxq_create_dense(Q, c) for Q, c in insts]
+    ref = B.veloxq_solve_batch(fresh, 32, 80, sched, seed=6)
+    assert np.array_equal(ref["E"], runs[1]["E"])

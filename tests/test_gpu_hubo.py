@@ -104,3 +104,42 @@ def test_stream_chunked_order_bitwise_equal_to_unchunked(B):
     small = B.veloxq_solve(ctx, 64, 30, sched, seed=7)
     assert B.veloxq_last_timing(ctx).stream_chunk == 0
     assert np.array_equal(big["E_per_replica"][:64], small["E_per_replica"])
+
+
+def test_hubo_chain_5e7_full_size(B):
+    """The third-order chain at the paper's largest scale (Sec. "HUBO": a
+    chain of N = 5e7 spins, reduced by eq. reduction to 1e8 second-order
+    spins, float couplings, auxiliary spins numbered next to their terms), as
+    the bench runs it: the field of sampled rows against the oracle's field
+    of the coupled pairs touching them (built from the reduced couplings,
+    which the CPU tests pin to the oracle's own reduction), and a solve whose
+    returned energy the energy entry point reproduces and whose third-order
+    cost bounds the reduced one."""
+    N, R = 5 * 10 ** 7, 2
+    inst = I.hubo_chain_3body(N, seed=0)
+    red = B.veloxq_hubo3_reduce(inst.n, inst.h, inst.pairs, inst.triples, local=True)
+    n = red["n"]
+    assert n == 2 * N - 2
+    ctx = B.veloxq_create_ising_csr(n, red["rowptr"], red["col"], red["val"], red["lin"])
+    rp = red["rowptr"]
+    rows = np.sort(np.random.default_rng(3).choice(n, size=64, replace=False))
+    ri = np.concatenate([np.full(rp[r + 1] - rp[r], r, dtype=np.int64) for r in rows])
+    cj = np.concatenate([red["col"][rp[r]:rp[r + 1]] for r in rows]).astype(np.int64)
+    jv = np.concatenate([red["val"][rp[r]:rp[r + 1]] for r in rows])
+    pi, pj = np.minimum(ri, cj), np.maximum(ri, cj)
+    _, first = np.unique(pi * n + pj, return_index=True)
+    psub, _ = O.ising_pairs_to_qubo(n, pi[first], pj[first], jv[first])
+    S = I.uniform_state(R, n, seed=4)
+    F = torch.empty(R, n, device="cuda")
+    B.veloxq_field_dev(ctx, R, B.VELOXQ_PREC_FP32, torch.as_tensor(S, device="cuda"), F)
+    torch.cuda.synchronize()
+    Fg = F.cpu().numpy()[:, rows].astype(np.float64)
+    Sd = S.astype(np.float64)
+    ref = O.field(psub, Sd)[:, rows]
+    sc = O.abs_field(psub, Sd)[:, rows]
+    assert np.all(np.abs(Fg - ref) <= 1e-5 * sc + 1e-30)
+    del S, Sd, F
+    out = B.veloxq_solve(ctx, R, 30, B.make_schedule(readout_every=0), seed=0)
+    assert out["E"] == np.min(out["E_per_replica"])
+    again = B.veloxq_energy(ctx, out["x"][None])
+    assert abs(again["E"][0] - out["E"]) <= 1e-9 * max(1.0, abs(out["E"]))
