@@ -111,6 +111,23 @@ def workload(name: str, for_oracle: bool = False) -> dict:
                 "K": 2000, "readout_every": 100,
                 "desc": "planted 3-regular 3-XORSAT (Sec. 3R3X), 1e5 equations and variables, reduced to second "
                         "order by eq. reduction (n = 2e5), ground energy -1e5 by construction, float CSR"}
+    if name in ("pegasus_p16", "zephyr_z12", "pegasus_p150", "zephyr_z150", "zephyr_z1750"):
+        m = int(name.split("_")[1][1:])
+        graph = "pegasus" if name.startswith("pegasus") else "zephyr"
+        R, K = (1024, 1000) if m <= 16 else (2, 50) if m > 1000 else (256, 400)
+        w = {"name": name, "kind": "qubo_csr", "graph": graph, "m": m, "R": R, "K": K, "readout_every": 50,
+             "desc": f"random QUBO on the {graph.capitalize()} graph "
+                     f"{'P' if graph == 'pegasus' else 'Z'}_{m}{'' if graph == 'pegasus' else ' (t = 4)'} "
+                     "(Sec. " + ("Pegasus" if graph == "pegasus" else "Zephyr") + " topology), Q_ij, c_i ~ U[-1, 1), "
+                     "float CSR"}
+        if m > 1000:
+            w["oracle_graph_m"] = 50          # the oracle's sample: Z_50 by the same recipe (same local structure)
+        if not (for_oracle and m > 1000):
+            w["sp"] = I.pegasus_qubo(m, seed=0) if graph == "pegasus" else I.zephyr_qubo(m, seed=0)
+            w["n"] = w["sp"].n
+        else:
+            w["n"] = 4 * 4 * m * (2 * m + 1)
+        return w
     if name == "lattice_l464":
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
@@ -167,6 +184,9 @@ def reduce_hubo(B, w):
 def create(B, w, stream=None):
     if w["kind"] == "hubo":
         reduce_hubo(B, w)
+    if w["kind"] == "qubo_csr":
+        sp = w["sp"]
+        return B.veloxq_create_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
     if w["kind"] in ("ising_csr", "grad", "hubo"):
         sp = w["sp"]
         return B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin, stream)
@@ -176,7 +196,7 @@ def create(B, w, stream=None):
 
 
 def input_arrays(w) -> list:
-    if w["kind"] in ("ising_csr", "grad", "hubo"):
+    if w["kind"] in ("ising_csr", "grad", "hubo", "qubo_csr"):
         sp = w["sp"]
         return [sp.rowptr, sp.col, sp.val, sp.lin]
     if w["kind"] == "batch":
@@ -195,6 +215,12 @@ def oracle_problem(w):
         sp = w["sp"]
         p, _ = O.ising_csr_to_qubo(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
         return p
+    if w["kind"] == "qubo_csr":
+        if "oracle_graph_m" in w:
+            sp = I.zephyr_qubo(w["oracle_graph_m"], seed=0)
+        else:
+            sp = w["sp"]
+        return O.problem_from_csr(sp.n, sp.rowptr, sp.col, sp.val.astype(np.float64), sp.lin)
     return O.problem_from_dense(w["Q"], w["c"])
 
 
@@ -272,10 +298,15 @@ def oracle_procs(w, R_s: int) -> int:
                 avail = min(avail, int(v)) if avail else int(v)
     except OSError:
         pass
-    n_eff = 2 * int(w["oracle_chain"]) if "oracle_chain" in w else int(w["n"])
+    if "oracle_chain" in w:
+        n_eff = 2 * int(w["oracle_chain"])
+    elif "oracle_graph_m" in w:
+        n_eff = 4 * 4 * w["oracle_graph_m"] * (2 * w["oracle_graph_m"] + 1)
+    else:
+        n_eff = int(w["n"])
     if "Q" in w:
         nnz = n_eff ** 2
-    elif "sp" in w and "oracle_chain" not in w:
+    elif "sp" in w and "oracle_chain" not in w and "oracle_graph_m" not in w:
         nnz = int(np.asarray(w["sp"].rowptr)[-1]) + n_eff
     else:
         nnz = 8 * n_eff
@@ -790,7 +821,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_iters = max(1, min(args.steps, 3 if run.batch else 5))
     pinned = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy() for a in input_arrays(w)]
     h2d = int(sum(a.nbytes for a in pinned))
-    if w["kind"] in ("ising_csr", "grad", "hubo"):
+    if w["kind"] in ("ising_csr", "grad", "hubo", "qubo_csr"):
         pw = dict(w)
         pw["sp"] = I.SparseCoupling(n, pinned[0], pinned[1], pinned[2], pinned[3])
     elif w["kind"] == "batch":
@@ -853,8 +884,10 @@ def run_ours(args, rank, world, local_rank):
         procs = oracle_procs(w, R_s)
         rate, dt, used = oracle_parallel_rate(w, R_s, K_s2, procs)
         what = "reverse-mode gradient over" if run.grad else "solve of"
-        inst = ("the same instance" if "oracle_chain" not in w else
-                f"a chain of {w['oracle_chain']:.0e} spins by the same recipe (n = {n_s} after reduction)")
+        inst = ("the same instance" if "oracle_chain" not in w and "oracle_graph_m" not in w else
+                f"a chain of {w['oracle_chain']:.0e} spins by the same recipe (n = {n_s} after reduction)"
+                if "oracle_chain" in w else
+                f"the Zephyr graph Z_{w['oracle_graph_m']} by the same recipe (n = {n_s})")
         cpu = {"value": rate, "unit": "spin-updates/s", "cores": used, "kind": "oracle",
                "sample": f"{what} {R_s} replicas x first {K_s2} of {K} steps of {inst}, FP64, "
                          f"{used} independent processes at once (replica-parallel, {dt:.1f} s wall)",

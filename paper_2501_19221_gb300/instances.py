@@ -19,6 +19,10 @@ Families (each cites the passage whose shape it imitates):
   planting family, very large sparse instances of Sec. "Zephyr").
 * ``random_sparse_qubo`` -- ragged sparse QUBO (empty rows, uneven degree) used
   as an edge case by the tests.
+* ``pegasus_edges`` / ``zephyr_csr`` and ``pegasus_qubo`` / ``zephyr_qubo`` --
+  the D-Wave Pegasus P_m and Zephyr Z_{m,t} topologies (Sec. "Pegasus
+  topology", Sec. "Zephyr topology") with random QUBO couplings on their
+  edges.
 
 Sparse instances are returned as symmetric CSR (both (i, j) and (j, i) are
 stored, column indices strictly increasing within each row, no diagonal).
@@ -41,6 +45,10 @@ __all__ = [
     "random_sparse_qubo",
     "uniform_state",
     "random_binary",
+    "pegasus_edges",
+    "pegasus_qubo",
+    "zephyr_csr",
+    "zephyr_qubo",
 ]
 
 
@@ -379,3 +387,170 @@ def xorsat_3r3x(n: int, seed: int = 0) -> Xorsat3R3X:
     empty = np.zeros(0, dtype=np.int64)
     hubo = Hubo3(n, np.zeros(n), (empty, empty, np.zeros(0)), (T[:, 0], T[:, 1], T[:, 2], K))
     return Xorsat3R3X(T, b, x, hubo, -float(n))
+
+
+# ----------------------------------------------------------------------------- annealer topologies
+# Both are graphs of line segments (qubits) on a grid: a vertical and a
+# horizontal segment that cross are joined by an internal coupler, collinear
+# neighbouring segments by an external coupler, and paired parallel segments
+# by an odd coupler (Boothby et al., "Next-generation topology of D-Wave
+# quantum processors", 2020, for Pegasus; the Zephyr topology white paper of
+# 2021 for Zephyr).
+
+# Pegasus: per-track offsets of the segments of the standard topology (track k
+# of a vertical / horizontal bundle), in units of the 12-track tile.
+_PEG_OFF_V = np.array([2, 2, 2, 2, 10, 10, 10, 10, 6, 6, 6, 6], dtype=np.int64)
+_PEG_OFF_H = np.array([6, 6, 6, 6, 2, 2, 2, 2, 10, 10, 10, 10], dtype=np.int64)
+
+
+def pegasus_edges(m: int):
+    """The Pegasus graph P_m, fabric only: (n, u, v) with edges u < v.
+
+    Qubit (o, w, k, z), o in {0 vertical, 1 horizontal}, w in [0, m),
+    k in [0, 12), z in [0, m - 1), is the segment on track 12 w + k spanning
+    [12 z + off_o[k], 12 z + off_o[k] + 12) along its direction. Internal
+    couplers join crossing vertical and horizontal segments, external ones
+    (o, w, k, z) and (o, w, k, z + 1), odd ones tracks 2i and 2i + 1 of the
+    same (o, w, z). Qubits without an internal coupler (at the boundary) are
+    not part of the fabric and are dropped; the rest are numbered in order of
+    (o, w, k, z)."""
+    if m < 2:
+        raise ValueError("Pegasus needs m >= 2")
+    M1 = m - 1
+
+    def idx(o, w, k, z):
+        return ((o * m + w) * 12 + k) * M1 + z
+
+    w, k, z = np.meshgrid(np.arange(m), np.arange(12), np.arange(M1), indexing="ij")
+    w, k, z = w.ravel(), k.ravel(), z.ravel()
+    us, vs = [], []
+    for o in (0, 1):
+        e = z + 1 < M1
+        us.append(idx(o, w[e], k[e], z[e]))
+        vs.append(idx(o, w[e], k[e], z[e] + 1))
+        e = k % 2 == 0
+        us.append(idx(o, w[e], k[e], z[e]))
+        vs.append(idx(o, w[e], k[e] + 1, z[e]))
+    # internal: each vertical segment crosses the 12 rows of its span; row y is
+    # track k' = y % 12 of horizontal bundle w' = y // 12, whose segment over
+    # column x = 12 w + k is z' = (x - off_H[k']) // 12
+    x = 12 * w + k
+    y0 = 12 * z + _PEG_OFF_V[k]
+    for dy in range(12):
+        y = y0 + dy
+        wp, kp = y // 12, y % 12
+        zp = np.floor_divide(x - _PEG_OFF_H[kp], 12)
+        e = (wp < m) & (zp >= 0) & (zp < M1)
+        us.append(idx(0, w[e], k[e], z[e]))
+        vs.append(idx(1, wp[e], kp[e], zp[e]))
+    u = np.concatenate(us)
+    v = np.concatenate(vs)
+    nfull = 2 * m * 12 * M1
+    internal = np.zeros(nfull, dtype=bool)
+    cut = sum(a.shape[0] for a in us[:4])          # the external and odd couplers come first
+    internal[u[cut:]] = True
+    internal[v[cut:]] = True
+    keep = internal[u] & internal[v]
+    new = np.cumsum(internal) - 1
+    u, v = new[u[keep]], new[v[keep]]
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    return int(internal.sum()), lo.astype(np.int64), hi.astype(np.int64)
+
+
+def _pair_uniform(lo: np.ndarray, hi: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """A value uniform in [-1, 1) per unordered pair (lo < hi), from a
+    counter-based hash of (seed, lo n + hi) (SplitMix64's finaliser): the same
+    at (i, j) and (j, i) without an edge list."""
+    x = (lo.astype(np.uint64) * np.uint64(n) + hi.astype(np.uint64)) ^ np.uint64((seed * 0x9E3779B97F4A7C15) & (2 ** 64 - 1))
+    with np.errstate(over="ignore"):
+        x = x + np.uint64(0x9E3779B97F4A7C15)
+        x = (x ^ (x >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        x = (x ^ (x >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+        x = x ^ (x >> np.uint64(31))
+    return ((x >> np.uint64(11)).astype(np.float64) * 2.0 ** -53) * 2.0 - 1.0
+
+
+def pegasus_qubo(m: int, seed: int = 0) -> SparseCoupling:
+    """Random QUBO on the Pegasus fabric P_m (Sec. "Pegasus topology"):
+    Q_ij ~ U[-1, 1) on every coupler, linear terms c_i ~ U[-1, 1). Stored as
+    a symmetric float32 CSR with Q_ij / 2 at both (i, j) and (j, i), so that a
+    pair contributes Q_ij x_i x_j to E(x) = sum_ij Q_ij x_i x_j + c x."""
+    n, u, v = pegasus_edges(m)
+    q = _pair_uniform(u, v, n, seed)
+    rowptr, col, val = _csr_from_edges(n, u, v, (0.5 * q).astype(np.float32))
+    lin = np.random.default_rng(seed + 1).uniform(-1.0, 1.0, size=n)
+    return SparseCoupling(n, rowptr, col, val, lin)
+
+
+def zephyr_csr(m: int, t: int = 4):
+    """The Zephyr graph Z_{m,t} as a symmetric CSR pattern: (n, rowptr, col).
+
+    Qubit (o, w, k, j, z), o in {0 vertical, 1 horizontal}, w in [0, 2m],
+    k in [0, t), j in {0, 1}, z in [0, m), is the segment on track (k, j) of
+    bundle w spanning half-tiles [2 z + j, 2 z + j + 2) along its direction
+    (the j = 1 tracks staggered by one half-tile). Internal couplers join
+    crossing segments (each crosses the 2t tracks of the two bundles of its
+    span: 4t of them away from the boundary), external ones (..., z) and
+    (..., z + 1), odd ones the two overlapping segments of the other track of
+    the same (o, w, k). n = 4 t m (2 m + 1); degree at most 4 t + 4.
+    Built as a table of every qubit's neighbours (4 t + 4 columns), so that no
+    global sort of the ~n (2t + 2) entries is needed."""
+    if m < 1 or t < 1:
+        raise ValueError("Zephyr needs m >= 1 and t >= 1")
+    W = 2 * m + 1
+    n = 2 * W * t * 2 * m
+
+    def idx(o, w, k, j, z):
+        return (((o * W + w) * t + k) * 2 + j) * m + z
+
+    D = 4 * t + 4
+    half = n // 2                                      # qubits of one orientation, in (w, k, j, z) order
+    it = np.int64 if n > 2 ** 31 - 2 else np.int32
+    nb = np.empty((n, D), dtype=it)
+    w, k, j, z = (a.ravel().astype(it) for a in
+                  np.meshgrid(np.arange(W), np.arange(t), np.arange(2), np.arange(m), indexing="ij"))
+    for o in (0, 1):
+        blk = nb[o * half:(o + 1) * half]              # rows of this orientation, contiguous
+        cols = []
+        # external
+        cols.append(np.where(z + 1 < m, idx(o, w, k, j, z + 1), -1))
+        cols.append(np.where(z >= 1, idx(o, w, k, j, z - 1), -1))
+        # odd: the segments of the other track of (o, w, k) that overlap this one
+        zb = np.where(j == 0, z - 1, z + 1)
+        cols.append(idx(o, w, k, 1 - j, z))
+        cols.append(np.where((zb >= 0) & (zb < m), idx(o, w, k, 1 - j, zb), -1))
+        # internal: bundles w' in {2z + j, 2z + j + 1} of the other orientation;
+        # track (k', j') of bundle w' covers this qubit's bundle w when
+        # j' <= w < 2m + j', with the segment z' = (w - j') // 2
+        for dw in (0, 1):
+            wp = 2 * z + j + dw
+            for kp in range(t):
+                for jp in (0, 1):
+                    cols.append(np.where((jp <= w) & (w < 2 * m + jp), idx(1 - o, wp, kp, jp, (w - jp) // 2), -1))
+        assert len(cols) == D
+        for c, v in enumerate(cols):
+            blk[:, c] = v
+        del cols
+    nb.sort(axis=1)                                    # -1 (absent) first, then ascending columns
+    deg = (nb >= 0).sum(axis=1)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(deg, out=rowptr[1:])
+    col = nb[nb >= 0].astype(np.int32)
+    return n, rowptr, col
+
+
+def zephyr_qubo(m: int, t: int = 4, seed: int = 0) -> SparseCoupling:
+    """Random QUBO on the Zephyr graph Z_{m,t} (Sec. "Zephyr topology"):
+    Q_ij ~ U[-1, 1) on every coupler, c_i ~ U[-1, 1); symmetric float32 CSR
+    with Q_ij / 2 at both positions, as pegasus_qubo."""
+    n, rowptr, col = zephyr_csr(m, t)
+    val = np.empty(col.shape[0], dtype=np.float32)
+    step = 1 << 22                                     # rows per chunk (bounded temporaries)
+    for r0 in range(0, n, step):
+        r1 = min(n, r0 + step)
+        p0, p1 = int(rowptr[r0]), int(rowptr[r1])
+        rows = np.repeat(np.arange(r0, r1, dtype=np.int64), np.diff(rowptr[r0:r1 + 1]))
+        c64 = col[p0:p1].astype(np.int64)
+        val[p0:p1] = 0.5 * _pair_uniform(np.minimum(rows, c64), np.maximum(rows, c64), n, seed)
+    lin = np.random.default_rng(seed + 1).uniform(-1.0, 1.0, size=n)
+    return SparseCoupling(n, rowptr, col, val, lin)
