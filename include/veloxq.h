@@ -149,8 +149,10 @@ typedef struct {
     int64_t launches;       /* kernels this library launched for the solve */
     int32_t path;           /* veloxq_path that ran */
     int32_t main_launches;  /* launches inside ms_main (1 for the resident kernel, else the step kernels) */
-    int32_t stream_gather;  /* streaming path: couplings gathered at a time (1, 4 or 6, timed per context
-                               and replica count); else 0 */
+    int32_t stream_gather;  /* streaming path: couplings gathered at a time (1, 4 or 6; timed per context
+                               and replica count, or fixed by the environment variable
+                               VELOXQ_STREAM_FORM="gather chunk", chunk in replicas as in stream_chunk,
+                               EINVAL if it does not fit); else 0 */
     int32_t stream_chunk;   /* streaming path: replicas per chunk of the step's thread order (every row of
                                one chunk before the next; 0: all replicas at once); else 0 */
     int32_t batch_stages;   /* one-launch veloxq_solve_batch: pipeline stages of the autotuned form; else 0 */

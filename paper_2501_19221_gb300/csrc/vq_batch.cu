@@ -32,70 +32,30 @@
 #include <queue>
 #include <vector>
 
+#include "vq_async.cuh"
 #include "vq_internal.cuh"
 
 namespace vq {
 
 namespace {
 
-constexpr long long kWaitCycles = 4000000000LL;
 enum { BT_ERR_PRODUCER = 1, BT_ERR_MMA = 2, BT_ERR_EPILOGUE = 4 };
 constexpr int TILE_M = 128, TILE_KB = 128;                // rows and bytes of K per tile
 constexpr uint32_t A_TILE = TILE_M * TILE_KB;             // 16 KB
 template <int PREC> constexpr int tile_k() { return PREC == 1 ? 64 : 128; }   // elements of K per tile
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mb_init(uint64_t* b, uint32_t c) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(c) : "memory");
-}
-__device__ __forceinline__ void mb_expect(uint64_t* b, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mb_arrive(uint64_t* b) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(b)) : "memory");
-}
-__device__ __forceinline__ bool mb_try(uint64_t* b, uint32_t par) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(par)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool mb_wait(uint64_t* b, uint32_t par, int* err, int code) {
-    const long long t0 = clock64();
-    uint32_t spins = 0;
-    while (!mb_try(b, par)) {
-        if ((++spins & 1023u) == 0) {
-            if (*(volatile int*)err) return false;
-            if (clock64() - t0 > kWaitCycles) {
-                atomicOr(err, code);
-                return false;
-            }
-        }
-    }
-    return true;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(su32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(su32(bar))
-                 : "memory");
-}
-// The same copy marked evict-first in L2: the coupling tiles stream through
-// once per step, and should not push out the replica operand, which every row
-// tile of the instance reads again.
-__device__ __forceinline__ uint64_t l2_evict_first_policy() {
-    uint64_t pol;
-    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
-    return pol;
-}
-__device__ __forceinline__ void bulk_g2s_stream(void* dst, const void* src, uint32_t bytes, uint64_t* bar,
-                                                uint64_t pol) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
-                 ::"r"(su32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(su32(bar)), "l"(pol)
-                 : "memory");
-}
+using vqa::bulk_g2s;
+using vqa::bulk_g2s_stream;
+using vqa::l2_evict_first_policy;
+using vqa::mb_arrive;
+using vqa::mb_expect;
+using vqa::mb_init;
+using vqa::mb_try;
+using vqa::mb_wait;
+using vqa::su32;
+// (bulk_g2s_stream with an evict-first policy: the coupling tiles stream
+// through once per step, and should not push out the replica operand, which
+// every row tile of the instance reads again)
 __device__ __forceinline__ void tcf_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tcf_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ uint64_t sdesc(const void* p) {

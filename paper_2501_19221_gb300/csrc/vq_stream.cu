@@ -6,6 +6,8 @@
 // Step (App. B, ballistic form):  F_i = sum_{j != i} Qs_ij s_j  over the CSR
 // row of i, then phi, y, s, walls. Couplings come as FP32 Qs or, for integer
 // instances with |2 Qs| <= 127, as int8 2Qs (F = acc / 2, exact scaling).
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "vq_internal.cuh"
@@ -257,10 +259,29 @@ static std::vector<int32_t> chunk_candidates(int64_t n, int32_t R) {
 
 // Pick the gather variant (one, four or six couplings at a time) and the
 // replica chunk width of the streaming kernels for R replicas by timing three
-// steps of each pair on the caller's buffers (contents are overwritten).
+// steps of each pair on the caller's buffers (contents are overwritten);
+// VELOXQ_STREAM_FORM fixes them instead.
 // Runs eagerly on ctx->stream; must not be called during stream capture.
 int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y) {
     if (ctx->stream_unroll != 0 && ctx->stream_tuned_R == R) return VELOXQ_OK;
+    if (const char* form = std::getenv("VELOXQ_STREAM_FORM")) {
+        // a form fixed by the caller: "gather chunk", the chunk in replicas (0: all at once)
+        const int V = vec_width(R);
+        const int32_t nvec = R / V;
+        int u = 0, cr = -1;
+        const bool parsed = std::sscanf(form, "%d %d", &u, &cr) == 2 && cr >= 0 && cr % V == 0;
+        const int32_t cv = parsed ? cr / V : -1;
+        const bool ok = parsed && (u == 1 || u == 4 || (u == 6 && ctx->uniform_deg == 6)) &&
+                        (cv == 0 || nvec % cv == 0);
+        if (!ok)
+            return fail(VELOXQ_EINVAL, "VELOXQ_STREAM_FORM must be \"gather chunk\": gather 1, 4 or 6 (rows of exactly "
+                                       "6 couplings) and a chunk of replicas (0: all) that the replica count splits "
+                                       "into");
+        ctx->stream_unroll = u;
+        ctx->stream_cvec = cv;
+        ctx->stream_tuned_R = R;
+        return VELOXQ_OK;
+    }
     cudaEvent_t e0, e1;
     VQ_CUDA(cudaEventCreate(&e0));
     VQ_CUDA(cudaEventCreate(&e1));
