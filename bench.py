@@ -51,6 +51,7 @@ NCU_TRAFFIC = {
     ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
+    ("k_tc_step", "sk_n8192_bf16"): 435_910_845,    # per step: one 200-step launch, 87.18 GB / 200
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
@@ -132,13 +133,18 @@ def workload(name: str, for_oracle: bool = False) -> dict:
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
                 "readout_every": 50, "desc": "periodic 3-D +-J lattice L=464 (n ~ 1e8), int8 CSR"}
-    if name in ("wishart_b512", "wishart_b512_fp8"):
+    if name in ("wishart_b512", "wishart_b512_fp8", "wishart_b128_k50", "wishart_b128_k50_fp8"):
         sizes = I.wishart_sizes(512, 100, 2000, seed=0)
         fp8 = name.endswith("fp8")
-        return {"name": name, "kind": "batch", "sizes": sizes, "n": int(sizes.sum()), "R": 64, "K": 1000,
-                "readout_every": 0, "prec": 2 if fp8 else 1,
-                "desc": "512 Wishart planted instances, n_i uniform in [100, 2000], alpha 0.75, "
-                        + ("FP8 E4M3 field (S in two terms)" if fp8 else "BF16 field") + ", one persistent launch"}
+        small = "_b128_" in name
+        if small:
+            # the first 128 instances of the same batch, 50 steps: a case small enough for a full ncu capture
+            sizes = sizes[:128]
+        return {"name": name, "kind": "batch", "sizes": sizes, "n": int(sizes.sum()), "R": 64,
+                "K": 50 if small else 1000, "readout_every": 0, "prec": 2 if fp8 else 1,
+                "desc": ("the first 128 of the " if small else "") + "512 Wishart planted instances, n_i uniform in "
+                        "[100, 2000], alpha 0.75, " + ("FP8 E4M3 field (S in two terms)" if fp8 else "BF16 field")
+                        + ", one persistent launch" + (", 50 steps" if small else "")}
     if name in ("sk_n8192_fp32", "sk_n8192_bf16", "sk_n8192_fp8", "sk_n8192_fp8_one_term"):
         Q, c = I.sk_qubo(8192, seed=0)
         form = name[len("sk_n8192_"):]

@@ -74,7 +74,12 @@ typedef enum { VELOXQ_I8 = 0, VELOXQ_I32 = 1, VELOXQ_F32 = 2, VELOXQ_F64 = 3 } v
  *   FP8_ONE_TERM:  the same with S as hi alone: half the tensor-core work, but
  *                  both operands rounded to 4 significant bits (about 3.7%
  *                  normwise). Parallel Annealing's operand (+-1) is exact in one
- *                  term, so FP8 runs it this way too. */
+ *                  term, so FP8 runs it this way too.
+ * BF16 and FP8 run every step up to a readout in one persistent launch; its
+ * tiles go column block (256 replicas) by column block, in groups of two
+ * blocks for BF16 and FP8_ONE_TERM. The environment variable
+ * VELOXQ_TC_COLGROUP (1 to 16 blocks per group) fixes the group; the results
+ * are the same bits for every group. */
 typedef enum {
     VELOXQ_PREC_FP32 = 0,
     VELOXQ_PREC_BF16 = 1,
@@ -82,7 +87,11 @@ typedef enum {
     VELOXQ_PREC_FP8_ONE_TERM = 3
 } veloxq_prec;
 
-/* Kernel path selection (VELOXQ_PATH_AUTO picks by size and format). */
+/* Kernel path selection. VELOXQ_PATH_AUTO picks by size and format: BF16 and
+ * FP8 on dense contexts take the dense path; FP32 on dense contexts the
+ * resident kernel when it fits, else the dense path; sparse contexts the
+ * resident kernel when its couplings fit in shared memory, else the
+ * streaming path. */
 typedef enum {
     VELOXQ_PATH_AUTO = 0,
     VELOXQ_PATH_RESIDENT = 1,  /* sparse rows, whole run in one launch, state in shared memory */

@@ -163,8 +163,12 @@ int upload_schedule(veloxq_ctx* ctx, const RunParams& p) {
 veloxq_path choose_path(const veloxq_ctx* ctx, veloxq_path want, veloxq_prec prec, int32_t R) {
     if (want != VELOXQ_PATH_AUTO) return want;
     if (ctx->dense && prec != VELOXQ_PREC_FP32) return VELOXQ_PATH_DENSE;
-    if (resident_fits(ctx, R, nullptr, nullptr, nullptr)) return VELOXQ_PATH_RESIDENT;
-    return ctx->dense ? VELOXQ_PATH_DENSE : VELOXQ_PATH_STREAM;
+    if (ctx->dense) return resident_fits(ctx, R, nullptr, nullptr, nullptr) ? VELOXQ_PATH_RESIDENT : VELOXQ_PATH_DENSE;
+    // sparse: the resident kernel only when its couplings stay in shared
+    // memory; when every CTA has to re-read them from L2 each step, the
+    // streaming step is faster (Pegasus P_16: 84 against 29 us per step at
+    // 1024 replicas, Zephyr Z_12: 228 against 29)
+    return resident_on_chip(ctx, R) ? VELOXQ_PATH_RESIDENT : VELOXQ_PATH_STREAM;
 }
 
 int check_path(const veloxq_ctx* ctx, veloxq_path path, veloxq_prec prec, int32_t R) {

@@ -175,6 +175,8 @@ int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y
 
 // sparse resident kernel (vq_resident.cu)
 bool resident_fits(const veloxq_ctx* ctx, int32_t R, int* rc, int* threads, size_t* smem);
+// the resident plan for R replicas keeps the couplings in shared memory
+bool resident_on_chip(const veloxq_ctx* ctx, int32_t R);
 int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, uint64_t seed, int k_begin, int k_end,
                  const float* S_in, const float* Y_in, float* S_out, float* Y_out, float* F_out,
                  int64_t* best_e, uint32_t* best_bits);

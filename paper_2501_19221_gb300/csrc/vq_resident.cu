@@ -93,6 +93,11 @@ bool resident_fits(const veloxq_ctx* ctx, int32_t R, int* rc, int* threads, size
     return p.ok;
 }
 
+bool resident_on_chip(const veloxq_ctx* ctx, int32_t R) {
+    const ResPlan p = make_plan(ctx, R);
+    return p.ok && p.csr_smem;
+}
+
 int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed, int k_begin, int k_end,
                  const float* S_in, const float* Y_in, float* S_out, float* Y_out, float* F_out, int64_t* best_e,
                  uint32_t* best_bits) {

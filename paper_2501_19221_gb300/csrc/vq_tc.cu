@@ -38,6 +38,7 @@
 #include <cuda_fp8.h>
 
 #include <algorithm>
+#include <cstdlib>
 
 #include "vq_internal.cuh"
 
@@ -268,7 +269,8 @@ struct TcArgs {
     float* Y;                // [R][n]
     void* sop[2];            // [R][n_pad] per term: operand buffers; the first step reads sop[cur]
     int32_t cur;
-    int32_t colmajor;        // tiles of a step column block by column block (runs of several steps)
+    int32_t colmajor;        // runs of several steps: tiles of a step in groups of this many replica
+                             // column blocks, row block by row block within a group; 0: row-major
     const float* bf;         // [n]
     const float* qscale;     // [n] FP8 row scales (FP8 only)
     const float* a_table;
@@ -301,9 +303,12 @@ __device__ __forceinline__ void store_op(void* base, int64_t idx, int64_t plane,
 // those steps, g = pair, pair + pairs, ... with g = j * tiles + t for step
 // k + j. A step's tile (row block r, replica column block c) reads the
 // operand of column block c over every variable, which the previous step's
-// tiles (all r, same c) write: with colmajor, t = c * MT + r, so a step's
-// first column block is ready as soon as the previous step's is, and pairs
-// flow from one step into the next without a grid-wide barrier. The
+// tiles (all r, same c) write: with colmajor = G, a step's tiles come in
+// groups of G column blocks (t = c0 MT + r gc + (c - c0) within the group
+// [c0, c0 + gc)), so a step's first group is ready as soon as the previous
+// step's is, and pairs flow from one step into the next without a
+// grid-wide barrier, while the column blocks of a group share each Qoff row
+// block in L2. The
 // dependency is counted per column block: every epilogue warp adds 1 to
 // done[c] (release) once its rows and columns of the tile are written; a
 // tile of step j > 0 starts loading the operand (and the epilogue reads its
@@ -351,8 +356,15 @@ __global__ void __launch_bounds__(320, 1) k_tc_step(const __grid_constant__ CUte
     // tile t of step j: row block r, column block c
     auto tile_rc = [&](int j, int t, int& r, int& c) {
         if (a.colmajor) {
-            c = t / MT;
-            r = t - c * MT;
+            // group of G column blocks [c0, c0 + gc): every row block of
+            // the group, its column blocks next to each other (they read
+            // the same Qoff row block at about the same time)
+            const int G = a.colmajor;
+            const int c0 = (t / (G * MT)) * G;
+            const int gc = min(G, NT - c0);
+            const int u = t - c0 * MT;
+            r = u / gc;
+            c = c0 + (u - r * gc);
         } else {
             const int tt2 = ((a.k + j) & 1) ? tiles - 1 - t : t;
             r = tt2 / NT;
@@ -742,6 +754,23 @@ int g_max_pairs[kMaxDevices];
 // Steps per launch at most: the completion counters (16 MT per column block
 // and step) stay far below 2^32.
 constexpr int kMaxRunSteps = 4096;
+
+// Replica column blocks per group of a multi-step run's tile order. One
+// block at a time lets the next step start after a quarter of this one (at
+// R = 1024) but reads Qoff once per column block; groups of two read it
+// half as often. Measured at SK n = 8192, R = 1024 (us per step, groups of
+// 1 / 2 / 4): BF16 82.5 / 80.0 / 98.0, FP8 one term 51.8 / 51.1 / 66.0, FP8
+// two terms (tensor-bound) 69.9 / 70.7 / 92.2. VELOXQ_TC_COLGROUP (1 to 16)
+// fixes it.
+int tc_column_group(int prec, int terms) {
+    static const int forced = [] {
+        const char* e = std::getenv("VELOXQ_TC_COLGROUP");
+        const int v = e ? std::atoi(e) : 0;
+        return (v >= 1 && v <= 16) ? v : 0;
+    }();
+    if (forced) return forced;
+    return (prec == VELOXQ_PREC_FP8 && terms == 2) ? 1 : 2;
+}
 }  // namespace
 
 int tc_run(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CUtensorMap* ms,
@@ -809,7 +838,7 @@ int tc_run(veloxq_ctx* ctx, int prec, int32_t R, const CUtensorMap& mq, const CU
         a.sop[0] = sop ? sop[0] : nullptr;
         a.sop[1] = sop ? sop[1] : nullptr;
         a.cur = (cur + (k0 - k_begin)) & 1;
-        a.colmajor = steps > 1 ? 1 : 0;
+        a.colmajor = steps > 1 ? (int32_t)std::min<int64_t>(tc_column_group(prec, terms), NT) : 0;
         a.bf = ctx->bf.as<float>();
         a.qscale = ctx->qscale8.as<float>();
         a.a_table = a_table;

@@ -256,12 +256,14 @@ def test_tc_field_mid_sizes(B, prec, n, R):
 
 @pytest.mark.parametrize("method", [0, 2])
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("n,R", [(3000, 1024), (700, 96)])
+@pytest.mark.parametrize("n,R", [(3000, 1024), (1500, 768), (700, 96)])
 def test_tc_run_equals_single_steps(B, prec, method, n, R):
     """Several steps in one launch (the solve's form: tiles of consecutive
-    steps overlap, each waiting for the column block of the state it reads)
-    give bit for bit the state and last field of the same steps launched one
-    at a time: the per-tile arithmetic is the same, only the schedule differs."""
+    steps overlap, each waiting for the column block of the state it reads;
+    column blocks in groups of two for BF16 and one-term FP8, the last group
+    of R = 768 a single block) give bit for bit the state and last field of
+    the same steps launched one at a time: the per-tile arithmetic is the
+    same, only the schedule differs."""
     if method == 2 and prec == FP8_ONE_TERM:
         pytest.skip("Parallel Annealing's FP8 forms are the same run")
     Q, c = I.sk_qubo(n, seed=13)

@@ -106,3 +106,18 @@ def test_zephyr_z150_full_size(B):
     assert B.veloxq_last_timing(ctx).path == 2
     again = B.veloxq_energy(ctx, out["x"][None])
     assert abs(again["E"][0] - out["E"]) <= 1e-9 * max(1.0, abs(out["E"]))
+
+
+def test_auto_path_by_where_couplings_fit(B):
+    """The automatic path: the resident kernel when the couplings fit in
+    shared memory (Chimera C16, int8 in packed words), the streaming step
+    when they do not (float couplings of Pegasus P_16 and Zephyr Z_12, which
+    the resident kernel would re-read from L2 every step)."""
+    sp = I.chimera_ising(16, 16, 4, seed=0)
+    ctx = B.veloxq_create_ising_csr(sp.n, sp.rowptr, sp.col, sp.val, sp.lin)
+    B.veloxq_solve(ctx, 1024, 10, B.make_schedule(), seed=1)
+    assert B.veloxq_last_timing(ctx).path == 1
+    for name in GRAPHS:
+        sp, ctx, _ = _make(B, name)
+        B.veloxq_solve(ctx, 1024, 10, B.make_schedule(), seed=1)
+        assert B.veloxq_last_timing(ctx).path == 2
