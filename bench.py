@@ -52,6 +52,8 @@ NCU_TRAFFIC = {
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_tc_step", "sk_n8192_bf16"): 435_910_845,    # per step: one 200-step launch, 87.18 GB / 200
+    ("k_batch", "wishart_b128_k50"): 22_553_989_000,
+    ("k_batch", "wishart_b128_k50_fp8"): 12_609_262_000,
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
@@ -855,7 +857,7 @@ def run_ours(args, rank, world, local_rank):
     e2e = {"value": world * n * R * K / e2e_s, "unit": "spin-updates/s", "h2d_bytes_per_step": h2d,
            "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1e3,
            "create_ms": t_create / e2e_iters * 1e3, "solve_call_ms": t_solve / e2e_iters * 1e3,
-           "includes": "context creation (H2D copy, device ingest, power iteration) + "
+           "includes": "context creation (H2D copy, device ingest, spectral-radius estimate) + "
                        + ("gradient (forward, recompute, reverse)" if run.grad else "solve") + " + D2H of results"}
 
     roof = roofline(B, w, run, path, statistics.mean(mains), main_launches)
@@ -990,7 +992,7 @@ def run_reference(args, rank, world):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="sk_n8192_fp8")
