@@ -123,12 +123,14 @@ def test_first_20_steps_free_running(B, method, name, path):
     assert np.linalg.norm(Sg - Sr) / np.linalg.norm(Sr) <= 1e-4
 
 
-@pytest.mark.parametrize("method", ["asb", "pa"])
-def test_resident_and_stream_paths_identical(B, method):
+@pytest.mark.parametrize("method,R", [("asb", 48), ("pa", 48), ("pa", 6), ("pa", 5)])
+def test_resident_and_stream_paths_identical(B, method, R):
+    """The same solve on both sparse paths gives the same bits (for Parallel
+    Annealing with vectors of 4, 2 and 1 replicas on the streaming path)."""
     ctx, p = inst_chimera(B, 4)
     kw = dict(readout_every=25, method=METHOD[method], dt=0.3)
-    a = B.veloxq_solve(ctx, 48, 400, B.make_schedule(path=1, **kw), seed=3)
-    b = B.veloxq_solve(ctx, 48, 400, B.make_schedule(path=2, **kw), seed=3)
+    a = B.veloxq_solve(ctx, R, 400, B.make_schedule(path=1, **kw), seed=3)
+    b = B.veloxq_solve(ctx, R, 400, B.make_schedule(path=2, **kw), seed=3)
     assert np.array_equal(a["E_per_replica"], b["E_per_replica"])
     assert np.array_equal(a["x"], b["x"]) and a["E_int"] == b["E_int"]
     assert O.energy(p, a["x"][None, :])[0] == a["E_int"]
