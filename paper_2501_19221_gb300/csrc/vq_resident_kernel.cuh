@@ -162,13 +162,51 @@ template <int RC> __device__ __forceinline__ void acc_fma(float (&acc)[RC], floa
 
 __device__ __forceinline__ float ent_w(uint32_t e) { return __half2float(__ushort_as_half((unsigned short)(e >> 16))); }
 
-template <int RC> __device__ __forceinline__ void sign_row(float (&v)[RC]) {
+// Parallel Annealing's binarised spins (+-1) as BF16 at the same element
+// index as the float layout (a row of RC = 8 is two 8-byte pieces at 2 o and
+// 2 (o ^ 4) bytes): half the bytes of the state per neighbour read, and
+// +-1 is exact. A BF16 value is the upper half of its FP32 bits.
+__device__ __forceinline__ float bf_lo(uint32_t w) { return __uint_as_float(w << 16); }
+__device__ __forceinline__ float bf_hi(uint32_t w) { return __uint_as_float(w & 0xFFFF0000u); }
+__device__ __forceinline__ uint32_t sign_bits(float x) { return vqd::pa_sign(x) > 0.0f ? 0x3F80u : 0xBF80u; }
+template <int RC> __device__ __forceinline__ void ld_spin_at(const uint16_t* g, int o, float (&v)[RC]) {
+    if constexpr (RC >= 4) {
 #pragma unroll
-    for (int r = 0; r < RC; ++r) v[r] = vqd::pa_sign(v[r]);
+        for (int h = 0; h < RC / 4; ++h) {
+            const uint2 a = *reinterpret_cast<const uint2*>(g + (h == 0 ? o : (o ^ 4)));
+            v[4 * h] = bf_lo(a.x); v[4 * h + 1] = bf_hi(a.x); v[4 * h + 2] = bf_lo(a.y); v[4 * h + 3] = bf_hi(a.y);
+        }
+    } else if constexpr (RC == 2) {
+        const uint32_t a = *reinterpret_cast<const uint32_t*>(g + o);
+        v[0] = bf_lo(a); v[1] = bf_hi(a);
+    } else {
+        v[0] = __uint_as_float((uint32_t)g[o] << 16);
+    }
+}
+template <int RC> __device__ __forceinline__ void ld_spin(const uint16_t* g, int j, float (&v)[RC]) {
+    if constexpr (RC >= 4) ld_spin_at<RC>(g, soff<RC>(j, 0), v);
+    else ld_spin_at<RC>(g, j * RC, v);
+}
+template <int RC> __device__ __forceinline__ void st_spin(uint16_t* g, int j, const float (&x)[RC]) {
+    if constexpr (RC >= 4) {
+#pragma unroll
+        for (int h = 0; h < RC / 4; ++h) {
+            uint2 a;
+            a.x = sign_bits(x[4 * h]) | (sign_bits(x[4 * h + 1]) << 16);
+            a.y = sign_bits(x[4 * h + 2]) | (sign_bits(x[4 * h + 3]) << 16);
+            *reinterpret_cast<uint2*>(g + soff<RC>(j, h)) = a;
+        }
+    } else if constexpr (RC == 2) {
+        *reinterpret_cast<uint32_t*>(g + 2 * j) = sign_bits(x[0]) | (sign_bits(x[1]) << 16);
+    } else {
+        g[j] = (uint16_t)sign_bits(x[0]);
+    }
 }
 
-// METHOD: the integrator (veloxq_method). For PA the state buffers hold the
-// analog spins x and the field is of their binarised spins. ELL: 0, rows in
+// METHOD: the integrator (veloxq_method). For PA the first state buffer
+// holds the analog spins x, read and written only by their owner thread, and
+// the second holds two BF16 buffers of their binarised spins (the field's
+// operand), current and next; readouts take x = [spin > 0] = [x > 0]. ELL: 0, rows in
 // CSR form; 6, six slots per row (Chimera graphs, cubic lattices), a count
 // known here, so the slot loops unroll completely; 1, a.ell_d slots.
 template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, int ELL, int METHOD>
@@ -243,10 +281,34 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             y[q][r] = yv;
         }
     }
+    // PA: the two spin buffers share the second state region
+    uint16_t* gc = reinterpret_cast<uint16_t*>(sB);
+    uint16_t* gn = gc + (pl.s1 - pl.s0) / sizeof(float);
+    if constexpr (SIGN) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < RPT; ++q) {
+            const int i = tid + q * T;
+            if (i < n) {
+                float x[RC];
+                ld_row<RC>(sA, i, x);
+                st_spin<RC>(gc, i, x);
+            }
+        }
+    }
     __syncthreads();
 
     float* sc = sA;
-    float* sn = sB;
+    float* sn = SIGN ? sA : sB;
+    // a neighbour's field operand: its state row, or (PA) its spin row
+    auto nb_at = [&](int o, float (&v)[RC]) {
+        if constexpr (SIGN) ld_spin_at<RC>(gc, o, v);
+        else ld_row_at<RC>(sc, o, v);
+    };
+    auto nb_row = [&](int j, float (&v)[RC]) {
+        if constexpr (SIGN) ld_spin<RC>(gc, j, v);
+        else ld_row<RC>(sc, j, v);
+    };
     for (int k = a.k_begin; k < a.k_end; ++k) {
         const float a_k = __ldg(a.a_table + k);
         const bool last = (k == a.k_end - 1);
@@ -261,9 +323,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                 for (int p = 0; p < ELLD; p += 2, e += 2 * n) {
                     const uint32_t e0 = e[0], e1 = e[n];
                     float s0[RC], s1[RC];
-                    ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
-                    ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
-                    if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); }
+                    nb_at((int)(e0 & 0xFFFFu), s0);
+                    nb_at((int)(e1 & 0xFFFFu), s1);
                     acc_fma<RC>(acc, ent_w(e0), s0);
                     acc_fma<RC>(acc, ent_w(e1), s1);
                 }
@@ -277,14 +338,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                     if constexpr (CSR_SMEM && PACKED) {
                         const uint32_t e = packs[p];
                         w = ent_w(e);
-                        ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
+                        nb_at((int)(e & 0xFFFFu), sj);
                     } else {
                         int j;
                         if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
                         else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
-                        ld_row<RC>(sc, j, sj);
+                        nb_row(j, sj);
                     }
-                    if constexpr (SIGN) sign_row<RC>(sj);
                     acc_fma<RC>(acc, w, sj);
                 }
             }
@@ -299,11 +359,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             for (int p = 0; p < ELLD; p += 2, e += 2 * n, f += 2 * n) {
                 const uint32_t e0 = e[0], e1 = e[n], f0 = f[0], f1 = f[n];
                 float s0[RC], s1[RC], t0[RC], t1[RC];
-                ld_row_at<RC>(sc, (int)(e0 & 0xFFFFu), s0);
-                ld_row_at<RC>(sc, (int)(e1 & 0xFFFFu), s1);
-                ld_row_at<RC>(sc, (int)(f0 & 0xFFFFu), t0);
-                ld_row_at<RC>(sc, (int)(f1 & 0xFFFFu), t1);
-                if constexpr (SIGN) { sign_row<RC>(s0); sign_row<RC>(s1); sign_row<RC>(t0); sign_row<RC>(t1); }
+                nb_at((int)(e0 & 0xFFFFu), s0);
+                nb_at((int)(e1 & 0xFFFFu), s1);
+                nb_at((int)(f0 & 0xFFFFu), t0);
+                nb_at((int)(f1 & 0xFFFFu), t1);
                 acc_fma<RC>(acc0, ent_w(e0), s0);
                 acc_fma<RC>(acc0, ent_w(e1), s1);
                 acc_fma<RC>(acc1, ent_w(f0), t0);
@@ -345,6 +404,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                 vqd::bsb_update(acc[0], b, a_k, a.dt, a.a0, a.c0, s[0], y[q][0]);
             }
             st_row<RC>(sn, i, s);
+            if constexpr (SIGN) st_spin<RC>(gn, i, s);
             if (last && a.F_out) {
 #pragma unroll
                 for (int r = 0; r < RC; ++r)
@@ -373,7 +433,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             }
         }
         __syncthreads();
-        float* tmp = sc; sc = sn; sn = tmp;
+        if constexpr (SIGN) {
+            uint16_t* t = gc; gc = gn; gn = t;      // x stays in its one buffer
+        } else {
+            float* tmp = sc; sc = sn; sn = tmp;
+        }
 
         const bool readout = (a.readout_every >= 0) &&
                              ((k == a.K - 1) || (a.readout_every > 0 && ((k + 1) % a.readout_every) == 0));
@@ -387,7 +451,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
             const int i = tid + q * T;
             if (i < n) {
                 float si[RC];
-                ld_row<RC>(sc, i, si);
+                nb_row(i, si);
                 bool any = false;
 #pragma unroll
                 for (int r = 0; r < RC; ++r) any |= si[r] > 0.0f;
@@ -402,7 +466,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                         for (int p = 0; p < ELLD; ++p, e += n) {
                             const uint32_t ev = e[0];
                             float sj[RC];
-                            ld_row_at<RC>(sc, (int)(ev & 0xFFFFu), sj);
+                            nb_at((int)(ev & 0xFFFFu), sj);
                             const int64_t wq = (int64_t)__float2int_rn(2.0f * ent_w(ev));
 #pragma unroll
                             for (int r = 0; r < RC; ++r) row[r] += sj[r] > 0.0f ? wq : 0;
@@ -417,12 +481,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
                         if constexpr (CSR_SMEM && PACKED) {
                             const uint32_t e = packs[p];
                             w = ent_w(e);
-                            ld_row_at<RC>(sc, (int)(e & 0xFFFFu), sj);
+                            nb_at((int)(e & 0xFFFFu), sj);
                         } else {
                             int j;
                             if constexpr (CSR_SMEM) { j = cols[p]; w = vals[p]; }
                             else { j = __ldg(a.col + p); w = __ldg(a.wf + p); }
-                            ld_row<RC>(sc, j, sj);
+                            nb_row(j, sj);
                         }
                         // 2 Qs for integer instances (exact), the fixed-point weight otherwise
                         const int64_t wq = a.wfix ? __ldg(a.wfix + p) : (int64_t)__float2int_rn(2.0f * w);
