@@ -1,8 +1,8 @@
 """Random QUBOs on the annealer topologies the paper benchmarks (Sec.
 "Pegasus topology", Sec. "Zephyr topology") through the library: the field,
 one fused step and a solve against the FP64 oracle, on the resident and the
-streaming kernels, and the Zephyr Z_150 instance (7.2e5 variables) at its
-full size on sampled rows."""
+streaming kernels, the automatic path choice, and the Zephyr Z_150 (7.2e5
+variables) and Z_1750 (9.8e7) instances at full size on sampled rows."""
 import numpy as np
 import pytest
 
@@ -121,3 +121,37 @@ def test_auto_path_by_where_couplings_fit(B):
         sp, ctx, _ = _make(B, name)
         B.veloxq_solve(ctx, 1024, 10, B.make_schedule(), seed=1)
         assert B.veloxq_last_timing(ctx).path == 2
+
+
+def test_zephyr_z1750_full_size(B):
+    """Z_1750, the paper's largest instance (9.8e7 variables, 1.96e9 CSR
+    entries), with 2 replicas as the bench runs it: the field of sampled rows
+    against the oracle's field of the couplers touching them, and a short
+    solve whose energy the energy entry point reproduces."""
+    sp = I.zephyr_qubo(1750, seed=0)
+    n, R = sp.n, 2
+    assert n > 9.8e7
+    ctx = B.veloxq_create_csr(n, sp.rowptr, sp.col, sp.val, sp.lin)
+    rows = np.sort(np.random.default_rng(7).choice(n, size=48, replace=False))
+    rp = sp.rowptr
+    ri = np.concatenate([np.full(rp[r + 1] - rp[r], r, dtype=np.int64) for r in rows])
+    cj = np.concatenate([sp.col[rp[r]:rp[r + 1]] for r in rows]).astype(np.int64)
+    qv = np.concatenate([sp.val[rp[r]:rp[r + 1]] for r in rows]).astype(np.float64)
+    pi, pj = np.minimum(ri, cj), np.maximum(ri, cj)
+    _, first = np.unique(pi * n + pj, return_index=True)
+    pi, pj, qv = pi[first], pj[first], qv[first]
+    ps = O.Problem(n, np.concatenate([pi, pj]), np.concatenate([pj, pi]), np.concatenate([qv, qv]), np.zeros(n))
+    S = I.uniform_state(R, n, seed=8)
+    F = torch.empty(R, n, device="cuda")
+    B.veloxq_field_dev(ctx, R, B.VELOXQ_PREC_FP32, _cuda(S), F)
+    torch.cuda.synchronize()
+    Fg = F.cpu().numpy()[:, rows].astype(np.float64)
+    Sd = S.astype(np.float64)
+    ref = O.field(ps, Sd)[:, rows]
+    sc = O.abs_field(ps, Sd)[:, rows]
+    assert np.all(np.abs(Fg - ref) <= 1e-5 * sc + 1e-30)
+    del S, Sd, F
+    out = B.veloxq_solve(ctx, R, 20, B.make_schedule(readout_every=0), seed=1)
+    assert B.veloxq_last_timing(ctx).path == 2
+    again = B.veloxq_energy(ctx, out["x"][None])
+    assert abs(again["E"][0] - out["E"]) <= 1e-9 * max(1.0, abs(out["E"]))
