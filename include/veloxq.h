@@ -55,7 +55,7 @@ typedef enum {
     VELOXQ_ENOMEM = -2,      /* device or host allocation failed */
     VELOXQ_ECUDA = -3,       /* CUDA runtime error (no device, launch failure) */
     VELOXQ_ETIMEDOUT = -4,   /* a bounded device-side wait gave up */
-    VELOXQ_EUNSUPPORTED = -5 /* valid request this build or device cannot run */
+    VELOXQ_EUNSUPPORTED = -5 /* a valid request that the library or the device cannot run */
 } veloxq_status;
 
 /* Element type of a coupling array passed in. */
