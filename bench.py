@@ -135,18 +135,21 @@ def workload(name: str, for_oracle: bool = False) -> dict:
         sp = I.cubic_lattice_ising(464, seed=0)
         return {"name": name, "kind": "ising_csr", "sp": sp, "n": sp.n, "R": 2, "K": 50,
                 "readout_every": 50, "desc": "periodic 3-D +-J lattice L=464 (n ~ 1e8), int8 CSR"}
-    if name in ("wishart_b512", "wishart_b512_fp8", "wishart_b128_k50", "wishart_b128_k50_fp8"):
+    if name in ("wishart_b512", "wishart_b512_fp8", "wishart_b128_k50", "wishart_b128_k50_fp8", "wishart_b512_k20",
+                "wishart_b512_k20_fp8"):
         sizes = I.wishart_sizes(512, 100, 2000, seed=0)
         fp8 = name.endswith("fp8")
         small = "_b128_" in name
         if small:
             # the first 128 instances of the same batch, 50 steps: a case small enough for a full ncu capture
             sizes = sizes[:128]
+        # the whole batch for 20 steps: the same sizes and L2 behaviour, short enough to capture
+        K = 50 if small else 20 if "_k20" in name else 1000
         return {"name": name, "kind": "batch", "sizes": sizes, "n": int(sizes.sum()), "R": 64,
-                "K": 50 if small else 1000, "readout_every": 0, "prec": 2 if fp8 else 1,
+                "K": K, "readout_every": 0, "prec": 2 if fp8 else 1,
                 "desc": ("the first 128 of the " if small else "") + "512 Wishart planted instances, n_i uniform in "
                         "[100, 2000], alpha 0.75, " + ("FP8 E4M3 field (S in two terms)" if fp8 else "BF16 field")
-                        + ", one persistent launch" + (", 50 steps" if small else "")}
+                        + ", one persistent launch" + (f", {K} steps" if K != 1000 else "")}
     if name in ("sk_n8192_fp32", "sk_n8192_bf16", "sk_n8192_fp8", "sk_n8192_fp8_one_term"):
         Q, c = I.sk_qubo(8192, seed=0)
         form = name[len("sk_n8192_"):]

@@ -306,15 +306,28 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                     // F = acc q_i / 448 (Qoff scaled by q_i, S by 448)
                     const float fscale = (PREC == 2 && row_ok) ? __ldg(in.qs + row) * (1.0f / 448.0f) : 1.0f;
                     uint8_t* op_row = sop_n + (size_t)(row / TK) * B_STRIDE;
-                    for (int c = 0; c < R / 16; ++c) {
-                        uint32_t v[16];
-                        tld16(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)R + (uint32_t)(c * 16), v);
-                        float sv[16], yv[16];
+                    // the state of 16 replicas at a time; with 6 stages (one CTA
+                    // per SM, registers to spare) the next chunk's loads are
+                    // issued before this chunk is updated
+                    constexpr bool AHEAD = STAGES == 6;
+                    float sv[16], yv[16];
+                    auto load_chunk = [&](int c, float (&sd)[16], float (&yd)[16]) {
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
                             const int64_t p = (int64_t)(c * 16 + j) * n + row;
-                            sv[j] = row_ok ? S[p] : 0.0f;
-                            yv[j] = row_ok ? Y[p] : 0.0f;
+                            sd[j] = row_ok ? S[p] : 0.0f;
+                            yd[j] = row_ok ? Y[p] : 0.0f;
+                        }
+                    };
+                    if constexpr (AHEAD) load_chunk(0, sv, yv);
+                    for (int c = 0; c < R / 16; ++c) {
+                        uint32_t v[16];
+                        tld16(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)R + (uint32_t)(c * 16), v);
+                        float sn[16], yn[16];
+                        if constexpr (AHEAD) {
+                            if (c + 1 < R / 16) load_chunk(c + 1, sn, yn);
+                        } else {
+                            load_chunk(c, sv, yv);
                         }
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
@@ -330,6 +343,13 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                                 Y[p] = y;
                                 put_op<PREC, TERMS>(op_row + swz<EB>(r0 + r, row % TK), lo_off,
                                                     METHOD == vqd::METHOD_PA ? vqd::pa_sign(s) : s);
+                            }
+                        }
+                        if constexpr (AHEAD) {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                sv[j] = sn[j];
+                                yv[j] = yn[j];
                             }
                         }
                     }
