@@ -6,7 +6,8 @@
 // instance and step, the CTA walks its 128-row tiles: warp 0 streams the
 // pre-tiled operands with 1-D bulk copies, warp 1 issues the MMAs
 // (M = 128 variables, N = R replicas, K = variables) into one of two tensor
-// memory buffers, warps 2-5 read the other buffer back and update their rows
+// memory buffers, warps 2-5 (2-9 in the 6-stage form) read the other buffer
+// back and update their rows
 // (the epilogue of tile t overlaps the main loop of tile t + 1). After the
 // last tile of a step the epilogue warps publish the next operand (a proxy
 // fence and a named barrier) before the producer may read it.
@@ -80,6 +81,12 @@ __device__ __forceinline__ void mma_tile(uint32_t d, uint64_t a, uint64_t b, uin
 __device__ __forceinline__ void mma_commit(uint64_t* b) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b)) : "memory");
 }
+__device__ __forceinline__ void tld8(uint32_t t, uint32_t (&v)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+                 : "r"(t));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void tld16(uint32_t t, uint32_t (&v)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -89,7 +96,14 @@ __device__ __forceinline__ void tld16(uint32_t t, uint32_t (&v)[16]) {
         : "r"(t));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+// Epilogue warps: 8 in the 6-stage form (one CTA per SM; two warps per
+// quarter of the tensor-memory lanes, each taking half of the replica
+// chunks), 4 in the 4-stage form (two CTAs per SM share the registers).
+template <int STAGES> constexpr int epi_warps() { return STAGES == 6 ? 8 : 4; }
+template <int STAGES> constexpr int batch_threads() { return 64 + 32 * epi_warps<STAGES>(); }
+template <int STAGES> __device__ __forceinline__ void epi_bar() {
+    asm volatile("bar.sync 1, %0;" ::"n"(32 * epi_warps<STAGES>()) : "memory");
+}
 
 // byte offset of operand element (row r, k) inside a swizzled tile, for
 // elements of EB bytes
@@ -146,7 +160,7 @@ struct BatchArgs {
 // ballistic form keeps its own register allocation. PREC: 1 BF16, 2 E4M3;
 // TERMS: E4M3 terms of S (1 or 2).
 template <int PREC, int TERMS, int STAGES, int METHOD>
-__global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchArgs a) {
+__global__ void __launch_bounds__(batch_threads<STAGES>(), STAGES == 4 ? 2 : 1) k_batch(const BatchArgs a) {
     constexpr int EB = PREC == 1 ? 2 : 1;
     constexpr int TK = tile_k<PREC>();
     extern __shared__ uint8_t smem_raw[];
@@ -178,7 +192,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
         }
         for (int b = 0; b < 2; ++b) {
             mb_init(&accf[b], 1);
-            mb_init(&acce[b], 4);
+            mb_init(&acce[b], epi_warps<STAGES>());
         }
         mb_init(stepr, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -266,8 +280,10 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
         }
     } else {
         // epilogue: 4 warps, warp w owns tensor-memory lanes 32 (w % 4) .. +31
-        const int q = warp & 3;
-        const int et = threadIdx.x - 64;           // 0..127 among the epilogue warps
+        constexpr int EW = epi_warps<STAGES>();
+        const int q = warp & 3;                    // tensor-memory lanes 32 q .. 32 q + 31
+        const int half = (warp - 2) >> 2;          // with 8 warps: which half of the replica chunks
+        const int et = threadIdx.x - 64;           // 0 .. 32 EW - 1 among the epilogue warps
         uint32_t tt = 0;
         bool ok = true;
         for (int w = first; w < last && ok; ++w) {
@@ -280,7 +296,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
             float* const Y = in.Y + (int64_t)r0 * n;
             // initial state (Philox with the instance's replica index, as every
             // other path) and the first operand
-            for (int64_t e = et; e < (int64_t)R * n; e += 128) {
+            for (int64_t e = et; e < (int64_t)R * n; e += 32 * EW) {
                 const int r = (int)(e / n), i = (int)(e - (int64_t)r * n);
                 float s0, y0;
                 vqd::init_pair(i, r0 + r, *a.seed, a.sigma0, &s0, &y0);
@@ -290,7 +306,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                                     METHOD == vqd::METHOD_PA ? vqd::pa_sign(s0) : s0);
             }
             asm volatile("fence.proxy.async.global;" ::: "memory");
-            epi_bar();
+            epi_bar<STAGES>();
             if (et == 0) mb_arrive(stepr);
             for (int k = 0; k < a.K && ok; ++k) {
                 const float a_k = __ldg(a.a_table + k);
@@ -306,38 +322,46 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                     // F = acc q_i / 448 (Qoff scaled by q_i, S by 448)
                     const float fscale = (PREC == 2 && row_ok) ? __ldg(in.qs + row) * (1.0f / 448.0f) : 1.0f;
                     uint8_t* op_row = sop_n + (size_t)(row / TK) * B_STRIDE;
-                    // the state of 16 replicas at a time; with 6 stages (one CTA
-                    // per SM, registers to spare) the next chunk's loads are
-                    // issued before this chunk is updated
-                    constexpr bool AHEAD = STAGES == 6;
-                    float sv[16], yv[16];
-                    auto load_chunk = [&](int c, float (&sd)[16], float (&yd)[16]) {
+                    // the state of CW replicas at a time: with 8 epilogue warps
+                    // (each half of the chunks) 8 at a time, the next chunk's
+                    // loads issued before this one is updated; with 4 warps 16
+                    constexpr int CW = EW == 8 ? 8 : 16;
+                    constexpr bool AHEAD = EW == 8;
+                    const int nch = R / CW;
+                    const int c_lo = EW == 8 ? half * ((nch + 1) / 2) : 0;
+                    const int c_hi = EW == 8 ? min(nch, c_lo + (nch + 1) / 2) : nch;
+                    float sv[CW], yv[CW];
+                    auto load_chunk = [&](int c, float (&sd)[CW], float (&yd)[CW]) {
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            const int64_t p = (int64_t)(c * 16 + j) * n + row;
+                        for (int j = 0; j < CW; ++j) {
+                            const int64_t p = (int64_t)(c * CW + j) * n + row;
                             sd[j] = row_ok ? S[p] : 0.0f;
                             yd[j] = row_ok ? Y[p] : 0.0f;
                         }
                     };
-                    if constexpr (AHEAD) load_chunk(0, sv, yv);
-                    for (int c = 0; c < R / 16; ++c) {
-                        uint32_t v[16];
-                        tld16(tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)R + (uint32_t)(c * 16), v);
-                        float sn[16], yn[16];
+                    if constexpr (AHEAD) {
+                        if (c_lo < c_hi) load_chunk(c_lo, sv, yv);
+                    }
+                    for (int c = c_lo; c < c_hi; ++c) {
+                        uint32_t v[CW];
+                        const uint32_t tcol = tmem + ((uint32_t)(q * 32) << 16) + b * (uint32_t)R + (uint32_t)(c * CW);
+                        if constexpr (CW == 8) tld8(tcol, v);
+                        else tld16(tcol, v);
+                        float sn[CW], yn[CW];
                         if constexpr (AHEAD) {
-                            if (c + 1 < R / 16) load_chunk(c + 1, sn, yn);
+                            if (c + 1 < c_hi) load_chunk(c + 1, sn, yn);
                         } else {
                             load_chunk(c, sv, yv);
                         }
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < CW; ++j) {
                             float s = sv[j], y = yv[j];
                             const float F = __uint_as_float(v[j]) * fscale;
                             if constexpr (METHOD == vqd::METHOD_PA) vqd::pa_update(F, bi, lam, a.dt, a.alpha, in.c0, s, y);
                             else if constexpr (METHOD == vqd::METHOD_ASB) vqd::asb_update(F, bi, a_k, a.dt, a.a0, in.c0, s, y);
                             else vqd::bsb_update(F, bi, a_k, a.dt, a.a0, in.c0, s, y);
                             if (row_ok) {
-                                const int r = c * 16 + j;
+                                const int r = c * CW + j;
                                 const int64_t p = (int64_t)r * n + row;
                                 S[p] = s;
                                 Y[p] = y;
@@ -347,7 +371,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                         }
                         if constexpr (AHEAD) {
 #pragma unroll
-                            for (int j = 0; j < 16; ++j) {
+                            for (int j = 0; j < CW; ++j) {
                                 sv[j] = sn[j];
                                 yv[j] = yn[j];
                             }
@@ -362,7 +386,7 @@ __global__ void __launch_bounds__(192, STAGES == 4 ? 2 : 1) k_batch(const BatchA
                 if (k + 1 < a.K) {
                     // the next step's operand must be complete and visible to the bulk copies
                     asm volatile("fence.proxy.async.global;" ::: "memory");
-                    epi_bar();
+                    epi_bar<STAGES>();
                     if (et == 0) mb_arrive(stepr);
                 }
             }
@@ -598,7 +622,8 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
     const size_t smem = batch_smem(stages, terms, RG);
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
-    VQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 192, smem));
+    VQ_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, stages == 6 ? batch_threads<6>() : batch_threads<4>(),
+                                                          smem));
     if (per_sm < 1) return fail(VELOXQ_EUNSUPPORTED, "the batched kernel does not fit an SM");
     std::vector<BatchInst> host((size_t)count);
     std::vector<double> cost((size_t)count);
@@ -758,7 +783,7 @@ int batch_run(veloxq_ctx* const* ctxs, int32_t count, int32_t R, const RunParams
         const unsigned flags = graph ? cudaEventRecordExternal : cudaEventRecordDefault;
         for (const auto& z : zero) VQ_CUDA(cudaMemsetAsync(z.first, 0, z.second, st));
         VQ_CUDA(cudaEventRecordWithFlags(e0, st, flags));
-        fn<<<ctas, 192, smem, st>>>(a);
+        fn<<<ctas, stages == 6 ? batch_threads<6>() : batch_threads<4>(), smem, st>>>(a);
         VQ_LAUNCH_CHECK("batch kernel");
         VQ_CUDA(cudaEventRecordWithFlags(e1, st, flags));
         for (int t = 0; t < 4; ++t) {
