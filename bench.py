@@ -52,8 +52,8 @@ NCU_TRAFFIC = {
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_tc_step", "sk_n8192_bf16"): 435_910_845,    # per step: one 200-step launch, 87.18 GB / 200
-    ("k_batch", "wishart_b128_k50"): 22_553_989_000,
-    ("k_batch", "wishart_b128_k50_fp8"): 12_609_262_000,
+    ("k_batch", "wishart_b512_k20"): 45_369_958_000,
+    ("k_batch", "wishart_b512_k20_fp8"): 29_200_151_000,
     ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
