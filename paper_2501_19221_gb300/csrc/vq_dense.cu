@@ -11,12 +11,30 @@ namespace vq {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 8, TM = 8, TN = 8;   // 256 threads, 8x8 outputs each
+constexpr int BST = 4;   // stages of the Qoff tile when it is copied asynchronously
+
+// 16-byte asynchronous copy global -> shared (cp.async, L2 only); the bytes
+// past `bytes` (0 to 16) are zero-filled
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
 
 // C[r][i] = sum_j S[r][j] Qoff[j][i]. Tiles are zero-filled past the edges.
 // With gridDim.z = ksplit > 1 (small problems: too few output tiles to fill
 // the GPU) block z sums k-tiles [z per, (z+1) per) into part[z][r][i] and
 // k_dense_finish adds the splits in order and applies the update.
-template <bool FIELD_ONLY>
+// ASYNC (rows of Qoff 16-byte aligned, n % 4 == 0): the Qoff tiles come
+// through BST stages of cp.async copies, three tiles ahead, so that their
+// DRAM latency is hidden; the S tiles are staged through registers one tile
+// ahead (they are transposed on the way). The sum of every output is taken
+// in the same order either way.
+template <bool FIELD_ONLY, bool ASYNC>
 __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const float* __restrict__ S_cur,
                                                     const float* __restrict__ Qoff, float* __restrict__ S_nxt,
                                                     float* __restrict__ Y, const float* __restrict__ bf,
@@ -24,7 +42,7 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
                                                     float c0, float* __restrict__ F_out, int method, float alpha,
                                                     int ktile_per, float* __restrict__ part) {
     __shared__ __align__(16) float As[2][BK][BM];
-    __shared__ __align__(16) float Bs[2][BK][BN];
+    __shared__ __align__(16) float Bs[ASYNC ? BST : 2][BK][BN];
     const int tid = threadIdx.x;
     const int tx = tid % 16, ty = tid / 16;
     const int64_t m0 = (int64_t)blockIdx.y * BM, n0 = (int64_t)blockIdx.x * BN;
@@ -58,21 +76,15 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
     const int ktiles = (int)div_up(n, BK);
     const int kt0 = (int)blockIdx.z * ktile_per, kt1 = min(ktiles, kt0 + ktile_per);
     float ra[4], rb[4];
-    if (kt0 < kt1) {
-        load_tiles(kt0, ra, rb);
-        store_tiles(0, ra, rb);
-    }
-    __syncthreads();
-    for (int kt = kt0; kt < kt1; ++kt) {
-        const int cur = (kt - kt0) & 1;
-        if (kt + 1 < kt1) load_tiles(kt + 1, ra, rb);
+    // the 8 k of one tile into acc
+    auto compute = [&](const float (*A)[BM], const float (*Bt)[BN]) {
 #pragma unroll
         for (int kk = 0; kk < BK; ++kk) {
             float av[TM], bv[TN];
-            const float4 a0v = *reinterpret_cast<const float4*>(&As[cur][kk][ty * 4]);
-            const float4 a1v = *reinterpret_cast<const float4*>(&As[cur][kk][64 + ty * 4]);
-            const float4 b0v = *reinterpret_cast<const float4*>(&Bs[cur][kk][tx * 4]);
-            const float4 b1v = *reinterpret_cast<const float4*>(&Bs[cur][kk][64 + tx * 4]);
+            const float4 a0v = *reinterpret_cast<const float4*>(&A[kk][ty * 4]);
+            const float4 a1v = *reinterpret_cast<const float4*>(&A[kk][64 + ty * 4]);
+            const float4 b0v = *reinterpret_cast<const float4*>(&Bt[kk][tx * 4]);
+            const float4 b1v = *reinterpret_cast<const float4*>(&Bt[kk][64 + tx * 4]);
             av[0] = a0v.x; av[1] = a0v.y; av[2] = a0v.z; av[3] = a0v.w;
             av[4] = a1v.x; av[5] = a1v.y; av[6] = a1v.z; av[7] = a1v.w;
             bv[0] = b0v.x; bv[1] = b0v.y; bv[2] = b0v.z; bv[3] = b0v.w;
@@ -82,8 +94,64 @@ __global__ void __launch_bounds__(256) k_dense_step(int32_t R, int32_t n, const 
 #pragma unroll
                 for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
         }
+    };
+    if constexpr (ASYNC) {
+        auto load_a = [&](int kt, float (&r)[4]) {
+            const int64_t gr = m0 + a_row;
+            const int64_t gk = (int64_t)kt * BK + a_k;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                r[q] = (gr < R && gk + q < n) ? vqd::field_operand(method, __ldg(S_cur + gr * n + gk + q)) : 0.0f;
+        };
+        auto store_a = [&](int buf, const float (&r)[4]) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) As[buf][a_k + q][a_row] = r[q];
+        };
+        // this thread's 16 bytes of the Qoff tile kt: row kt BK + b_k, columns n0 + b_col ..
+        auto issue_b = [&](int kt, int st) {
+            const int64_t bk = (int64_t)kt * BK + b_k;
+            const int64_t bc = n0 + b_col;
+            const float* src = Qoff;
+            int bytes = 0;
+            if (bk < n && bc < n) {
+                src = Qoff + bk * n + bc;
+                bytes = (n - bc) >= 4 ? 16 : (int)((n - bc) * 4);
+            }
+            cp_async16(&Bs[st][b_k][b_col], src, bytes);
+        };
+        const int nk = kt1 - kt0;
+#pragma unroll
+        for (int st = 0; st < BST - 1; ++st) {
+            if (st < nk) issue_b(kt0 + st, st);
+            cp_async_commit();
+        }
+        if (nk > 0) {
+            load_a(kt0, ra);
+            store_a(0, ra);
+        }
+        for (int t = 0; t < nk; ++t) {
+            cp_async_wait<BST - 2>();      // this thread's copies of tile t have landed
+            __syncthreads();               // every copy of tile t and its S tile are visible; tile t - 1 is free
+            if (t + BST - 1 < nk) issue_b(kt0 + t + BST - 1, (t + BST - 1) % BST);
+            cp_async_commit();
+            if (t + 1 < nk) load_a(kt0 + t + 1, ra);
+            compute(As[t & 1], Bs[t % BST]);
+            if (t + 1 < nk) store_a((t + 1) & 1, ra);
+        }
+        cp_async_wait<0>();
+    } else {
+    if (kt0 < kt1) {
+        load_tiles(kt0, ra, rb);
+        store_tiles(0, ra, rb);
+    }
+    __syncthreads();
+    for (int kt = kt0; kt < kt1; ++kt) {
+        const int cur = (kt - kt0) & 1;
+        if (kt + 1 < kt1) load_tiles(kt + 1, ra, rb);
+        compute(As[cur], Bs[cur]);
         if (kt + 1 < kt1) store_tiles(cur ^ 1, ra, rb);
         __syncthreads();
+    }
     }
     if (gridDim.z > 1) {   // partial sums of this k-range; the update runs in k_dense_finish
         float* P = part + (int64_t)blockIdx.z * R * n;
@@ -243,9 +311,16 @@ int launch_dense_step(veloxq_ctx* ctx, int32_t R, const float* S_cur, float* S_n
         part = ctx->dpart.as<float>();
     }
     dim3 g((unsigned)div_up(n, BN), (unsigned)div_up(R, BM), (unsigned)ksplit);
-    k_dense_step<FIELD_ONLY><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
-                                                         ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out,
-                                                         rule.method, rule.alpha, per, part);
+    // cp.async needs 16-byte aligned rows of Qoff
+    const bool async_b = n % 4 == 0 && (reinterpret_cast<uintptr_t>(ctx->qoff32.p) & 15) == 0;
+    if (async_b)
+        k_dense_step<FIELD_ONLY, true><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
+                                                                   ctx->bf.as<float>(), a_table, k, dt, a0, c0,
+                                                                   F_out, rule.method, rule.alpha, per, part);
+    else
+        k_dense_step<FIELD_ONLY, false><<<g, 256, 0, ctx->stream>>>(R, n, S_cur, ctx->qoff32.as<float>(), S_nxt, Y,
+                                                                    ctx->bf.as<float>(), a_table, k, dt, a0, c0,
+                                                                    F_out, rule.method, rule.alpha, per, part);
     if (ksplit > 1)
         k_dense_finish<FIELD_ONLY><<<(unsigned)div_up((int64_t)R * n, 256), 256, 0, ctx->stream>>>(
             R, n, ksplit, part, S_cur, S_nxt, Y, ctx->bf.as<float>(), a_table, k, dt, a0, c0, F_out, rule.method,
