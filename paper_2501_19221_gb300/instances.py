@@ -23,6 +23,8 @@ Families (each cites the passage whose shape it imitates):
   the D-Wave Pegasus P_m and Zephyr Z_{m,t} topologies (Sec. "Pegasus
   topology", Sec. "Zephyr topology") with random QUBO couplings on their
   edges.
+* ``tile_planted_ising`` -- tile-planted periodic square lattice with a known
+  ground state (Sec. "Tile planting").
 
 Sparse instances are returned as symmetric CSR (both (i, j) and (j, i) are
 stored, column indices strictly increasing within each row, no diagonal).
@@ -49,6 +51,7 @@ __all__ = [
     "pegasus_qubo",
     "zephyr_csr",
     "zephyr_qubo",
+    "tile_planted_ising",
 ]
 
 
@@ -554,3 +557,76 @@ def zephyr_qubo(m: int, t: int = 4, seed: int = 0) -> SparseCoupling:
         val[p0:p1] = 0.5 * _pair_uniform(np.minimum(rows, c64), np.maximum(rows, c64), n, seed)
     lin = np.random.default_rng(seed + 1).uniform(-1.0, 1.0, size=n)
     return SparseCoupling(n, rowptr, col, val, lin)
+
+
+# ----------------------------------------------------------------------------- tile planting
+# Coupling values of the four tile classes, in the convention of Sec. "Tile
+# planting" (H_C = -sum over the tile's four edges of J_ij s_i s_j, target
+# ground state all +1). The paper defines class C_i only by its ground-state
+# count: i ground states, up to the global flip, one of them all +1. Here each
+# tile is a frustrated square (one antiferromagnetic bond, J = -1) whose other
+# bonds are ferromagnetic, i - 1 of them with J = +1 and 4 - i with J = +2.
+# A frustrated square violates an odd number of bonds in every state, so its
+# ground states are those that violate exactly one of its weakest bonds: i of
+# them up to the flip, all +1 (which violates the -1 bond) among them, at
+# energy -(sum |J|) + 2 = i - 6.
+TILE_CLASS_J = {1: (-1, 2, 2, 2), 2: (-1, 1, 2, 2), 3: (-1, 1, 1, 2), 4: (-1, 1, 1, 1)}
+
+
+class TilePlanted:
+    """A tile-planted square-lattice Ising instance: the couplings in the
+    library's Ising convention (sp), the planted ground state, its energy and
+    the class of every tile."""
+
+    def __init__(self, sp, s_planted, E0, tile_class, L):
+        self.sp = sp                  # SparseCoupling, H(s) = sum_{i<j} J_ij s_i s_j (h = 0)
+        self.s_planted = s_planted    # [n] int8, +-1: a ground state
+        self.x_planted = ((s_planted.astype(np.int16) + 1) // 2).astype(np.uint8)
+        self.E0 = E0                  # ground energy of H (sum of the tiles' minima)
+        self.tile_class = tile_class  # [L*L/2] int8, the class 1..4 of tile t
+        self.L = L
+
+
+def tile_plaquettes(L: int) -> np.ndarray:
+    """The tiles of the periodic L x L square lattice (L even): the plaquettes
+    of one colour of the checkerboard, those with lower-left corner (x, y) and
+    x + y even. Returns [L*L/2][4][2] site indices of the tile's four edges in
+    the order bottom, right, top, left; site (x, y) is y*L + x. Every lattice
+    edge lies in exactly one tile and every site in two."""
+    ys, xs = np.divmod(np.arange(L * L, dtype=np.int64), L)
+    keep = (xs + ys) % 2 == 0
+    x, y = xs[keep], ys[keep]
+    x1, y1 = (x + 1) % L, (y + 1) % L
+    a, b, c, d = y * L + x, y * L + x1, y1 * L + x1, y1 * L + x   # corners counter-clockwise
+    return np.stack([np.stack([a, b], 1), np.stack([b, c], 1), np.stack([d, c], 1), np.stack([a, d], 1)], 1)
+
+
+def tile_planted_ising(L: int, p=(0.0, 0.2, 0.0, 0.8), seed: int = 0, gauge: bool = True) -> TilePlanted:
+    """Tile-planted instance on the periodic L x L square lattice (Sec. "Tile
+    planting"): every tile of the checkerboard draws its class C_i with
+    probability p[i-1] and its four coupling values (TILE_CLASS_J) in a random
+    order over its four edges. All tiles then share the ground state all +1,
+    so the lattice does too, with energy sum_tiles (i - 6). With gauge, a
+    random s* in {+-1}^n hides it: J_ij -> s*_i s*_j J_ij, ground state s*.
+    The paper's benchmark draws p = (0, p2, 0, 1 - p2), p2 = 0.2 (easy) or 0.8
+    (hard), L in [10, 300]. The couplings are returned in the library's Ising
+    convention, H(s) = sum_{i<j} J_ij s_i s_j (that is, -J of the tile
+    Hamiltonian), as int8 CSR with h = 0."""
+    if L < 4 or L % 2:
+        raise ValueError("tile planting needs an even L >= 4 (a periodic checkerboard with distinct neighbours)")
+    p = np.asarray(p, dtype=np.float64)
+    if p.shape != (4,) or np.any(p < 0) or abs(p.sum() - 1.0) > 1e-12:
+        raise ValueError("p must be four probabilities summing to 1")
+    rng = np.random.default_rng(seed)
+    n = L * L
+    tiles = tile_plaquettes(L)
+    cls = (rng.choice(4, size=tiles.shape[0], p=p) + 1).astype(np.int8)
+    table = np.array([TILE_CLASS_J[i] for i in range(1, 5)], dtype=np.int8)
+    J = rng.permuted(table[cls - 1], axis=1)           # tile-convention couplings, per edge of each tile
+    s = (2 * rng.integers(0, 2, size=n) - 1).astype(np.int8) if gauge else np.ones(n, dtype=np.int8)
+    u, v = tiles[:, :, 0].reshape(-1), tiles[:, :, 1].reshape(-1)
+    Jg = (J.reshape(-1) * s[u] * s[v]).astype(np.int8)
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    rowptr, col, val = _csr_from_edges(n, lo, hi, (-Jg).astype(np.int8))
+    E0 = float(np.sum(cls.astype(np.int64) - 6))
+    return TilePlanted(SparseCoupling(n, rowptr, col, val, np.zeros(n, dtype=np.float64)), s, E0, cls, L)

@@ -44,7 +44,8 @@ def test_tts99_formula():
 
 
 @pytest.mark.parametrize("name", ["dense_n20", "chimera_c16", "sk_n8192_fp8", "wishart_b128_k50",
-                                  "pegasus_p16", "zephyr_z12", "xorsat_3r3x_1e5"])
+                                  "pegasus_p16", "zephyr_z12", "xorsat_3r3x_1e5",
+                                  "tile_planting_l300"])
 def test_workload_recipes(name):
     """Each workload states its sizes, replicas and steps consistently with
     the instance it builds."""
@@ -56,6 +57,8 @@ def test_workload_recipes(name):
         assert w["sp"].n == w["n"] and w["sp"].rowptr.shape[0] == w["n"] + 1
     if w["kind"] == "batch":
         assert w["n"] == int(np.sum(w["sizes"])) and len(w["sizes"]) == 128
+    if "E0_ising" in w:
+        assert w["n"] == 300 * 300 and w["E0_ising"] < 0
 
 
 def test_oracle_samples_of_the_largest_workloads_are_bounded():
