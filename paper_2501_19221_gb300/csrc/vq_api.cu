@@ -35,11 +35,107 @@ int cuda_fail(cudaError_t e, const char* what) {
     return VELOXQ_ECUDA;
 }
 
+// ---------------------------------------------------------------------------
+// Cache of released device blocks. Creating a context, solving on it and
+// destroying it allocates and frees some twenty buffers; cudaMalloc and
+// cudaFree of large blocks cost 0.1-0.35 ms each (page mapping), as much as a
+// short solve. Released blocks are kept per device, up to a bounded total, and
+// handed to the next request they fit (at most 1/4 + 64 KiB larger). A block
+// enters the cache only after the device has finished all work issued so far
+// (the wait cudaFree would do), so a later owner never races a kernel of the
+// previous one. When an allocation fails, the device's cached blocks are freed
+// and the allocation is tried once more.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t kCacheMaxBytes = size_t(8) << 30;     // per device
+
+struct BlockCache {
+    std::mutex mu;
+    std::map<int, std::multimap<size_t, void*>> free_blocks;   // device -> size -> block
+    std::map<int, size_t> cached;                             // device -> bytes held
+};
+
+BlockCache& block_cache() {
+    static BlockCache* c = new BlockCache();   // never destroyed: blocks go with the process
+    return *c;
+}
+
+bool cache_enabled() {
+    static const bool on = [] {
+        const char* v = std::getenv("VELOXQ_ALLOC_CACHE");
+        return !(v && v[0] == '0');
+    }();
+    return on;
+}
+
+void* cache_take(int dev, size_t b, size_t* got) {
+    if (!cache_enabled()) return nullptr;
+    BlockCache& c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto& m = c.free_blocks[dev];
+    auto it = m.lower_bound(b);
+    if (it == m.end() || it->first > b + b / 4 + (size_t(64) << 10)) return nullptr;
+    void* p = it->second;
+    *got = it->first;
+    c.cached[dev] -= it->first;
+    m.erase(it);
+    return p;
+}
+
+void cache_trim(int dev) {
+    BlockCache& c = block_cache();
+    std::vector<void*> out;
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        for (auto& kv : c.free_blocks[dev]) out.push_back(kv.second);
+        c.free_blocks[dev].clear();
+        c.cached[dev] = 0;
+    }
+    for (void* q : out) cudaFree(q);
+}
+}  // namespace
+
+void DevBuf::release() {
+    if (!p) return;
+    bool kept = false;
+    int cur = -1;
+    if (cache_enabled() && cudaGetDevice(&cur) == cudaSuccess && cur == dev &&
+        cudaDeviceSynchronize() == cudaSuccess) {
+        BlockCache& c = block_cache();
+        std::lock_guard<std::mutex> lk(c.mu);
+        if (c.cached[dev] + bytes <= kCacheMaxBytes) {
+            c.free_blocks[dev].emplace(bytes, p);
+            c.cached[dev] += bytes;
+            kept = true;
+        }
+    }
+    if (!kept) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+    dev = -1;
+}
+
 int DevBuf::ensure(size_t b) {
     if (b <= bytes && p) return VELOXQ_OK;
     release();
     if (b == 0) b = 16;
-    cudaError_t e = cudaMalloc(&p, b);
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e == cudaSuccess) {
+        size_t got = 0;
+        if (void* q = cache_take(d, b, &got)) {
+            p = q;
+            bytes = got;
+            dev = d;
+            return VELOXQ_OK;
+        }
+        e = cudaMalloc(&p, b);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            cache_trim(d);
+            e = cudaMalloc(&p, b);
+        }
+    }
     if (e != cudaSuccess) {
         p = nullptr;
         bytes = 0;
@@ -48,6 +144,7 @@ int DevBuf::ensure(size_t b) {
                     std::string("device allocation of ") + std::to_string(b) + " bytes failed: " + cudaGetErrorString(e));
     }
     bytes = b;
+    dev = d;
     return VELOXQ_OK;
 }
 

@@ -38,16 +38,19 @@ int cuda_fail(cudaError_t e, const char* what);
         if (_e != cudaSuccess) return ::vq::cuda_fail(_e, what);        \
     } while (0)
 
-// Device buffer owned by a context.
+// Device buffer owned by a context (or by one call, for temporaries). Its
+// memory comes from a per-device cache of released blocks when one of a
+// fitting size is there, else from cudaMalloc; release() waits for the device
+// like cudaFree and returns the block to that cache (vq_api.cu).
 struct DevBuf {
     void* p = nullptr;
     size_t bytes = 0;
+    int dev = -1;               // device the block belongs to
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
     ~DevBuf() { release(); }
-    void release() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        bytes = 0;
-    }
+    void release();
     // grow to at least `b` bytes (contents not kept)
     int ensure(size_t b);
     template <typename T> T* as() const { return static_cast<T*>(p); }
