@@ -258,8 +258,8 @@ static std::vector<int32_t> chunk_candidates(int64_t n, int32_t R) {
 }
 
 // Pick the gather variant (one, four or six couplings at a time) and the
-// replica chunk width of the streaming kernels for R replicas by timing three
-// steps of each pair on the caller's buffers (contents are overwritten);
+// replica chunk width of the streaming kernels for R replicas by timing steps
+// of each pair on the caller's buffers (contents are overwritten);
 // VELOXQ_STREAM_FORM fixes them instead.
 // Runs eagerly on ctx->stream; must not be called during stream capture.
 int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y) {
@@ -285,33 +285,47 @@ int stream_autotune(veloxq_ctx* ctx, int32_t R, float* S_a, float* S_b, float* Y
     cudaEvent_t e0, e1;
     VQ_CUDA(cudaEventCreate(&e0));
     VQ_CUDA(cudaEventCreate(&e1));
-    float best = 1e30f;
-    int pick = 1;
-    int32_t pick_cv = 0;
     VQ_TRY(launch_init_state(ctx, R, 1, 0.1f, LAYOUT_NR, S_a, Y));
     const float* at = ctx->a_table.as<float>();
+    std::vector<std::pair<int, int32_t>> cands;   // (gather, chunk)
     for (int32_t cv : chunk_candidates(ctx->n, R))
-        for (int u : {1, 4, 6}) {
-            if (u == 6 && ctx->uniform_deg != 6) continue;
-            ctx->stream_unroll = u;
-            ctx->stream_cvec = cv;
-            VQ_TRY((launch_step<false, false>(ctx, R, S_a, S_b, Y, Y, at, 0, 0.5f, 1.0f, 0.1f, nullptr, Rule())));   // warm
-            VQ_CUDA(cudaEventRecord(e0, ctx->stream));
-            for (int k = 0; k < 3; ++k)
-                VQ_TRY((launch_step<false, false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f,
-                                                  1.0f, 0.1f, nullptr, Rule())));
-            VQ_CUDA(cudaEventRecord(e1, ctx->stream));
-            VQ_CUDA(cudaEventSynchronize(e1));
+        for (int u : {1, 4, 6})
+            if (u != 6 || ctx->uniform_deg == 6) cands.emplace_back(u, cv);
+    auto timed = [&](int reps, float* ms) -> int {
+        VQ_CUDA(cudaEventRecord(e0, ctx->stream));
+        for (int k = 0; k < reps; ++k)
+            VQ_TRY((launch_step<false, false>(ctx, R, (k & 1) ? S_b : S_a, (k & 1) ? S_a : S_b, Y, Y, at, 0, 0.5f,
+                                              1.0f, 0.1f, nullptr, Rule())));
+        VQ_CUDA(cudaEventRecord(e1, ctx->stream));
+        VQ_CUDA(cudaEventSynchronize(e1));
+        VQ_CUDA(cudaEventElapsedTime(ms, e0, e1));
+        return VELOXQ_OK;
+    };
+    // Two rounds over all candidates, each timing `reps` steps of one form
+    // (10 when a step is shorter than 0.3 ms, else 3); a form's time is its
+    // faster round, so a round disturbed by the previous form's state in L2
+    // or by a clock change does not decide the pick.
+    std::vector<float> per_step(cands.size(), 1e30f);
+    int reps = 3;
+    for (int round = 0; round < 2; ++round)
+        for (size_t c = 0; c < cands.size(); ++c) {
+            ctx->stream_unroll = cands[c].first;
+            ctx->stream_cvec = cands[c].second;
             float ms = 0.f;
-            VQ_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) {
-                best = ms;
-                pick = u;
-                pick_cv = cv;
+            if (round == 0) {
+                VQ_TRY(timed(1, &ms));                 // warm; the first form's step sets the step count
+                if (c == 0 && ms < 0.3f) reps = 10;
             }
+            VQ_TRY(timed(reps, &ms));
+            per_step[c] = std::min(per_step[c], ms / (float)reps);
         }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    size_t bi = 0;
+    for (size_t c = 1; c < cands.size(); ++c)
+        if (per_step[c] < per_step[bi]) bi = c;
+    const int pick = cands[bi].first;
+    const int32_t pick_cv = cands[bi].second;
     ctx->stream_unroll = pick;
     ctx->stream_cvec = pick_cv;
     ctx->stream_tuned_R = R;
