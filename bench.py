@@ -50,6 +50,7 @@ NCU_TRAFFIC = {
     ("k_stream_step", "lattice_l100"): 4_104_791_000,
     ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
+    ("k_stream_step", "tile_planting_l300"): 314_659_499,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_tc_step", "sk_n8192_bf16"): 435_910_845,    # per step: one 200-step launch, 87.18 GB / 200
     ("k_batch", "wishart_b512_k20"): 45_369_958_000,
