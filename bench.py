@@ -51,11 +51,11 @@ NCU_TRAFFIC = {
     ("k_stream_step", "hubo_chain_1e7"): 3_555_804_000,
     ("k_stream_step", "xorsat_3r3x_1e5"): 846_672_128,
     ("k_stream_step", "tile_planting_l300"): 314_659_499,
+    ("k_adj_a+k_adj_b", "grad_l100"): 9_577_706_240,
     ("k_tc_step", "sk_n8192_fp8"): 291_477_740,     # per step: one 200-step launch, 58.30 GB / 200
     ("k_tc_step", "sk_n8192_bf16"): 435_910_845,    # per step: one 200-step launch, 87.18 GB / 200
     ("k_batch", "wishart_b512_k20"): 45_369_958_000,
     ("k_batch", "wishart_b512_k20_fp8"): 29_200_151_000,
-    ("k_adj_a+k_adj_b", "grad_l100"): 10_720_588_000,
 }
 SMEM_BYTES_PER_CLK_PER_SM = 128     # 32 banks x 4 bytes
 FP32_LANES_PER_SM = 128
@@ -528,10 +528,11 @@ def roofline(B, w, runner, path, main_ms, main_launches):
                 "frac": ach / peaks["hbm_gbs"], "traffic": None, "peak_source": f"{src} hbm_gbs",
                 "algorithmic_bytes_per_launch": hbm, "ms_per_launch": main_ms}
     if runner.grad:
-        # one reverse step: k_adj_a reads s_k, y_k, lam_s, lam_y and writes g_phi, the local g_s and lam_y
-        # (28 B per variable-replica); k_adj_b reads the local g_s and g_phi (gathered, from L2 after one
-        # DRAM read) and writes lam_s (12 B); each gathers through the int8 couplings and columns once
-        hbm_bytes = 40 * n * R + 2 * 5 * runner.nnz_field
+        # one reverse step: k_adj_a reads s_k, y_k, lam_s, lam_y and writes the local g_s and lam_y (24 B per
+        # variable-replica); k_adj_b reads the local g_s and the new lam_y (gathered, from L2 after one DRAM
+        # read; g_phi = dt c0 lam_y is formed on the fly) and writes lam_s (12 B); each gathers through the
+        # int8 couplings and columns once
+        hbm_bytes = 36 * n * R + 2 * 5 * runner.nnz_field
         per = main_ms / K
         ach = hbm_bytes / (per / 1e3) / 1e9
         return {"kernel": "k_adj_a+k_adj_b", "bound": "hbm", "achieved": ach, "peak": peaks["hbm_gbs"],

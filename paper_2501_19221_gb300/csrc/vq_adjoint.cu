@@ -80,15 +80,17 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_loss(int64_t n, int32_t R, 
 }
 
 // Reverse of one step, elementwise part (F of s_k recomputed in the forward
-// order). Writes g_phi and the local part of g_s; replaces lam_y by g_y;
-// per-block partial sums of (dL/ddt, dL/dc0, dL/da_k).
+// order). Writes the local part of g_s and replaces lam_y by g_y (= g_yh);
+// g_phi = dt c0 g_yh is not stored: k_adj_b forms it from the new lam_y
+// with the same product, which saves one state array of writes and reads
+// per step. Per-block partial sums of (dL/ddt, dL/dc0, dL/da_k).
 template <int V, typename WT, int UNROLL>
 __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col, const WT* __restrict__ w,
                                                        float wscale, const float* __restrict__ Sk,
                                                        const float* __restrict__ Yk, const float* __restrict__ bf,
                                                        float a_k, float dt, float a0, float c0,
-                                                       const float* __restrict__ lam_s, float* lam_y, float* gphi,
+                                                       const float* __restrict__ lam_s, float* lam_y,
                                                        float* gsl, double* parts3, int udeg) {
     __shared__ double sh[3 * kAdjThreads];
     double acc3[3] = {0.0, 0.0, 0.0};
@@ -99,7 +101,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
         vqd::split_index(t, n, nvec, i, vi);
         const int64_t off = (int64_t)vi * V;
         const int64_t me = i * R + off;
-        float acc[V], s[V], y[V], ls[V], ly[V], gp[V], gs[V], gy[V];
+        float acc[V], s[V], y[V], ls[V], ly[V], gs[V], gy[V];
         vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, Sk, R, off, i, acc, udeg);
         vqd::vload<V>(Sk + me, s);
         vqd::vload<V>(Yk + me, y);
@@ -118,13 +120,11 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
             ddt += a0 * o.yh * g_sh;
             gy[l] = g_yh;
             g_s += -dt * (a0 - a_k) * g_yh;
-            gp[l] = dt * c0 * g_yh;
             ddt += o.drive * g_yh;
             da += dt * s[l] * g_yh;
             dc0 += dt * o.phi * g_yh;
             gs[l] = g_s;
         }
-        vqd::vstore<V>(gphi + me, gp);
         vqd::vstore<V>(gsl + me, gs);
         vqd::vstore<V>(lam_y + me, gy);
         acc3[0] += ddt;
@@ -139,11 +139,16 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_a(int64_t n, int32_t R, int
     }
 }
 
-// lam_s = g_s(local) - Qoff g_phi / 2.
+// lam_s = g_s(local) - Qoff g_phi / 2, with g_phi_j = dt c0 g_y_j formed
+// from the gathered g_y (the new lam_y) as k_adj_a would have formed it.
+// The six-at-once gather of lattices fits 32 registers, eight blocks per SM
+// (0.54 against 0.65 ms at 34 registers and seven blocks, lattice L = 100,
+// 256 replicas); the four-at-a-time forms would spill there and keep their
+// own count.
 template <int V, typename WT, int UNROLL>
-__global__ void __launch_bounds__(kAdjThreads) k_adj_b(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
+__global__ void __launch_bounds__(kAdjThreads, UNROLL == 6 ? 8 : 1) k_adj_b(int64_t n, int32_t R, int32_t nvec, const int64_t* __restrict__ rp,
                                                        const int32_t* __restrict__ col, const WT* __restrict__ w,
-                                                       float wscale, const float* __restrict__ gphi,
+                                                       float wscale, const float* __restrict__ gy, float dt, float c0,
                                                        const float* __restrict__ gsl, float* lam_s, int udeg) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n * nvec) return;
@@ -153,7 +158,7 @@ __global__ void __launch_bounds__(kAdjThreads) k_adj_b(int64_t n, int32_t R, int
     const int64_t off = (int64_t)vi * V;
     const int64_t me = i * R + off;
     float acc[V], g[V];
-    vqd::csr_row_dot<V, WT, UNROLL>(rp, col, w, gphi, R, off, i, acc, udeg);
+    vqd::csr_row_dot<V, WT, UNROLL, false, true>(rp, col, w, gy, R, off, i, acc, udeg, dt * c0);
     vqd::vload<V>(gsl + me, g);
 #pragma unroll
     for (int l = 0; l < V; ++l) g[l] = g[l] - 0.5f * (acc[l] * wscale);
@@ -215,16 +220,17 @@ struct AdjLaunch {
                                                                          c->bf.as<float>(), ls, ly, parts, c->uniform_deg);
     }
     static void a(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* Sk, const float* Yk, float a_k, float dt,
-                  float a0, float c0, const float* ls, float* ly, float* gp, float* gs, double* parts3) {
+                  float a0, float c0, const float* ls, float* ly, float* gs, double* parts3) {
         k_adj_a<V, WT, U><<<kAdjBlocks, kAdjThreads, 0, c->stream>>>(c->n, R, R / V, c->rowptr.as<int64_t>(),
                                                                       c->col.as<int32_t>(), w, ws, Sk, Yk,
-                                                                      c->bf.as<float>(), a_k, dt, a0, c0, ls, ly, gp,
-                                                                      gs, parts3, c->uniform_deg);
+                                                                      c->bf.as<float>(), a_k, dt, a0, c0, ls, ly, gs,
+                                                                      parts3, c->uniform_deg);
     }
-    static void b(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* gp, const float* gs, float* ls) {
+    static void b(veloxq_ctx* c, int32_t R, const WT* w, float ws, const float* gy, float dt, float c0, const float* gs,
+                  float* ls) {
         const int64_t total = c->n * (int64_t)(R / V);
         k_adj_b<V, WT, U><<<(unsigned)div_up(total, kAdjThreads), kAdjThreads, 0, c->stream>>>(
-            c->n, R, R / V, c->rowptr.as<int64_t>(), c->col.as<int32_t>(), w, ws, gp, gs, ls, c->uniform_deg);
+            c->n, R, R / V, c->rowptr.as<int64_t>(), c->col.as<int32_t>(), w, ws, gy, dt, c0, gs, ls, c->uniform_deg);
     }
 };
 
@@ -237,13 +243,13 @@ void adj_loss_v(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const fl
 }
 template <typename WT, int U>
 void adj_step_v(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const float* Sk, const float* Yk, float a_k,
-                float dt, float a0, float c0, float* ls, float* ly, float* gp, float* gs, double* parts3) {
-    if (V == 4) AdjLaunch<4, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
-    else if (V == 2) AdjLaunch<2, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
-    else AdjLaunch<1, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
-    if (V == 4) AdjLaunch<4, WT, U>::b(c, R, w, ws, gp, gs, ls);
-    else if (V == 2) AdjLaunch<2, WT, U>::b(c, R, w, ws, gp, gs, ls);
-    else AdjLaunch<1, WT, U>::b(c, R, w, ws, gp, gs, ls);
+                float dt, float a0, float c0, float* ls, float* ly, float* gs, double* parts3) {
+    if (V == 4) AdjLaunch<4, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
+    else if (V == 2) AdjLaunch<2, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
+    else AdjLaunch<1, WT, U>::a(c, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
+    if (V == 4) AdjLaunch<4, WT, U>::b(c, R, w, ws, ly, dt, c0, gs, ls);
+    else if (V == 2) AdjLaunch<2, WT, U>::b(c, R, w, ws, ly, dt, c0, gs, ls);
+    else AdjLaunch<1, WT, U>::b(c, R, w, ws, ly, dt, c0, gs, ls);
 }
 
 template <typename WT>
@@ -257,11 +263,11 @@ int adj_dispatch_loss(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, co
 }
 template <typename WT>
 int adj_dispatch_step(veloxq_ctx* c, int V, int32_t R, const WT* w, float ws, const float* Sk, const float* Yk, float a_k,
-                      float dt, float a0, float c0, float* ls, float* ly, float* gp, float* gs, double* parts3) {
+                      float dt, float a0, float c0, float* ls, float* ly, float* gs, double* parts3) {
     if (c->stream_unroll == 6 && c->uniform_deg == 6)
-        adj_step_v<WT, 6>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
-    else if (c->stream_unroll == 4) adj_step_v<WT, 4>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
-    else adj_step_v<WT, 1>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gp, gs, parts3);
+        adj_step_v<WT, 6>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
+    else if (c->stream_unroll == 4) adj_step_v<WT, 4>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
+    else adj_step_v<WT, 1>(c, V, R, w, ws, Sk, Yk, a_k, dt, a0, c0, ls, ly, gs, parts3);
     VQ_LAUNCH_CHECK("adjoint step");
     return VELOXQ_OK;
 }
@@ -277,11 +283,11 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
     const int M = (int)div_up(K, C);                  // checkpoints: states before steps 0, C, 2C, ...
     const int V = vec_width(R);
     const size_t blk = sizeof(float) * (size_t)nR;
-    // checkpoints (S, Y) x M, segment states (S, Y) x C, 4 adjoint blocks
+    // checkpoints (S, Y) x M, segment states (S, Y) x C, 3 adjoint blocks
     DevBuf ck, seg, adj, red;
     VQ_TRY(ck.ensure(2 * blk * (size_t)M));
     VQ_TRY(seg.ensure(2 * blk * (size_t)(C + 1)));
-    VQ_TRY(adj.ensure(4 * blk));
+    VQ_TRY(adj.ensure(3 * blk));
     VQ_TRY(red.ensure(sizeof(double) * (size_t)(3 * kAdjBlocks + kAdjBlocks + 2 + K + 8 + n_knots)));
     auto ckS = [&](int m) { return ck.as<float>() + (size_t)(2 * m) * nR; };
     auto ckY = [&](int m) { return ck.as<float>() + (size_t)(2 * m + 1) * nR; };
@@ -289,8 +295,7 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
     auto sgY = [&](int t) { return seg.as<float>() + (size_t)(2 * t + 1) * nR; };
     float* lam_s = adj.as<float>();
     float* lam_y = lam_s + nR;
-    float* gphi = lam_y + nR;
-    float* gsl = gphi + nR;
+    float* gsl = lam_y + nR;
     double* parts3 = red.as<double>();
     double* parts = parts3 + 3 * kAdjBlocks;
     double* acc = parts + kAdjBlocks;                  // [0] ddt [1] dc0 [2..2+K) da_k
@@ -346,10 +351,10 @@ int adjoint_run(veloxq_ctx* ctx, int32_t R, const RunParams& p, const std::vecto
             const int t = k - k0;
             if (ctx->w8.p)
                 VQ_TRY(adj_dispatch_step<int8_t>(ctx, V, R, ctx->w8.as<int8_t>(), 0.5f, sgS(t), sgY(t), a_host[k], p.dt,
-                                                 p.a0, p.c0, lam_s, lam_y, gphi, gsl, parts3));
+                                                 p.a0, p.c0, lam_s, lam_y, gsl, parts3));
             else
                 VQ_TRY(adj_dispatch_step<float>(ctx, V, R, ctx->wf.as<float>(), 1.0f, sgS(t), sgY(t), a_host[k], p.dt,
-                                                p.a0, p.c0, lam_s, lam_y, gphi, gsl, parts3));
+                                                p.a0, p.c0, lam_s, lam_y, gsl, parts3));
             k_adj_reduce<<<1, kAdjThreads, 0, st>>>(parts3, kAdjBlocks, k, acc);
             VQ_LAUNCH_CHECK("adjoint reduce");
         }

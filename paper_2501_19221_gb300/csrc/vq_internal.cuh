@@ -476,16 +476,21 @@ __device__ __forceinline__ float wval(int8_t w) { return (float)w; }
 // couplings per round so that their gathers are in flight together (a slot
 // past the row end reads row i itself with weight 0 and adds an exact 0);
 // UNROLL = 1 is the plain loop. Both give the same sums.
-// acc = sum over row i of w_ij o(X_j) for V replicas, o the identity or (SIGN)
-// PA's binarised spin.
+// acc = sum over row i of w_ij o(X_j) for V replicas, o the identity, (SIGN)
+// PA's binarised spin or (SCALE) the product xs X_j, each rounded before it
+// enters the sum.
 template <int V> __device__ __forceinline__ void sign_vec(float (&v)[V]) {
 #pragma unroll
     for (int l = 0; l < V; ++l) v[l] = pa_sign(v[l]);
 }
-template <int V, typename WT, int UNROLL, bool SIGN = false>
+template <int V> __device__ __forceinline__ void scale_vec(float (&v)[V], float xs) {
+#pragma unroll
+    for (int l = 0; l < V; ++l) v[l] = xs * v[l];
+}
+template <int V, typename WT, int UNROLL, bool SIGN = false, bool SCALE = false>
 __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
                                             const WT* __restrict__ w, const float* X, int32_t R, int64_t off,
-                                            int64_t i, float (&acc)[V], int udeg = -1) {
+                                            int64_t i, float (&acc)[V], int udeg = -1, float xs = 1.0f) {
 #pragma unroll
     for (int l = 0; l < V; ++l) acc[l] = 0.0f;
     if constexpr (UNROLL == 6) {
@@ -507,6 +512,10 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
 #pragma unroll
             for (int u = 0; u < 6; ++u) sign_vec<V>(sj[u]);
         }
+        if constexpr (SCALE) {
+#pragma unroll
+            for (int u = 0; u < 6; ++u) scale_vec<V>(sj[u], xs);
+        }
 #pragma unroll
         for (int u = 0; u < 6; ++u)
 #pragma unroll
@@ -523,6 +532,7 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
             float sj[V];
             vload<V>(X + j * R + off, sj);
             if constexpr (SIGN) sign_vec<V>(sj);
+            if constexpr (SCALE) scale_vec<V>(sj, xs);
 #pragma unroll
             for (int l = 0; l < V; ++l) acc[l] = fmaf(wv, sj[l], acc[l]);
         }
@@ -542,6 +552,10 @@ __device__ __forceinline__ void csr_row_dot(const int64_t* __restrict__ rp, cons
         if constexpr (SIGN) {
 #pragma unroll
             for (int u = 0; u < 4; ++u) sign_vec<V>(sj[u]);
+        }
+        if constexpr (SCALE) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) scale_vec<V>(sj[u], xs);
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u)
