@@ -35,6 +35,13 @@
  *  - A context owns every device buffer it allocates; veloxq_destroy frees
  *    them. A context is not thread-safe; different contexts are independent
  *    (they may be created, used and destroyed from different threads at once).
+ *  - Freed device buffers (of contexts and of a call's temporaries) go to a
+ *    cache of the library, after the device has finished the work issued so
+ *    far, and later buffers of the same device reuse them: up to 8 GiB per
+ *    device stays allocated for the process's lifetime. An allocation that
+ *    fails frees that device's cache and is tried once more. Setting the
+ *    environment variable VELOXQ_ALLOC_CACHE=0 before the first call sends
+ *    every freed buffer back to cudaFree instead.
  *  - A context lives on the device that was current when it was created;
  *    every later call on it needs that device current (EINVAL otherwise).
  */
