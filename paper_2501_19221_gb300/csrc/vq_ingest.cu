@@ -966,6 +966,10 @@ int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
     const int64_t grid_cap = (int64_t)device_sms(ctx->device) * (2048 / kPiBlock);
     const unsigned grid = (unsigned)std::max<int64_t>(
         1, std::min<int64_t>(ctx->dense ? div_up(n, kPiBlock / 32) : div_up(n, kPiBlock), grid_cap));
+    // the vector update touches n elements: one thread each, no more blocks
+    // (a dense matrix pass has a warp per row, 32 times as many threads,
+    // and a block count that large only lengthens the update's reduction)
+    const unsigned ugrid = (unsigned)std::min<int64_t>(grid, std::max<int64_t>(1, div_up(n, kPiBlock)));
     const int m = (int)std::min<int64_t>(kLzSteps, n);
     DevBuf buf;
     const size_t vbytes = (sizeof(float) * (size_t)(3 * n) + 15) & ~size_t(15);
@@ -986,7 +990,7 @@ int power_iteration(veloxq_ctx* ctx, int iters, double* rho) {
         else
             k_lz_spmv<<<grid, kPiBlock, 0, st>>>(n, ctx->rowptr.as<int64_t>(), ctx->col.as<int32_t>(),
                                                  ctx->wf.as<float>(), wj, u, sc, j);
-        if (j + 1 < m) k_lz_update<<<grid, kPiBlock, 0, st>>>(n, u, wj, wv[(j + 2) % 3], sc, j);
+        if (j + 1 < m) k_lz_update<<<ugrid, kPiBlock, 0, st>>>(n, u, wj, wv[(j + 2) % 3], sc, j);
     }
     VQ_LAUNCH_CHECK("Lanczos");
     std::vector<double> al((size_t)m), n2((size_t)m);
