@@ -10,13 +10,13 @@ namespace {
 
 using namespace resident;
 
-KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, int ell, int method) {
+KFn pick_kernel(int rc, int rpt, bool csr_smem, bool packed, int ell, int threads, int method) {
 #define VQ_PICK_RC(M)                                                           \
     switch (rc) {                                                               \
-        case 1: return resident_pick_rc1_m##M(rpt, csr_smem, packed, ell);    \
-        case 2: return resident_pick_rc2_m##M(rpt, csr_smem, packed, ell);    \
-        case 4: return resident_pick_rc4_m##M(rpt, csr_smem, packed, ell);    \
-        default: return resident_pick_rc8_m##M(rpt, csr_smem, packed, ell);   \
+        case 1: return resident_pick_rc1_m##M(rpt, csr_smem, packed, ell, threads); \
+        case 2: return resident_pick_rc2_m##M(rpt, csr_smem, packed, ell, threads); \
+        case 4: return resident_pick_rc4_m##M(rpt, csr_smem, packed, ell, threads); \
+        default: return resident_pick_rc8_m##M(rpt, csr_smem, packed, ell, threads); \
     }
     if (method == VELOXQ_METHOD_PA) { VQ_PICK_RC(2) }
     if (method == VELOXQ_METHOD_ASB) { VQ_PICK_RC(1) }
@@ -133,7 +133,7 @@ int resident_run(veloxq_ctx* ctx, int32_t R, const RunParams& rp, uint64_t seed,
     a.F_out = F_out;
     a.best_e = best_e;
     a.best_bits = best_bits;
-    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d, rp.method);
+    KFn fn = pick_kernel(p.rc, p.rpt, p.csr_smem, p.packed, p.ell_d, p.threads, rp.method);
     if (!fn) return fail(VELOXQ_EUNSUPPORTED, "no resident kernel variant for this plan");
     VQ_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem));
     fn<<<(unsigned)div_up(R, p.rc), p.threads, p.smem, ctx->stream>>>(a);

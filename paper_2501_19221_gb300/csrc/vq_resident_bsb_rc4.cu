@@ -4,6 +4,6 @@
 
 namespace vq {
 
-VQ_RESIDENT_PICK(4, 0) { return resident::pick_rpt<4, 0>(rpt, csr_smem, packed, ell); }
+VQ_RESIDENT_PICK(4, 0) { return resident::pick_rpt<4, 0>(rpt, csr_smem, packed, ell, threads); }
 
 }  // namespace vq

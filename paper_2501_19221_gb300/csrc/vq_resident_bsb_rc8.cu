@@ -4,6 +4,6 @@
 
 namespace vq {
 
-VQ_RESIDENT_PICK(8, 0) { return resident::pick_rpt<8, 0>(rpt, csr_smem, packed, ell); }
+VQ_RESIDENT_PICK(8, 0) { return resident::pick_rpt<8, 0>(rpt, csr_smem, packed, ell, threads); }
 
 }  // namespace vq

@@ -208,13 +208,18 @@ template <int RC> __device__ __forceinline__ void st_spin(uint16_t* g, int j, co
 // the second holds two BF16 buffers of their binarised spins (the field's
 // operand), current and next; readouts take x = [spin > 0] = [x > 0]. ELL: 0, rows in
 // CSR form; 6, six slots per row (Chimera graphs, cubic lattices), a count
-// known here, so the slot loops unroll completely; 1, a.ell_d slots.
+// known here, so the slot loops unroll completely; 1, a.ell_d slots; 32, at
+// most 32 slots with one row per thread (RPT = 1): the thread keeps its row's
+// coupling words in registers for the whole run, so a step issues the
+// neighbours' loads back to back instead of each behind a shared-memory load
+// of its coupling word (small dense instances, whose steps are latency-bound).
 template <int RC, int RPT, bool CSR_SMEM, bool PACKED, int MAXT, int ELL, int METHOD>
 __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     constexpr bool SIGN = METHOD == vqd::METHOD_PA;
     extern __shared__ __align__(16) unsigned char smem[];
     const int n = a.n;
     const int ELLD = ELL == 6 ? 6 : a.ell_d;   // slots per row (ELL != 0)
+    static_assert(ELL != 32 || RPT == 1, "coupling words in registers need one row per thread");
     const int T = blockDim.x;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
@@ -298,6 +303,12 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
     }
     __syncthreads();
 
+    // ELL == 32: this thread's row of coupling words, held for the whole run
+    uint32_t pk[ELL == 32 ? 32 : 1];
+    if constexpr (ELL == 32) {
+#pragma unroll
+        for (int p = 0; p < 32; ++p) pk[p] = (p < ELLD && tid < n) ? packs[(int64_t)p * n + tid] : 0u;
+    }
     float* sc = sA;
     float* sn = SIGN ? sA : sB;
     // a neighbour's field operand: its state row, or (PA) its spin row
@@ -316,7 +327,16 @@ __global__ void __launch_bounds__(MAXT, 1) k_resident(const ResArgs a) {
         auto row_field = [&](int i, float (&acc)[RC]) {
 #pragma unroll
             for (int r = 0; r < RC; ++r) acc[r] = 0.0f;
-            if constexpr (ELL != 0) {
+            if constexpr (ELL == 32) {
+                // slot order, as in the other layouts
+#pragma unroll
+                for (int p = 0; p < 32; ++p)
+                    if (p < ELLD) {
+                        float sj[RC];
+                        nb_at((int)(pk[p] & 0xFFFFu), sj);
+                        acc_fma<RC>(acc, ent_w(pk[p]), sj);
+                    }
+            } else if constexpr (ELL != 0) {
                 // two slots per iteration: both neighbours' loads are in flight together
                 const uint32_t* e = packs + i;
 #pragma unroll
@@ -561,12 +581,16 @@ using KFn = void (*)(const ResArgs);
 
 // 1024-thread CTAs keep at most 8 momenta per thread in registers (64-register
 // cap); 512-thread CTAs up to 32.
-template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, int ell_d) {
+template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, int ell_d, int threads) {
     constexpr int MAXT = (RC * RPT <= 8) ? 1024 : 512;
     if constexpr (RC * RPT > 32) {
         return nullptr;   // never planned (the momenta do not fit in registers)
     } else {
         if (!csr_smem) return k_resident<RC, RPT, false, false, MAXT, 0, METHOD>;
+        if constexpr (RPT == 1) {
+            // the 32 coupling words need the 128-register budget of a 512-thread CTA
+            if (ell_d > 0 && ell_d <= 32 && threads <= 512) return k_resident<RC, 1, true, true, 512, 32, METHOD>;
+        }
         if (ell_d == 6) return k_resident<RC, RPT, true, true, MAXT, 6, METHOD>;
         if (ell_d > 0) return k_resident<RC, RPT, true, true, MAXT, 1, METHOD>;
         return packed ? k_resident<RC, RPT, true, true, MAXT, 0, METHOD>
@@ -575,13 +599,13 @@ template <int RC, int RPT, int METHOD> KFn pick_csr(bool csr_smem, bool packed, 
 }
 
 // the variants of one replica count per CTA and one integrator
-template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, int ell) {
+template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, int ell, int threads) {
     switch (rpt) {
-        case 1: return pick_csr<RC, 1, METHOD>(csr_smem, packed, ell);
-        case 2: return pick_csr<RC, 2, METHOD>(csr_smem, packed, ell);
-        case 4: return pick_csr<RC, 4, METHOD>(csr_smem, packed, ell);
-        case 8: return pick_csr<RC, 8, METHOD>(csr_smem, packed, ell);
-        default: return pick_csr<RC, 16, METHOD>(csr_smem, packed, ell);
+        case 1: return pick_csr<RC, 1, METHOD>(csr_smem, packed, ell, threads);
+        case 2: return pick_csr<RC, 2, METHOD>(csr_smem, packed, ell, threads);
+        case 4: return pick_csr<RC, 4, METHOD>(csr_smem, packed, ell, threads);
+        case 8: return pick_csr<RC, 8, METHOD>(csr_smem, packed, ell, threads);
+        default: return pick_csr<RC, 16, METHOD>(csr_smem, packed, ell, threads);
     }
 }
 
@@ -589,7 +613,7 @@ template <int RC, int METHOD> KFn pick_rpt(int rpt, bool csr_smem, bool packed, 
 
 // one per replica count per CTA and integrator (vq_resident_*.cu, compiled in parallel)
 #define VQ_RESIDENT_PICK(RC, M) \
-    resident::KFn resident_pick_rc##RC##_m##M(int rpt, bool csr_smem, bool packed, int ell)
+    resident::KFn resident_pick_rc##RC##_m##M(int rpt, bool csr_smem, bool packed, int ell, int threads)
 VQ_RESIDENT_PICK(1, 0); VQ_RESIDENT_PICK(2, 0); VQ_RESIDENT_PICK(4, 0); VQ_RESIDENT_PICK(8, 0);
 VQ_RESIDENT_PICK(1, 1); VQ_RESIDENT_PICK(2, 1); VQ_RESIDENT_PICK(4, 1); VQ_RESIDENT_PICK(8, 1);
 VQ_RESIDENT_PICK(1, 2); VQ_RESIDENT_PICK(2, 2); VQ_RESIDENT_PICK(4, 2); VQ_RESIDENT_PICK(8, 2);

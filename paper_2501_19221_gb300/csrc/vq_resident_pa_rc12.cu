@@ -4,7 +4,7 @@
 
 namespace vq {
 
-VQ_RESIDENT_PICK(1, 2) { return resident::pick_rpt<1, 2>(rpt, csr_smem, packed, ell); }
-VQ_RESIDENT_PICK(2, 2) { return resident::pick_rpt<2, 2>(rpt, csr_smem, packed, ell); }
+VQ_RESIDENT_PICK(1, 2) { return resident::pick_rpt<1, 2>(rpt, csr_smem, packed, ell, threads); }
+VQ_RESIDENT_PICK(2, 2) { return resident::pick_rpt<2, 2>(rpt, csr_smem, packed, ell, threads); }
 
 }  // namespace vq

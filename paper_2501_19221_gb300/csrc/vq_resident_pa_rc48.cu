@@ -4,7 +4,7 @@
 
 namespace vq {
 
-VQ_RESIDENT_PICK(4, 2) { return resident::pick_rpt<4, 2>(rpt, csr_smem, packed, ell); }
-VQ_RESIDENT_PICK(8, 2) { return resident::pick_rpt<8, 2>(rpt, csr_smem, packed, ell); }
+VQ_RESIDENT_PICK(4, 2) { return resident::pick_rpt<4, 2>(rpt, csr_smem, packed, ell, threads); }
+VQ_RESIDENT_PICK(8, 2) { return resident::pick_rpt<8, 2>(rpt, csr_smem, packed, ell, threads); }
 
 }  // namespace vq
