@@ -90,11 +90,13 @@ __global__ void k_dense_mirror(T* q, int64_t n) {
     }
 }
 
-// Per row: off-diagonal row sum, |.| row sum, diagonal (one block per row).
+// Per row: off-diagonal row sum, |.| row sum, diagonal (one block per row,
+// rows row0, row0 + 1, ...).
 template <typename T>
-__global__ void k_dense_rows(const T* __restrict__ q, int64_t n, double* rowsum, double* absrow, double* diag) {
+__global__ void k_dense_rows(const T* __restrict__ q, int64_t n, int64_t row0, double* rowsum, double* absrow,
+                             double* diag) {
     __shared__ double s1[256], s2[256];
-    const int64_t i = blockIdx.x;
+    const int64_t i = row0 + blockIdx.x;
     const T* row = q + i * n;
     double a = 0.0, b = 0.0;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x)
@@ -121,19 +123,21 @@ __global__ void k_dense_rows(const T* __restrict__ q, int64_t n, double* rowsum,
 }
 
 // Per column: off-diagonal column sums, as partial sums over chunks of
-// kColRows rows (grid: column blocks x row chunks, loads coalesced over the
-// columns), then the chunks added in order for each column.
+// kColRows rows (grid: column blocks x row chunks chunk0, chunk0 + 1, ...,
+// loads coalesced over the columns), then the chunks added in order for each
+// column.
 constexpr int kColRows = 256;
 template <typename T>
-__global__ void k_dense_cols_part(const T* __restrict__ q, int64_t n, double* __restrict__ part) {
+__global__ void k_dense_cols_part(const T* __restrict__ q, int64_t n, int64_t chunk0, double* __restrict__ part) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t i0 = (int64_t)blockIdx.y * kColRows, i1 = i0 + kColRows < n ? i0 + kColRows : n;
+    const int64_t c = chunk0 + blockIdx.y;
+    const int64_t i0 = c * kColRows, i1 = i0 + kColRows < n ? i0 + kColRows : n;
     if (j >= n) return;
     double a = 0.0;
 #pragma unroll 8
     for (int64_t i = i0; i < i1; ++i)
         if (i != j) a += to_d(q[i * n + j]);
-    part[(int64_t)blockIdx.y * n + j] = a;
+    part[c * n + j] = a;
 }
 __global__ void k_dense_cols_sum(int64_t n, int chunks, const double* __restrict__ part, double* colsum) {
     const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -651,7 +655,6 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     cudaStream_t st = ctx->stream;
     const size_t qbytes = sizeof(T) * (size_t)n * (size_t)n;
     VQ_TRY(ctx->qx.ensure(qbytes));
-    VQ_CUDA(cudaMemcpyAsync(ctx->qx.p, Qh, qbytes, cudaMemcpyHostToDevice, st));
     T* q = ctx->qx.as<T>();
     DevBuf tmp;
     // rowsum, colsum, absrow, diag, lin, d, absd, part, scalars, column-sum chunks
@@ -673,10 +676,48 @@ int ingest_dense_t(veloxq_ctx* ctx, const void* Qh, const double* ch, bool ising
     else VQ_CUDA(cudaMemsetAsync(lin, 0, sizeof(double) * n, st));
     const int64_t total = n * n;
     const int gb = (int)std::min<int64_t>(div_up(total, 256), (int64_t)device_sms(ctx->device) * 16);
-    k_dense_check<T><<<gb, 256, 0, st>>>(q, total, err);
-    if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
-    k_dense_rows<T><<<(unsigned)n, 256, 0, st>>>(q, n, rowsum, absrow, diag);
-    k_dense_cols_part<T><<<dim3((unsigned)div_up(n, 128), (unsigned)col_chunks), 128, 0, st>>>(q, n, cpart);
+    // Q goes up in row chunks (whole kColRows blocks) on a helper stream; the
+    // checks, row sums and column partial sums of a chunk run on the context
+    // stream as soon as it has arrived, under the upload of the next one. The
+    // sums are the same as over the whole matrix at once (per row, and per
+    // kColRows-row chunk of a column). Ising input is mirrored across the
+    // diagonal first, which needs every row: it goes up in one piece.
+    const int64_t rows_per = (ising || n < 4 * kColRows) ? n : div_up(div_up(n, 4), kColRows) * kColRows;
+    const int nup = (int)div_up(n, rows_per);
+    struct Upload {
+        cudaStream_t s = nullptr;
+        std::vector<cudaEvent_t> ev;
+        ~Upload() {
+            for (cudaEvent_t e : ev)
+                if (e) cudaEventDestroy(e);
+            if (s) cudaStreamDestroy(s);   // released once its copies are done
+        }
+    } up;
+    if (nup > 1) {
+        VQ_CUDA(cudaStreamCreateWithFlags(&up.s, cudaStreamNonBlocking));
+        up.ev.assign((size_t)nup + 1, nullptr);
+        for (cudaEvent_t& e : up.ev) VQ_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        VQ_CUDA(cudaEventRecord(up.ev[0], st));            // after everything enqueued on the context stream
+        VQ_CUDA(cudaStreamWaitEvent(up.s, up.ev[0], 0));
+    }
+    const T* Qt = static_cast<const T*>(Qh);
+    for (int c = 0; c < nup; ++c) {
+        const int64_t r0 = c * rows_per, r1 = std::min<int64_t>(n, r0 + rows_per);
+        const int64_t cnt = (r1 - r0) * n;
+        if (nup > 1) {
+            VQ_CUDA(cudaMemcpyAsync(q + r0 * n, Qt + r0 * n, sizeof(T) * (size_t)cnt, cudaMemcpyHostToDevice, up.s));
+            VQ_CUDA(cudaEventRecord(up.ev[(size_t)c + 1], up.s));
+            VQ_CUDA(cudaStreamWaitEvent(st, up.ev[(size_t)c + 1], 0));
+        } else {
+            VQ_CUDA(cudaMemcpyAsync(q, Qh, qbytes, cudaMemcpyHostToDevice, st));
+        }
+        const int gbc = (int)std::min<int64_t>(div_up(cnt, 256), (int64_t)gb);
+        k_dense_check<T><<<gbc, 256, 0, st>>>(q + r0 * n, cnt, err);
+        if (ising) k_dense_mirror<T><<<gb, 256, 0, st>>>(q, n);
+        k_dense_rows<T><<<(unsigned)(r1 - r0), 256, 0, st>>>(q, n, r0, rowsum, absrow, diag);
+        k_dense_cols_part<T><<<dim3((unsigned)div_up(n, 128), (unsigned)div_up(r1 - r0, kColRows)), 128, 0, st>>>(
+            q, n, r0 / kColRows, cpart);
+    }
     k_dense_cols_sum<<<(unsigned)div_up(n, 256), 256, 0, st>>>(n, col_chunks, cpart, colsum);
     VQ_TRY(ctx->qoff32.ensure(sizeof(float) * (size_t)total));
     dim3 tb(32, 8), tg((unsigned)div_up(n, 32), (unsigned)div_up(n, 32));
